@@ -1,0 +1,154 @@
+"""Seeded synthetic inputs for primed-PCA workloads.
+
+This module is shared by the tests, ``bench.py`` and ``__graft_entry__.smoke()``
+and feeds both the CUDA path and the FP64 oracle.  It holds none of the pPCA
+arithmetic: it only draws data matrices with a prescribed population spectrum
+and initial bases.
+
+Generators:
+
+* ``gaussian_data``: X = G diag(sqrt(lambda)) Q^T with G i.i.d. N(0, 1), Q Haar
+  orthogonal, columns centred -- the known-lambda recipe of the workloads.
+* ``exact_spectrum_data``: X = U diag(sigma) Q^T with U's orthonormal columns
+  orthogonal to the all-ones vector, so X is centred and X^T X = Q diag(sigma^2)
+  Q^T holds up to rounding: eigenpairs known in closed form.
+* ``initial_basis``: Gaussian d x m starting basis for the primers.
+
+Small problems are drawn with numpy on the host (float64, then rounded to the
+storage type).  Large problems (``*_torch``) are drawn on a torch device in
+row chunks so that nothing larger than one chunk of G is ever materialised.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .configs import CONFIGS, Config, spectrum  # noqa: F401
+
+
+def haar_orthogonal(d: int, rng: np.random.Generator) -> np.ndarray:
+    """Haar-distributed d x d orthogonal matrix: QR of a Gaussian, R's diagonal made positive."""
+    G = rng.standard_normal((d, d))
+    Q, R = np.linalg.qr(G)
+    return Q * np.sign(np.diag(R))[None, :]
+
+
+def gaussian_data(n: int, d: int, lam, seed: int, center: bool = True):
+    """(X, Q): X = G diag(sqrt(lam)) Q^T in float64, columns centred."""
+    lam = np.asarray(lam, dtype=np.float64)
+    assert lam.shape == (d,)
+    rng = np.random.default_rng(seed)
+    Q = haar_orthogonal(d, rng)
+    G = rng.standard_normal((n, d))
+    X = (G * np.sqrt(lam)[None, :]) @ Q.T
+    if center:
+        X -= X.mean(axis=0, keepdims=True)
+    return X, Q
+
+
+def exact_spectrum_data(n: int, d: int, sigma, seed: int):
+    """(X, Q): X = U diag(sigma) Q^T, U^T U = I, U^T 1 = 0, so X^T X = Q diag(sigma^2) Q^T.
+
+    Requires n > d.  U is the QR factor of a column-centred Gaussian n x d.
+    """
+    sigma = np.asarray(sigma, dtype=np.float64)
+    assert sigma.shape == (d,) and n > d
+    rng = np.random.default_rng(seed)
+    Q = haar_orthogonal(d, rng)
+    A = rng.standard_normal((n, d))
+    A -= A.mean(axis=0, keepdims=True)
+    U, R = np.linalg.qr(A)
+    U = U * np.sign(np.diag(R))[None, :]
+    X = (U * sigma[None, :]) @ Q.T
+    return X, Q
+
+
+def initial_basis(d: int, m: int, seed: int) -> np.ndarray:
+    """Gaussian d x m starting basis (float64)."""
+    rng = np.random.default_rng(seed + 7919)
+    return rng.standard_normal((d, m))
+
+
+def affine_to_unit_and_recentre(X: np.ndarray) -> np.ndarray:
+    """Global affine map of all entries to [0, 1], then columns re-centred (image-like data)."""
+    lo, hi = float(X.min()), float(X.max())
+    Y = (X - lo) / (hi - lo)
+    return Y - Y.mean(axis=0, keepdims=True)
+
+
+# ---------------------------------------------------------------------------
+# Large problems on a torch device
+# ---------------------------------------------------------------------------
+
+def gaussian_data_torch(n: int, d: int, lam, seed: int, device, out_dtype, chunk_rows: int = 65536,
+                        image_like: bool = False):
+    """X = G diag(sqrt(lam)) Q^T drawn on ``device`` in row chunks, stored as ``out_dtype``.
+
+    Returns (X, Q_host).  Q is Haar (drawn on the host in float64); G comes from
+    a seeded torch generator on the device.  Columns are centred with column
+    means accumulated in float64.  With ``image_like`` the values are mapped by
+    one global affine map to [0, 1] and re-centred.
+    """
+    import torch
+
+    lam = np.asarray(lam, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    Q = haar_orthogonal(d, rng)
+    B = torch.from_numpy((np.sqrt(lam)[:, None] * Q.T).astype(np.float32)).to(device)   # d x d
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    X = torch.empty((n, d), dtype=torch.float32, device=device)
+    for r0 in range(0, n, chunk_rows):
+        r1 = min(n, r0 + chunk_rows)
+        G = torch.randn((r1 - r0, d), generator=gen, device=device, dtype=torch.float32)
+        X[r0:r1] = G @ B
+        del G
+    mean = torch.zeros(d, dtype=torch.float64, device=device)
+    for r0 in range(0, n, chunk_rows):
+        mean += X[r0:r0 + chunk_rows].double().sum(0)
+    mean /= n
+    X -= mean.float()[None, :]
+    if image_like:
+        lo, hi = float(X.min()), float(X.max())
+        X -= lo
+        X /= (hi - lo)
+        mean.zero_()
+        for r0 in range(0, n, chunk_rows):
+            mean += X[r0:r0 + chunk_rows].double().sum(0)
+        mean /= n
+        X -= mean.float()[None, :]
+    if out_dtype != torch.float32:
+        Xo = torch.empty((n, d), dtype=out_dtype, device=device)
+        for r0 in range(0, n, chunk_rows):
+            Xo[r0:r0 + chunk_rows] = X[r0:r0 + chunk_rows].to(out_dtype)
+        del X
+        X = Xo
+    return X, Q
+
+
+def counterexample_points():
+    """The 6-point, 3-dimensional data set of the counterexample (Section 4.1)."""
+    return np.array([[3, 0, 0], [-3, 0, 0], [0, 2, 0], [0, -2, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)
+
+
+def minibatch_schedule_rows(n: int, b: int, steps: int, t0: int = 0):
+    """Row ranges a primer visits (for bookkeeping of bytes streamed)."""
+    per_epoch = -(-n // b)
+    out = []
+    for t in range(t0, t0 + steps):
+        j = t % per_epoch
+        out.append((j * b, min(n, j * b + b)))
+    return out
+
+
+def bytes_of(n: int, d: int, dtype: str) -> int:
+    return n * d * {"f32": 4, "bf16": 2, "fp8": 1}[dtype] + (4 * n if dtype == "fp8" else 0)
+
+
+def ceil_div(a: int, b: int) -> int:
+    return -(-a // b)
+
+
+def log2_int(x: int) -> int:
+    return int(math.log2(x))

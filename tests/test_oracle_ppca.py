@@ -1,0 +1,186 @@
+"""Pins for the oracle's pPCA step (Algorithm 1), orthonormalisation and metrics.
+
+* the counterexample of Section 4.1, with the paper's numbers (golden fixture);
+* the variance identity of Section 4.2 (Var of X~ is Var of X restricted to S);
+* the pPCA output lies in span(V), is orthonormal, depends only on span(V), and
+  equals the top-k eigenpairs of P_V X^T X P_V (computed separately in d dims);
+* exact recovery when span(V) is a dominant eigenspace (Theorem 4.4's limit);
+* Cauchy interlacing of the Ritz values;
+* the LCES worked example of Section 5.3.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(name):
+    with open(os.path.join(GOLDEN, name)) as f:
+        return json.load(f)
+
+
+# --------------------------------------------------------------------------- orth
+
+@pytest.mark.parametrize("shape", [(10, 1), (50, 7), (200, 32)])
+def test_orth_is_thin_qr_with_positive_diagonal(shape):
+    rng = np.random.default_rng(shape[0])
+    V = rng.standard_normal(shape)
+    Q, R = oracle.qr_pos(V)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(shape[1]), atol=1e-14)
+    np.testing.assert_allclose(Q @ R, V, atol=1e-12)
+    assert np.all(np.diag(R) > 0)
+    assert np.allclose(np.tril(Q.T @ V, -1), 0.0, atol=1e-12)
+    # unique thin QR: agrees with LAPACK's after fixing signs
+    Ql, Rl = np.linalg.qr(V)
+    Ql = Ql * np.sign(np.diag(Rl))[None, :]
+    np.testing.assert_allclose(Q, Ql, atol=1e-12)
+
+
+def test_orth_ill_conditioned():
+    rng = np.random.default_rng(3)
+    U, _ = np.linalg.qr(rng.standard_normal((300, 20)))
+    V = U * (10.0 ** -np.arange(20) * 0.5)[None, :]   # kappa ~ 1e19 by column scaling
+    Q = oracle.orth(V @ np.triu(np.ones((20, 20))))
+    np.testing.assert_allclose(Q.T @ Q, np.eye(20), atol=1e-13)
+
+
+# --------------------------------------------------------------- counterexample
+
+def test_counterexample_covariance_matches_paper():
+    g = load("counterexample.json")
+    X = np.array(g["points"], dtype=float)
+    np.testing.assert_array_equal(X, synth.counterexample_points())
+    C = oracle.covariance(X) / X.shape[0]
+    np.testing.assert_allclose(3.0 * C, np.array(g["covariance_over_n_times_3"], dtype=float), atol=1e-15)
+    E, lam = oracle.ground_truth(X, 2)
+    np.testing.assert_allclose(np.abs(E.T), np.array(g["top2_principal_directions"], dtype=float), atol=1e-15)
+    np.testing.assert_allclose(lam, [3.0, 4.0 / 3.0], rtol=1e-15)
+
+
+@pytest.mark.parametrize("eps", load("counterexample.json")["eps_cases"])
+def test_counterexample_ppca(eps):
+    X = synth.counterexample_points()
+    V = np.array([[eps, 0.0], [0.0, 1.0], [math.sqrt(1 - eps * eps), 0.0]])
+    E, lam = oracle.ppca_finalize(X, V, 2)
+    # projected covariance diag((1 + 8 eps^2)/3, 4/3) (corrected (1,1) entry)
+    expected = sorted([(1 + 8 * eps * eps) / 3.0, 4.0 / 3.0], reverse=True)
+    np.testing.assert_allclose(lam, expected, rtol=1e-13)
+    e1 = np.array([1.0, 0.0, 0.0])
+    if eps * eps < 3.0 / 8.0:
+        # pPCA swaps: its first direction is the second priming vector (0,1,0)
+        assert oracle.angle(E[:, 0], [0.0, 1.0, 0.0]) < 1e-12
+        assert abs(E[:, 0] @ e1) ** 2 < eps * eps + 1e-15 or eps == 0.0
+        assert abs(E[:, 0] @ e1) < 1e-12
+    else:
+        assert oracle.angle(E[:, 0], V[:, 0]) < 1e-12
+        assert oracle.angle(E[:, 1], [0.0, 1.0, 0.0]) < 1e-12
+
+
+# ------------------------------------------------------------ pPCA invariants
+
+def _problem(seed=11, n=500, d=30, m=6):
+    rng = np.random.default_rng(seed)
+    lam = 0.8 ** np.arange(1, d + 1)
+    X, _ = synth.gaussian_data(n, d, lam, seed)
+    V = rng.standard_normal((d, m))
+    return X, V
+
+
+def test_variance_restricted_to_S():
+    """Section 4.2: v^T (X~^T X~) v = v^T (X^T X) v for v in S."""
+    X, V = _problem()
+    Q = oracle.orth(V)
+    Xt = X @ Q @ Q.T                      # projected points x~_i = P_S x_i
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        v = Q @ rng.standard_normal(Q.shape[1])
+        v /= np.linalg.norm(v)
+        assert math.isclose(oracle.variance_captured(Xt, v), oracle.variance_captured(X, v), rel_tol=1e-12)
+
+
+def test_ppca_output_in_span_orthonormal_and_top_eigs_of_projected_cov():
+    X, V = _problem()
+    n, d = X.shape
+    k = 4
+    E, lam = oracle.ppca_finalize(X, V, k)
+    Q = oracle.orth(V)
+    np.testing.assert_allclose(E.T @ E, np.eye(k), atol=1e-13)
+    np.testing.assert_allclose(E - Q @ (Q.T @ E), 0.0, atol=1e-13)
+    # full d x d eigenproblem of P C P, solved separately
+    P = Q @ Q.T
+    C = oracle.covariance(X)
+    w_full, U_full = oracle.eigh_desc(P @ C @ P)
+    np.testing.assert_allclose(lam * n, w_full[:k], rtol=1e-11)
+    for i in range(k):
+        assert oracle.angle(E[:, i], U_full[:, i]) < 1e-9
+    # residual of the projected problem
+    R = P @ C @ P @ E - E * (lam * n)[None, :]
+    assert np.abs(R).max() < 1e-10 * lam[0] * n
+
+
+def test_ppca_depends_only_on_span():
+    X, V = _problem(seed=4)
+    rng = np.random.default_rng(9)
+    M = rng.standard_normal((V.shape[1], V.shape[1])) + 3 * np.eye(V.shape[1])
+    E1, l1 = oracle.ppca_finalize(X, V, 5)
+    E2, l2 = oracle.ppca_finalize(X, V @ M, 5)
+    np.testing.assert_allclose(l1, l2, rtol=1e-11)
+    np.testing.assert_allclose(E1, E2, atol=1e-9)
+
+
+def test_ppca_exact_when_span_is_dominant_eigenspace():
+    X, _ = _problem(seed=8, n=600, d=25)
+    Etrue, ltrue = oracle.ground_truth(X)
+    rng = np.random.default_rng(2)
+    m, k = 7, 5
+    V = Etrue[:, :m] @ (rng.standard_normal((m, m)) + 2 * np.eye(m))
+    E, lam = oracle.ppca_finalize(X, V, k)
+    np.testing.assert_allclose(lam, ltrue[:k], rtol=1e-11)
+    for i in range(k):
+        assert oracle.angle(E[:, i], Etrue[:, i]) < 1e-9
+
+
+def test_interlacing():
+    X, V = _problem(seed=21, m=8)
+    n = X.shape[0]
+    _, lfull = oracle.ground_truth(X)
+    _, lproj = oracle.ppca_finalize(X, V, 8)
+    assert np.all(lproj <= lfull[:8] * (1 + 1e-12))
+
+
+# --------------------------------------------------------------------- metrics
+
+def test_lces_worked_example():
+    g = load("lces_example.json")
+    V = math.pi / 8
+    angles = [a * V for a in g["angles_in_units_of_V"]]
+    assert oracle.lces(angles, V) == g["expected_lces"]
+    # strict inequality, and a full streak
+    assert oracle.lces([V, 0.0], V) == 0
+    assert oracle.lces([0.0, 0.1 * V], V) == 2
+
+
+def test_angle_sign_invariant_and_small_angles():
+    e = np.array([1.0, 0.0, 0.0])
+    for t in [1e-9, 1e-6, 1e-3, 0.5, math.pi / 2]:
+        v = np.array([math.cos(t), math.sin(t), 0.0])
+        assert math.isclose(oracle.angle(v, e), t, rel_tol=1e-9, abs_tol=1e-15)
+        assert math.isclose(oracle.angle(-3.0 * v, e), t, rel_tol=1e-9, abs_tol=1e-15)
+
+
+def test_principal_angles_known():
+    d = 6
+    t = [0.3, 1e-5]
+    Q = np.eye(d)[:, :2]
+    E = np.zeros((d, 2))
+    E[:, 0] = [math.cos(t[0]), 0, math.sin(t[0]), 0, 0, 0]
+    E[:, 1] = [0, math.cos(t[1]), 0, math.sin(t[1]), 0, 0]
+    pa = oracle.principal_angles(Q, E)
+    np.testing.assert_allclose(pa, sorted(t), rtol=1e-9)

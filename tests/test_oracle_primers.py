@@ -1,0 +1,200 @@
+"""Pins for the oracle's primers (block power, Oja/Sanger, EigenGame) and schedule.
+
+* fixed points: the exact eigenvectors are fixed by a power step, give a zero
+  Oja/Sanger update with the full batch (Section 2.2) and a zero Riemannian
+  EigenGame gradient (the Nash equilibrium, Section 2.3);
+* special cases: Oja with one point and one neuron is the paper's single-neuron
+  rule (Section 2.2); EigenGame with one player is gradient ascent on
+  v^T M v (Eq. 1);
+* convergence rate of simultaneous iteration (Rutishauser's bound);
+* ordered convergence: Sanger and EigenGame find the individual eigenvectors,
+  not just the subspace -- and two planted mistakes (Oja's symmetric subspace
+  rule, EigenGame without the penalty) are shown to fail that pin.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import oracle.core as core
+import synth
+
+
+def small_problem(n=3000, d=12, seed=3):
+    sigma = np.sqrt(n * np.linspace(3.0, 0.5, d) ** 2)
+    X, Q = synth.exact_spectrum_data(n, d, sigma, seed)
+    lam = sigma ** 2 / n                      # eig(X^T X)/n exactly
+    return X, Q, lam
+
+
+# ------------------------------------------------------------------ schedule
+
+def test_minibatch_schedule_epoch_aligned():
+    n, b = 1000, 256
+    seen = np.zeros(n, dtype=int)
+    for t in range(4):
+        r0, r1 = oracle.minibatch_rows(t, n, b)
+        seen[r0:r1] += 1
+    assert np.all(seen == 1)
+    assert oracle.minibatch_rows(3, n, b) == (768, 1000)
+    assert oracle.minibatch_rows(4, n, b) == (0, 256)
+    assert oracle.minibatch_rows(0, 100, 256) == (0, 100)
+
+
+# ------------------------------------------------------------------ power
+
+def test_power_fixed_point():
+    X, Q, lam = small_problem()
+    E = Q[:, :5]
+    E = E * np.sign(E[np.argmax(np.abs(E), axis=0), np.arange(5)])
+    S = oracle.power_step(X, E)
+    # orth keeps a positive diagonal, E's columns are already orthonormal
+    np.testing.assert_allclose(np.abs(S.T @ E), np.eye(5), atol=1e-12)
+
+
+@pytest.mark.parametrize("T", [1, 3, 6])
+def test_power_rutishauser_bound(T):
+    X, Q, lam = small_problem(seed=7)
+    m = 4
+    rng = np.random.default_rng(T)
+    V0 = rng.standard_normal((X.shape[1], m))
+    Q0 = oracle.orth(V0)
+    theta0 = oracle.principal_angles(Q0, Q[:, :m]).max()
+    QT = oracle.power_prime(X, V0, T)
+    for i in range(m):
+        e = Q[:, i]
+        s = np.linalg.norm(e - QT @ (QT.T @ e))
+        tan_i = math.tan(math.asin(min(1.0, s)))
+        bound = (lam[m] / lam[i]) ** T * math.tan(theta0)
+        assert tan_i <= bound * (1 + 1e-9) + 1e-13
+
+
+def test_power_then_ppca_converges_to_ground_truth():
+    X, Q, lam = small_problem(seed=9)
+    V = oracle.power_prime(X, np.random.default_rng(0).standard_normal((12, 6)), 60)
+    E, l = oracle.ppca_finalize(X, V, 4)
+    np.testing.assert_allclose(l, lam[:4], rtol=1e-10)
+    for i in range(4):
+        assert oracle.angle(E[:, i], Q[:, i]) < 1e-6
+
+
+# ------------------------------------------------------------------ Oja / Sanger
+
+def test_oja_full_batch_fixed_point():
+    X, Q, lam = small_problem()
+    W = Q[:, :5].copy()
+    W2 = oracle.oja_step(X, W, 0, X.shape[0], lr=0.3)
+    np.testing.assert_allclose(W2, W, atol=1e-12)
+
+
+def test_oja_single_point_single_neuron_is_the_papers_rule():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((5, 7))
+    w = rng.standard_normal((7, 1))
+    alpha = 0.01
+    for t in range(5):
+        x = X[t:t + 1].T
+        y = float((x.T @ w)[0, 0])
+        paper = w + alpha * (x * y - y * y * w)          # dw = alpha (x y - y^2 w)
+        np.testing.assert_allclose(oracle.oja_step(X, w, t, 1, alpha), paper, atol=1e-14)
+
+
+def _ordered_convergence_oja(step_fn, X, Q, m, epochs=60, b=100):  # lr 0.02/(1+t/200)
+    rng = np.random.default_rng(4)
+    W = oracle.orth(rng.standard_normal((X.shape[1], m)))
+    steps = epochs * (-(-X.shape[0] // b))
+    for t in range(steps):
+        W = step_fn(X, W, t, b, 0.02 / (1.0 + t / 200.0))
+    return max(oracle.angle(W[:, i], Q[:, i]) for i in range(m))
+
+
+def test_oja_sanger_finds_individual_eigenvectors():
+    X, Q, lam = small_problem(n=2000, d=8, seed=12)
+    assert _ordered_convergence_oja(oracle.oja_step, X, Q, 3) < 0.02
+
+
+def _symmetric_subspace_rule(X, W, t, b, lr):
+    """Planted mistake: full Y^T Y instead of its upper triangle (Oja's subspace rule)."""
+    r0, r1 = oracle.minibatch_rows(t, X.shape[0], b)
+    Xb = X[r0:r1]
+    Y = Xb @ W
+    return W + lr / (r1 - r0) * (Xb.T @ Y - W @ (Y.T @ Y))
+
+
+def test_planted_mistake_in_oja_fails_the_ordering_pin():
+    X, Q, lam = small_problem(n=2000, d=8, seed=12)
+    assert _ordered_convergence_oja(_symmetric_subspace_rule, X, Q, 3) > 0.1
+
+
+# ------------------------------------------------------------------ EigenGame
+
+def test_eigengame_nash_equilibrium():
+    X, Q, lam = small_problem()
+    V = Q[:, :5].copy()
+    grad, MV, C = oracle.eigengame_gradients(X, V)
+    riem = grad - V * np.sum(V * grad, axis=0, keepdims=True)
+    assert np.abs(riem).max() < 1e-12 * lam[0]
+    V2, buf = oracle.eigengame_step(X, V, np.zeros_like(V), 0, X.shape[0], lr=0.1)
+    np.testing.assert_allclose(V2, V, atol=1e-13)
+
+
+def test_eigengame_single_player_is_rayleigh_ascent():
+    X, Q, lam = small_problem()
+    rng = np.random.default_rng(5)
+    v = oracle.orth(rng.standard_normal((X.shape[1], 1)))
+    grad, MV, C = oracle.eigengame_gradients(X, v)
+    M = X.T @ X / X.shape[0]
+    np.testing.assert_allclose(grad, 2.0 * M @ v, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(C, v.T @ M @ v, rtol=1e-13)
+
+
+def test_eigengame_utilities_gradient_by_finite_differences():
+    """Eq. 3: the oracle's gradient is the derivative of U_j in v_j."""
+    rng = np.random.default_rng(6)
+    Xb = rng.standard_normal((50, 6))
+    V = rng.standard_normal((6, 3))
+    M = Xb.T @ Xb / Xb.shape[0]
+
+    def U(j, Vm):
+        u = Vm[:, j] @ M @ Vm[:, j]
+        for i in range(j):
+            u -= (Vm[:, j] @ M @ Vm[:, i]) ** 2 / (Vm[:, i] @ M @ Vm[:, i])
+        return u
+
+    grad, _, _ = oracle.eigengame_gradients(Xb, V)
+    h = 1e-6
+    for j in range(3):
+        for a in range(6):
+            Vp, Vm_ = V.copy(), V.copy()
+            Vp[a, j] += h
+            Vm_[a, j] -= h
+            fd = (U(j, Vp) - U(j, Vm_)) / (2 * h)
+            assert abs(fd - grad[a, j]) < 1e-6 * max(1.0, abs(fd))
+
+
+def _ordered_convergence_eg(grad_fn, X, Q, m, steps=3000, b=500, lr=0.005):
+    saved = core.eigengame_gradients
+    core.eigengame_gradients = grad_fn
+    try:
+        V = oracle.eigengame_prime(X, np.random.default_rng(8).standard_normal((X.shape[1], m)),
+                                   b, steps, lr, 0.9)
+    finally:
+        core.eigengame_gradients = saved
+    return max(oracle.angle(V[:, i], Q[:, i]) for i in range(m))
+
+
+def test_eigengame_finds_individual_eigenvectors():
+    X, Q, lam = small_problem(n=2000, d=8, seed=12)
+    assert _ordered_convergence_eg(core.eigengame_gradients, X, Q, 3) < 0.02
+
+
+def _no_penalty(Xb, V):
+    """Planted mistake: each player ignores the others (drops Eq. 3's penalty)."""
+    MV = Xb.T @ (Xb @ V) / Xb.shape[0]
+    return 2.0 * MV, MV, V.T @ MV
+
+
+def test_planted_mistake_in_eigengame_fails_the_ordering_pin():
+    X, Q, lam = small_problem(n=2000, d=8, seed=12)
+    assert _ordered_convergence_eg(_no_penalty, X, Q, 3) > 0.1
