@@ -1,0 +1,260 @@
+/*
+ * ppca.h -- C ABI of the GB300 primed-PCA (pPCA) library.
+ *
+ * Primed PCA (Algorithm 1, "Primed PCA (pPCA_l)") takes a centred data set of
+ * n points in d dimensions and two integers k > 0, l >= 0, runs a PRIMING
+ * method that returns m = k + l approximate principal directions (step 1),
+ * projects the data onto their span (steps 2-3) and runs an exact PCA in that
+ * m-dimensional subspace (step 4), returning the first k principal components
+ * (step 5).  This library implements the data-parallel hot path on one GPU:
+ *
+ *   ppca_create    borrow X (n x d, device) and validate it           (Input)
+ *   ppca_prime     PRIMING(X, k + l): block power, Oja, EigenGame     (step 1)
+ *   ppca_finalize  span -> project -> full-PCA -> top k               (steps 2-5)
+ *
+ * plus the individual steps (one X-pass, orthonormalisation, the small
+ * eigensolve, quantisation) so that each can be checked and timed alone.
+ *
+ * Conventions shared by every call:
+ *   - Pointers marked "device" are CUDA device pointers on the handle's device;
+ *     "host" pointers are ordinary host memory.  The caller owns every buffer
+ *     it passes (X, scales, V0, outputs); the library never frees them and does
+ *     not retain them beyond the handle's lifetime.  A handle owns only its own
+ *     workspace, allocated on first use and freed by ppca_destroy.
+ *   - X is row-major with leading dimension ld (elements), ld >= d; its base
+ *     address and the row pitch ld * sizeof(element) must be multiples of 16
+ *     bytes (the kernels stage X with the Tensor Memory Accelerator).
+ *   - Basis and eigenvector matrices (V0, V, Z, Q, E) are d x m column-major
+ *     FP32: column j (one direction) is d contiguous floats, columns d apart.
+ *   - X is assumed already centred (Section 1); the library does not centre.
+ *   - All device work is enqueued on the handle's stream (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream) and is asynchronous.  Errors
+ *     found on the host (arguments, allocation, launch) are returned at once.
+ *     Errors found on the device (a Cholesky breakdown, a Jacobi sweep cap, a
+ *     bounded wait that ran out) are written to a device status word and
+ *     returned by the next ppca_sync() on that handle.
+ *   - No call throws; every call returns a ppca_status.  ppca_last_error()
+ *     gives a message for the last non-OK status of the calling thread.
+ *   - Eigenvalues are reported as eig(X^T X) / n, in descending order;
+ *     eigenvectors are unit vectors signed so that each one's largest-magnitude
+ *     entry (lowest index among ties) is positive.
+ */
+#ifndef PPCA_H
+#define PPCA_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PPCA_API __attribute__((visibility("default")))
+#else
+#define PPCA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ppca_status {
+    PPCA_OK = 0,
+    PPCA_ERR_INVALID = 1,     /* an argument is out of range or inconsistent          */
+    PPCA_ERR_OOM = 2,         /* workspace allocation failed or exceeds the set limit  */
+    PPCA_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed           */
+    PPCA_ERR_STATE = 4,       /* call out of order (e.g. finalize before prime)        */
+    PPCA_ERR_NUMERICAL = 5,   /* device reported a breakdown (see ppca_sync)           */
+    PPCA_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (see ppca_sync)    */
+    PPCA_ERR_UNSUPPORTED = 7  /* valid request this build does not implement           */
+} ppca_status;
+
+/* Storage type of X. */
+typedef enum ppca_dtype {
+    PPCA_F32 = 0,             /* IEEE binary32                                          */
+    PPCA_BF16 = 1,            /* bfloat16                                               */
+    PPCA_FP8_E4M3 = 2         /* OCP FP8 E4M3 codes with one FP32 scale per row:       */
+                              /*   x[r][j] = e4m3(code[r][j]) * scale[r]                */
+} ppca_dtype;
+
+/* PRIMING methods (Section 2; Section 5 for the optimiser). */
+typedef enum ppca_method {
+    PPCA_POWER = 0,           /* simultaneous (block) power iteration, Section 2.1     */
+    PPCA_OJA = 1,             /* generalised Oja / Sanger rule, Section 2.2            */
+    PPCA_EIGENGAME = 2        /* EigenGame utilities (Section 2.3, Eqs. 1-3), SGD with */
+                              /* Nesterov momentum (Section 5), parallel players        */
+} ppca_method;
+
+/* Arithmetic of the X-streaming products (tensor cores, FP32 accumulation). */
+typedef enum ppca_precision {
+    PPCA_PREC_AUTO = 0,       /* prime: FAST; finalize: ACCURATE                        */
+    PPCA_PREC_FAST = 1,       /* one product in the storage type (BF16 / FP8 / TF32)    */
+    PPCA_PREC_ACCURATE = 2    /* split precision: the FP32 operand is split into BF16   */
+                              /* (or TF32) pieces, about FP32 accuracy (BF16x3, 3xTF32) */
+} ppca_precision;
+
+typedef struct ppca_handle ppca_handle;
+
+/* Parameters of ppca_prime.  Zero-initialise, then call
+ * ppca_prime_params_default() to get the defaults of a method. */
+typedef struct ppca_prime_params {
+    const float *V0;          /* device, d x m column-major starting basis; NULL: the  */
+                              /* library draws a Gaussian d x m basis from `seed`.      */
+                              /* Either way the first basis is orth(V0).                */
+    uint64_t seed;            /* seed of the library's own initial basis               */
+    int64_t batch;            /* Oja / EigenGame minibatch rows (> 0)                   */
+    double lr;                /* Oja: step t uses lr / (t + lr_offset);                 */
+    double lr_offset;         /* EigenGame: constant lr (lr_offset ignored)             */
+    double momentum;          /* EigenGame Nesterov momentum                            */
+    int64_t t0;               /* step counter of the first step (for resume)            */
+    int32_t precision;        /* ppca_precision of the priming passes                   */
+    int32_t reserved;         /* must be 0                                              */
+} ppca_prime_params;
+
+/* Library version, (major << 16) | minor. */
+PPCA_API int32_t ppca_version(void);
+
+/* Message for the last non-OK status returned to the calling thread. */
+PPCA_API const char *ppca_last_error(void);
+
+/* Defaults: POWER -- nothing; OJA -- batch 256, lr 1, lr_offset 100 (so step t
+ * uses 1/(t+100)); EIGENGAME -- batch 1024, lr 0.05, momentum 0.9.  Sets every
+ * other field to zero / NULL.  Returns PPCA_ERR_INVALID for a NULL p or an
+ * unknown method. */
+PPCA_API ppca_status ppca_prime_params_default(ppca_prime_params *p, ppca_method method);
+
+/*
+ * Create a handle over the data set X (Algorithm 1, Input).
+ *   X           device, n x d row-major, leading dimension ld (>= d) elements,
+ *               type dtype; borrowed, must stay valid until ppca_destroy.
+ *   row_scales  device, n FP32 per-row scales; required for PPCA_FP8_E4M3,
+ *               must be NULL otherwise.
+ *   stream      cudaStream_t (as void*) every call of this handle enqueues on.
+ * Requires n >= 2, d >= 1, ld >= d, 16-byte aligned X and row pitch.
+ * No device work is enqueued.  On error *out is set to NULL.
+ */
+PPCA_API ppca_status ppca_create(ppca_handle **out, const void *X, int64_t n, int64_t d, int64_t ld,
+                        ppca_dtype dtype, const float *row_scales, void *stream);
+
+/*
+ * Optional second copy of the same data in a wider type (e.g. BF16 when X is
+ * FP8) that ppca_finalize reads instead of X.  Same shape n x d; borrowed.
+ * Pass NULL to remove it.
+ */
+PPCA_API ppca_status ppca_set_refine(ppca_handle *h, const void *X_refine, int64_t ld, ppca_dtype dtype);
+
+/* Cap the handle's workspace (bytes, 0 = no cap); exceeding it gives PPCA_ERR_OOM. */
+PPCA_API ppca_status ppca_set_workspace_limit(ppca_handle *h, int64_t bytes);
+
+/*
+ * PRIMING (Algorithm 1, step 1): compute m = k + l approximate directions.
+ *   POWER      T iterations of V <- orth(X^T X V) (Section 2.1, simultaneous
+ *              iteration), orth = thin QR with positive diagonal by CholeskyQR2.
+ *   OJA        T minibatch steps of the Sanger rule (Section 2.2), averaged over
+ *              the batch: W += lr_t / |b| (X_b^T Y - W triu(Y^T Y)), Y = X_b W.
+ *   EIGENGAME  T minibatch steps; every player ascends its utility (Eq. 3)
+ *              with M_b = X_b^T X_b / |b|, gradient projected on the sphere's
+ *              tangent space, Nesterov momentum, then renormalised.
+ * Minibatch t covers rows [j b, min((j+1) b, n)), j = t mod ceil(n / b).
+ * Requires 1 <= m <= min(d, n - 1, 128) and T >= 0.  p may be NULL (defaults).
+ * Resets the handle's priming state (basis, step counter, momentum).
+ */
+PPCA_API ppca_status ppca_prime(ppca_handle *h, ppca_method method, int32_t m, int64_t T,
+                       const ppca_prime_params *p);
+
+/*
+ * Continue the current priming run for T more steps / iterations (same method
+ * and parameters), so that pPCA can be evaluated along the priming trajectory.
+ */
+PPCA_API ppca_status ppca_prime_continue(ppca_handle *h, int64_t T);
+
+/*
+ * pPCA step (Algorithm 1, steps 2-5): Q = orth(V); one pass over X gives the
+ * m x m matrix G = (X Q)^T (X Q); G = U diag(w) U^T by Jacobi; E = Q U[:, :k].
+ *   k       1 <= k <= m (m of the last ppca_prime)
+ *   E       device, d x k column-major FP32 output (unit eigenvectors, signed)
+ *   lambda  device, k FP64 output: w[:k] / n, descending
+ * Does not change the priming state: it can be called at any point of a run.
+ * Returns PPCA_ERR_STATE if ppca_prime was never called.
+ */
+PPCA_API ppca_status ppca_finalize(ppca_handle *h, int32_t k, float *E, double *lambda,
+                          ppca_precision precision);
+
+/* Device copy of the current primed basis V (d x m column-major FP32). */
+PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
+
+/* Wait for the handle's stream; return the first device-side error, if any,
+ * and clear it. */
+PPCA_API ppca_status ppca_sync(ppca_handle *h);
+
+/* Device-time accounting of the X-passes (the hot step), for measurement. */
+typedef struct ppca_timing {
+    double pass_ms[3];        /* summed device time of the X-passes since the reset,     */
+                              /* indexed by the pass's ppca_precision (FAST, ACCURATE)    */
+    int64_t passes[3];        /* X-passes timed, by precision                              */
+    int64_t pass_rows[3];     /* rows of X those passes streamed, by precision             */
+    int64_t launches;         /* kernels the library launched (all handles) since the reset */
+} ppca_timing;
+
+/* enable != 0: record a CUDA event pair around every X-pass of this handle,
+ * on its stream, and reset the counters; enable == 0: stop recording. */
+PPCA_API ppca_status ppca_set_timing(ppca_handle *h, int32_t enable);
+
+/* Synchronise the handle's stream and report the counters since the reset. */
+PPCA_API ppca_status ppca_get_timing(ppca_handle *h, ppca_timing *out);
+
+/*
+ * Checkpoint of the priming state (basis, momentum, step counter, method and
+ * parameters) to host memory.  With buf == NULL, *bytes receives the size
+ * needed.  ppca_set_state restores it into a handle over the same (n, d).
+ * Synchronises the handle's stream.
+ */
+PPCA_API ppca_status ppca_get_state(ppca_handle *h, void *buf, int64_t *bytes);
+PPCA_API ppca_status ppca_set_state(ppca_handle *h, const void *buf, int64_t bytes);
+
+/* Free the handle and its workspace (after the stream's work completes). */
+PPCA_API ppca_status ppca_destroy(ppca_handle *h);
+
+/* ---------------------------------------------------------------------------
+ * Individual steps of the hot path.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * One fused X-pass (the product X^T X V of Sections 2.1-2.3, restricted to rows
+ * [r0, r1)):  Y = X[r0:r1] V,  Z = X[r0:r1]^T Y.
+ *   V  device, d x m column-major FP32 input (1 <= m <= 128)
+ *   Z  device, d x m column-major FP32 output
+ * Requires 0 <= r0 < r1 <= n.
+ */
+PPCA_API ppca_status ppca_xpass(ppca_handle *h, const float *V, int32_t m, int64_t r0, int64_t r1,
+                       float *Z, ppca_precision precision);
+
+/*
+ * Orthonormalise the columns of V (d x m column-major, device) into Q (may
+ * alias V): thin QR with positive diagonal by CholeskyQR2 -- G = V^T V in FP64,
+ * G = R^T R (Cholesky, FP64), V <- V R^-1, twice.  A non-positive pivot
+ * (rank-deficient V) is reported as PPCA_ERR_NUMERICAL by ppca_sync.
+ */
+PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *Q, int32_t m);
+
+/*
+ * Symmetric eigensolve of an m x m FP64 matrix (the full-PCA of step 4):
+ * G (device, m x m, symmetric) -> w (device, m, descending) and U (device,
+ * m x m column-major, column j = unit eigenvector of w[j], sign convention as
+ * above).  1 <= m <= 128.  G is not modified.
+ */
+PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, double *w, double *U);
+
+/*
+ * Data-format step: quantise FP32 rows (device, n x d, leading dimension ld_in)
+ * to BF16 (round to nearest even) or to FP8 E4M3 with one scale per row,
+ *   scale[r] = max_j |x[r][j]| / 448 (1 for an all-zero row),
+ *   code[r][j] = E4M3_RNE(x[r][j] / scale[r])  (both divisions in FP32).
+ * Outputs are device arrays with leading dimension ld_out.  stream as above.
+ */
+PPCA_API ppca_status ppca_quantize_bf16(const float *X, int64_t n, int64_t d, int64_t ld_in,
+                               uint16_t *out, int64_t ld_out, void *stream);
+PPCA_API ppca_status ppca_quantize_fp8(const float *X, int64_t n, int64_t d, int64_t ld_in,
+                              uint8_t *out, int64_t ld_out, float *scales, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PPCA_H */

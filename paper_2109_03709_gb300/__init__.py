@@ -1,0 +1,303 @@
+"""Python binding of the GB300 primed-PCA library (``include/ppca.h``).
+
+Argument marshalling only: every function has the name of its C entry point,
+turns torch tensors into device pointers and sizes, calls the shared library
+and raises ``PPCAError`` on a non-OK status.  All arithmetic runs in the CUDA
+kernels of ``libppca_gb300.so``; there is no CPU path.  If the library has not
+been built, importing works but the first call raises.
+
+Layouts (as in the header): X is n x d row-major; bases and eigenvectors are
+d x m column-major FP32, i.e. torch tensors of shape (m, d) whose row j is
+direction j (``V.T`` is the d x m matrix).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "PPCAError", "load_library", "library_path",
+    "PPCA_OK", "PPCA_F32", "PPCA_BF16", "PPCA_FP8_E4M3", "PPCA_POWER", "PPCA_OJA", "PPCA_EIGENGAME",
+    "PPCA_PREC_AUTO", "PPCA_PREC_FAST", "PPCA_PREC_ACCURATE", "ppca_prime_params",
+    "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
+    "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
+    "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
+    "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
+    "ppca_timing", "EXPORTED_SYMBOLS",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "_lib", "libppca_gb300.so")
+
+PPCA_OK = 0
+PPCA_F32, PPCA_BF16, PPCA_FP8_E4M3 = 0, 1, 2
+PPCA_POWER, PPCA_OJA, PPCA_EIGENGAME = 0, 1, 2
+PPCA_PREC_AUTO, PPCA_PREC_FAST, PPCA_PREC_ACCURATE = 0, 1, 2
+
+_STATUS = {0: "PPCA_OK", 1: "PPCA_ERR_INVALID", 2: "PPCA_ERR_OOM", 3: "PPCA_ERR_CUDA", 4: "PPCA_ERR_STATE",
+           5: "PPCA_ERR_NUMERICAL", 6: "PPCA_ERR_TIMEOUT", 7: "PPCA_ERR_UNSUPPORTED"}
+
+EXPORTED_SYMBOLS = [
+    "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
+    "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
+    "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
+    "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
+]
+
+
+class PPCAError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        self.status = status
+        self.status_name = _STATUS.get(status, str(status))
+        super().__init__(f"{func}: {self.status_name}: {message}")
+
+
+class ppca_prime_params(ctypes.Structure):
+    _fields_ = [
+        ("V0", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64),
+        ("batch", ctypes.c_int64),
+        ("lr", ctypes.c_double),
+        ("lr_offset", ctypes.c_double),
+        ("momentum", ctypes.c_double),
+        ("t0", ctypes.c_int64),
+        ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class ppca_timing(ctypes.Structure):
+    _fields_ = [
+        ("pass_ms", ctypes.c_double * 3),
+        ("passes", ctypes.c_int64 * 3),
+        ("pass_rows", ctypes.c_int64 * 3),
+        ("launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_c_status = ctypes.c_int
+_vp, _i64, _i32, _dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+
+_SIGS = {
+    "ppca_version": (_i32, []),
+    "ppca_last_error": (ctypes.c_char_p, []),
+    "ppca_prime_params_default": (_c_status, [ctypes.POINTER(ppca_prime_params), ctypes.c_int]),
+    "ppca_create": (_c_status, [ctypes.POINTER(_vp), _vp, _i64, _i64, _i64, ctypes.c_int, _vp, _vp]),
+    "ppca_set_refine": (_c_status, [_vp, _vp, _i64, ctypes.c_int]),
+    "ppca_set_workspace_limit": (_c_status, [_vp, _i64]),
+    "ppca_prime": (_c_status, [_vp, ctypes.c_int, _i32, _i64, ctypes.POINTER(ppca_prime_params)]),
+    "ppca_prime_continue": (_c_status, [_vp, _i64]),
+    "ppca_finalize": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int]),
+    "ppca_get_basis": (_c_status, [_vp, _vp]),
+    "ppca_sync": (_c_status, [_vp]),
+    "ppca_get_state": (_c_status, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "ppca_set_state": (_c_status, [_vp, _vp, _i64]),
+    "ppca_destroy": (_c_status, [_vp]),
+    "ppca_xpass": (_c_status, [_vp, _vp, _i32, _i64, _i64, _vp, ctypes.c_int]),
+    "ppca_orthonormalize": (_c_status, [_vp, _vp, _vp, _i32]),
+    "ppca_eigh": (_c_status, [_vp, _vp, _i32, _vp, _vp]),
+    "ppca_quantize_bf16": (_c_status, [_vp, _i64, _i64, _i64, _vp, _i64, _vp]),
+    "ppca_quantize_fp8": (_c_status, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
+    "ppca_set_timing": (_c_status, [_vp, _i32]),
+    "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
+}
+
+
+def library_path() -> str:
+    return _LIBPATH
+
+
+def load_library(path: str | None = None):
+    """Load libppca_gb300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or _LIBPATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"the pPCA CUDA library is not built ({p} missing); "
+                               "run `python -m paper_2109_03709_gb300.build`")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, func: str):
+    if status != PPCA_OK:
+        msg = load_library().ppca_last_error()
+        raise PPCAError(status, func, msg.decode() if msg else "")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float32:
+        return PPCA_F32
+    if t.dtype == torch.bfloat16:
+        return PPCA_BF16
+    if t.dtype == torch.uint8 or (hasattr(torch, "float8_e4m3fn") and t.dtype == torch.float8_e4m3fn):
+        return PPCA_FP8_E4M3
+    raise TypeError(f"unsupported X dtype {t.dtype}")
+
+
+class Handle:
+    """Owns a ppca_handle* and keeps the borrowed tensors alive."""
+
+    def __init__(self, ptr: int, keep: list):
+        self.ptr = ptr
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                load_library().ppca_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- C ABI mirror
+
+def ppca_version() -> int:
+    return load_library().ppca_version()
+
+
+def ppca_last_error() -> str:
+    return load_library().ppca_last_error().decode()
+
+
+def ppca_prime_params_default(method: int) -> ppca_prime_params:
+    p = ppca_prime_params()
+    _check(load_library().ppca_prime_params_default(ctypes.byref(p), method), "ppca_prime_params_default")
+    return p
+
+
+def ppca_create(X, row_scales=None, stream=None, *, n=None, d=None, ld=None, dtype=None) -> Handle:
+    """Create a handle over X (a 2-D CUDA tensor, row-major; strides give ld)."""
+    lib = load_library()
+    if n is None:
+        n, d = X.shape
+        ld = X.stride(0)
+        if X.stride(1) != 1:
+            raise ValueError("X must be row-major (unit column stride)")
+        dtype = _dtype_code(X)
+    out = ctypes.c_void_p()
+    _check(lib.ppca_create(ctypes.byref(out), _ptr(X), n, d, ld, dtype, _ptr(row_scales), _stream_ptr(stream)),
+           "ppca_create")
+    return Handle(out.value, [X, row_scales])
+
+
+def ppca_set_refine(h: Handle, X_refine, ld=None, dtype=None):
+    if X_refine is None:
+        _check(load_library().ppca_set_refine(h.ptr, None, 0, 0), "ppca_set_refine")
+        return
+    ld = X_refine.stride(0) if ld is None else ld
+    dtype = _dtype_code(X_refine) if dtype is None else dtype
+    _check(load_library().ppca_set_refine(h.ptr, _ptr(X_refine), ld, dtype), "ppca_set_refine")
+    h._keep.append(X_refine)
+
+
+def ppca_set_workspace_limit(h: Handle, nbytes: int):
+    _check(load_library().ppca_set_workspace_limit(h.ptr, nbytes), "ppca_set_workspace_limit")
+
+
+def ppca_prime(h: Handle, method: int, m: int, T: int, params: ppca_prime_params | None = None, V0=None):
+    if params is None:
+        params = ppca_prime_params_default(method)
+    if V0 is not None:
+        params.V0 = _ptr(V0)
+    _check(load_library().ppca_prime(h.ptr, method, m, T, ctypes.byref(params)), "ppca_prime")
+
+
+def ppca_prime_continue(h: Handle, T: int):
+    _check(load_library().ppca_prime_continue(h.ptr, T), "ppca_prime_continue")
+
+
+def ppca_finalize(h: Handle, k: int, E, lam, precision: int = PPCA_PREC_AUTO):
+    _check(load_library().ppca_finalize(h.ptr, k, _ptr(E), _ptr(lam), precision), "ppca_finalize")
+
+
+def ppca_get_basis(h: Handle, V_out):
+    _check(load_library().ppca_get_basis(h.ptr, _ptr(V_out)), "ppca_get_basis")
+
+
+def ppca_sync(h: Handle):
+    _check(load_library().ppca_sync(h.ptr), "ppca_sync")
+
+
+def ppca_get_state(h: Handle) -> bytes:
+    lib = load_library()
+    nbytes = ctypes.c_int64(0)
+    _check(lib.ppca_get_state(h.ptr, None, ctypes.byref(nbytes)), "ppca_get_state")
+    buf = ctypes.create_string_buffer(nbytes.value)
+    _check(lib.ppca_get_state(h.ptr, buf, ctypes.byref(nbytes)), "ppca_get_state")
+    return buf.raw[:nbytes.value]
+
+
+def ppca_set_state(h: Handle, state: bytes):
+    buf = ctypes.create_string_buffer(state, len(state))
+    _check(load_library().ppca_set_state(h.ptr, buf, len(state)), "ppca_set_state")
+
+
+def ppca_destroy(h: Handle):
+    if h.ptr:
+        _check(load_library().ppca_destroy(h.ptr), "ppca_destroy")
+        h.ptr = None
+
+
+def ppca_xpass(h: Handle, V, m: int, r0: int, r1: int, Z, precision: int = PPCA_PREC_AUTO):
+    _check(load_library().ppca_xpass(h.ptr, _ptr(V), m, r0, r1, _ptr(Z), precision), "ppca_xpass")
+
+
+def ppca_orthonormalize(h: Handle, V, Q, m: int):
+    _check(load_library().ppca_orthonormalize(h.ptr, _ptr(V), _ptr(Q), m), "ppca_orthonormalize")
+
+
+def ppca_eigh(h: Handle, G, m: int, w, U):
+    _check(load_library().ppca_eigh(h.ptr, _ptr(G), m, _ptr(w), _ptr(U)), "ppca_eigh")
+
+
+def ppca_quantize_bf16(X, out, stream=None):
+    n, d = X.shape
+    _check(load_library().ppca_quantize_bf16(_ptr(X), n, d, X.stride(0), _ptr(out), out.stride(0),
+                                             _stream_ptr(stream)), "ppca_quantize_bf16")
+
+
+def ppca_quantize_fp8(X, out, scales, stream=None):
+    n, d = X.shape
+    _check(load_library().ppca_quantize_fp8(_ptr(X), n, d, X.stride(0), _ptr(out), out.stride(0), _ptr(scales),
+                                            _stream_ptr(stream)), "ppca_quantize_fp8")
+
+
+def ppca_set_timing(h: Handle, enable: bool = True):
+    _check(load_library().ppca_set_timing(h.ptr, 1 if enable else 0), "ppca_set_timing")
+
+
+def ppca_get_timing(h: Handle) -> ppca_timing:
+    t = ppca_timing()
+    _check(load_library().ppca_get_timing(h.ptr, ctypes.byref(t)), "ppca_get_timing")
+    return t

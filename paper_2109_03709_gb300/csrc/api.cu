@@ -1,0 +1,602 @@
+// api.cu -- the C ABI of include/ppca.h: handle, validation, orchestration.
+//
+// Algorithm 1 (primed PCA) maps onto the calls as follows:
+//   step 1 PRIMING            ppca_prime / ppca_prime_continue
+//   steps 2-5 span, project,  ppca_finalize: Q = orth(V); Z = X^T X Q (one pass);
+//   full-PCA, return          G = Q^T Z; G = U diag(w) U^T; E = Q U[:, :k]
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "kernels.h"
+#include "pass_tc.h"
+
+using namespace ppca;
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void ppca::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t ppca::launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_last_error;
+
+ppca_status fail(ppca_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CUDA_TRY(expr)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e__ = (expr);                                                                        \
+        if (e__ != cudaSuccess) return fail(PPCA_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e__), \
+                                            __FILE__, __LINE__);                                         \
+    } while (0)
+
+#define PPCA_TRY(expr)                        \
+    do {                                      \
+        ppca_status s__ = (expr);             \
+        if (s__ != PPCA_OK) return s__;       \
+    } while (0)
+
+size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+int dtype_size(ppca_dtype t) { return t == PPCA_F32 ? 4 : (t == PPCA_BF16 ? 2 : 1); }
+
+}  // namespace
+
+struct ppca_handle {
+    XView x;                  // data used by the priming passes
+    XView xref;               // optional finalize copy
+    bool has_ref = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    int64_t ws_limit = 0;
+
+    // workspace (sized for ws_m, ws_rows)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_m = 0;
+    int* status = nullptr;    // device status word (own allocation)
+
+    float* V = nullptr;       // primed basis d x m
+    float* Z = nullptr;       // pass output d x m
+    float* Q = nullptr;       // orthonormal basis d x m (finalize)
+    float* T = nullptr;       // temporary d x m
+    float* buf = nullptr;     // EigenGame momentum d x m
+    double* G = nullptr;      // m x m
+    float* Rf = nullptr;      // m x m
+    double* w = nullptr;      // m
+    double* U = nullptr;      // m x m
+    float* gram_part = nullptr;
+    void* jac = nullptr;
+    double* eg = nullptr;
+    SimtPassScratch simt;
+    TcPassScratch tc;
+
+    // priming state
+    int method = -1;
+    int m = 0;
+    int64_t t = 0;            // next minibatch step
+    int64_t iters = 0;        // power iterations done
+    ppca_prime_params params{};
+
+    // measurement
+    bool timing = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
+    std::vector<int> event_prec;
+    size_t events_used = 0;
+    int64_t timed_passes[3] = {0, 0, 0}, timed_rows[3] = {0, 0, 0}, launch_base = 0;
+};
+
+namespace {
+
+ppca_status ensure_workspace(ppca_handle* h, int m) {
+    if (h->ws && h->ws_m >= m) return PPCA_OK;
+    const int64_t d = h->x.d, n = h->x.n;
+    const size_t dm = al256((size_t)d * m * sizeof(float));
+    const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
+    size_t need = 5 * dm + al256((size_t)m * m * 8) + al256((size_t)m * m * 4) + al256((size_t)m * 8) +
+                  al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
+                  al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
+                  al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
+    if (h->ws_limit > 0 && (int64_t)need > h->ws_limit)
+        return fail(PPCA_ERR_OOM, "workspace of %zu bytes exceeds the limit of %lld bytes", need,
+                    (long long)h->ws_limit);
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->ws);
+        h->ws = nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PPCA_ERR_OOM, "cudaMalloc(%zu) failed: %s", need, cudaGetErrorString(e));
+    }
+    h->ws = p;
+    h->ws_bytes = need;
+    h->ws_m = m;
+    char* c = static_cast<char*>(p);
+    auto take = [&](size_t b) { char* r = c; c += al256(b); return r; };
+    h->V = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->Z = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->Q = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->T = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->buf = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->G = reinterpret_cast<double*>(take((size_t)m * m * 8));
+    h->Rf = reinterpret_cast<float*>(take((size_t)m * m * 4));
+    h->w = reinterpret_cast<double*>(take((size_t)m * 8));
+    h->U = reinterpret_cast<double*>(take((size_t)m * m * 8));
+    h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
+    h->jac = take(jacobi_scratch_bytes(m));
+    h->eg = reinterpret_cast<double*>(take(eigengame_scratch_bytes(d, m)));
+    h->simt.nsplit = nsplit;
+    h->simt.Y = reinterpret_cast<float*>(take(simt_pass_scratch_floats(n, d, m, nsplit) * 4));
+    h->simt.Zpart = h->simt.Y + (size_t)n * m;
+    h->tc = tc_pass_scratch_carve(take(tc_pass_scratch_bytes(n, d, m, h->num_sms)), n, d, m, h->num_sms);
+    return PPCA_OK;
+}
+
+ppca_status validate_x(const void* X, int64_t n, int64_t d, int64_t ld, ppca_dtype dt, const float* scales) {
+    if (!X) return fail(PPCA_ERR_INVALID, "X is NULL");
+    if (n < 2) return fail(PPCA_ERR_INVALID, "n = %lld: need at least 2 points", (long long)n);
+    if (d < 1) return fail(PPCA_ERR_INVALID, "d = %lld: need d >= 1", (long long)d);
+    if (ld < d) return fail(PPCA_ERR_INVALID, "ld = %lld < d = %lld", (long long)ld, (long long)d);
+    if (dt != PPCA_F32 && dt != PPCA_BF16 && dt != PPCA_FP8_E4M3) return fail(PPCA_ERR_INVALID, "unknown dtype %d", (int)dt);
+    if ((dt == PPCA_FP8_E4M3) != (scales != nullptr))
+        return fail(PPCA_ERR_INVALID, "row_scales must be given for FP8 data and only for FP8 data");
+    if (reinterpret_cast<uintptr_t>(X) % 16 != 0) return fail(PPCA_ERR_INVALID, "X is not 16-byte aligned");
+    if ((ld * dtype_size(dt)) % 16 != 0)
+        return fail(PPCA_ERR_INVALID, "row pitch ld * sizeof = %lld bytes is not a multiple of 16",
+                    (long long)(ld * dtype_size(dt)));
+    return PPCA_OK;
+}
+
+// One X-pass over rows [r0, r1) of view x: Z = X^T X V.
+ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
+                      ppca_precision prec) {
+    cudaEvent_t ev_end = nullptr;
+    if (h->timing) {
+        if (h->events_used == h->events.size()) {
+            cudaEvent_t a, b;
+            CUDA_TRY(cudaEventCreate(&a));
+            CUDA_TRY(cudaEventCreate(&b));
+            h->events.emplace_back(a, b);
+            h->event_prec.push_back(0);
+        }
+        h->event_prec[h->events_used] = (int)prec;
+        auto& pr = h->events[h->events_used++];
+        CUDA_TRY(cudaEventRecord(pr.first, h->stream));
+        ev_end = pr.second;
+        ++h->timed_passes[(int)prec];
+        h->timed_rows[(int)prec] += r1 - r0;
+    }
+    if (tc_pass_supported(x, m)) {
+        CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->status, h->num_sms, h->stream));
+    } else {
+        CUDA_TRY(xpass_simt(x, V, m, r0, r1, Z, h->simt, h->stream));
+    }
+    if (ev_end) CUDA_TRY(cudaEventRecord(ev_end, h->stream));
+    return PPCA_OK;
+}
+
+// CholeskyQR2: Q = orth(V) with positive diagonal, Q may alias V.
+ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
+    const int64_t d = h->x.d;
+    const float* src = V;
+    for (int rep = 0; rep < 2; ++rep) {
+        CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream));
+        CUDA_TRY(cholesky(h->G, m, h->Rf, h->status, h->stream));
+        CUDA_TRY(apply_rinv(src, h->Rf, d, m, Q, h->stream));
+        src = Q;
+    }
+    return PPCA_OK;
+}
+
+void minibatch(int64_t t, int64_t n, int64_t b, int64_t& r0, int64_t& r1) {
+    const int64_t per_epoch = (n + b - 1) / b;
+    const int64_t j = t % per_epoch;
+    r0 = j * b;
+    r1 = r0 + b < n ? r0 + b : n;
+}
+
+ppca_precision prime_prec(const ppca_handle* h) {
+    const int p = h->params.precision;
+    return p == PPCA_PREC_AUTO ? PPCA_PREC_FAST : (ppca_precision)p;
+}
+
+ppca_status run_steps(ppca_handle* h, int64_t T) {
+    const int m = h->m;
+    const int64_t n = h->x.n, d = h->x.d;
+    for (int64_t i = 0; i < T; ++i) {
+        switch (h->method) {
+        case PPCA_POWER:
+            PPCA_TRY(run_xpass(h, h->x, h->V, m, 0, n, h->Z, prime_prec(h)));
+            PPCA_TRY(run_orth(h, h->Z, h->V, m));
+            ++h->iters;
+            break;
+        case PPCA_OJA: {
+            int64_t r0, r1;
+            minibatch(h->t, n, h->params.batch, r0, r1);
+            PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
+            CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // S = Y^T Y = W^T Z
+            const double lr = h->params.lr / ((double)h->t + h->params.lr_offset);
+            CUDA_TRY(oja_update(h->V, h->Z, h->G, d, m, lr / (double)(r1 - r0), h->stream));
+            ++h->t;
+            break;
+        }
+        case PPCA_EIGENGAME: {
+            int64_t r0, r1;
+            minibatch(h->t, n, h->params.batch, r0, r1);
+            PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
+            CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // C = V^T Z
+            CUDA_TRY(eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)(r1 - r0), h->params.lr,
+                                      h->params.momentum, h->eg, h->stream));
+            ++h->t;
+            break;
+        }
+        default:
+            return fail(PPCA_ERR_STATE, "no priming method set");
+        }
+    }
+    return PPCA_OK;
+}
+
+constexpr uint32_t kStateMagic = 0x50504341u;   // "PPCA"
+
+struct StateHeader {
+    uint32_t magic;
+    int32_t version;
+    int64_t n, d;
+    int32_t method, m;
+    int64_t t, iters;
+    ppca_prime_params params;
+};
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+int32_t ppca_version(void) { return (1 << 16) | 0; }
+
+const char* ppca_last_error(void) { return g_last_error.c_str(); }
+
+ppca_status ppca_prime_params_default(ppca_prime_params* p, ppca_method method) {
+    if (!p) return fail(PPCA_ERR_INVALID, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    switch (method) {
+    case PPCA_POWER:
+        break;
+    case PPCA_OJA:
+        p->batch = 256;
+        p->lr = 1.0;
+        p->lr_offset = 100.0;
+        break;
+    case PPCA_EIGENGAME:
+        p->batch = 1024;
+        p->lr = 0.05;
+        p->momentum = 0.9;
+        break;
+    default:
+        return fail(PPCA_ERR_INVALID, "unknown method %d", (int)method);
+    }
+    return PPCA_OK;
+}
+
+ppca_status ppca_create(ppca_handle** out, const void* X, int64_t n, int64_t d, int64_t ld, ppca_dtype dtype,
+                        const float* row_scales, void* stream) {
+    if (!out) return fail(PPCA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    PPCA_TRY(validate_x(X, n, d, ld, dtype, row_scales));
+    ppca_handle* h = new (std::nothrow) ppca_handle();
+    if (!h) return fail(PPCA_ERR_OOM, "host allocation failed");
+    h->x.ptr = X;
+    h->x.n = n;
+    h->x.d = d;
+    h->x.ld = ld;
+    h->x.dtype = dtype;
+    h->x.scales = row_scales;
+    h->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&h->status), 256);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, 256, h->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->status) cudaFree(h->status);
+        delete h;
+        return fail(PPCA_ERR_CUDA, "device setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_refine(ppca_handle* h, const void* X_refine, int64_t ld, ppca_dtype dtype) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (!X_refine) {
+        h->has_ref = false;
+        return PPCA_OK;
+    }
+    if (dtype == PPCA_FP8_E4M3) return fail(PPCA_ERR_INVALID, "the refine copy must be FP32 or BF16");
+    PPCA_TRY(validate_x(X_refine, h->x.n, h->x.d, ld, dtype, nullptr));
+    h->xref = h->x;
+    h->xref.ptr = X_refine;
+    h->xref.ld = ld;
+    h->xref.dtype = dtype;
+    h->xref.scales = nullptr;
+    h->has_ref = true;
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_workspace_limit(ppca_handle* h, int64_t bytes) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (bytes < 0) return fail(PPCA_ERR_INVALID, "negative limit");
+    h->ws_limit = bytes;
+    return PPCA_OK;
+}
+
+static ppca_status check_m(const ppca_handle* h, int32_t m) {
+    const int64_t cap = std::min<int64_t>(std::min<int64_t>(h->x.d, h->x.n - 1), kMaxM);
+    if (m < 1 || m > cap)
+        return fail(PPCA_ERR_INVALID, "m = k + l = %d out of range [1, min(d, n-1, %d) = %lld]", m, kMaxM,
+                    (long long)cap);
+    return PPCA_OK;
+}
+
+ppca_status ppca_prime(ppca_handle* h, ppca_method method, int32_t m, int64_t T, const ppca_prime_params* p) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (method != PPCA_POWER && method != PPCA_OJA && method != PPCA_EIGENGAME)
+        return fail(PPCA_ERR_INVALID, "unknown method %d", (int)method);
+    PPCA_TRY(check_m(h, m));
+    if (T < 0) return fail(PPCA_ERR_INVALID, "T = %lld < 0", (long long)T);
+    ppca_prime_params prm;
+    if (p) {
+        prm = *p;
+    } else {
+        PPCA_TRY(ppca_prime_params_default(&prm, method));
+    }
+    if (prm.reserved != 0) return fail(PPCA_ERR_INVALID, "reserved field must be 0");
+    if (prm.precision < PPCA_PREC_AUTO || prm.precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", prm.precision);
+    if (method != PPCA_POWER) {
+        if (prm.batch <= 0) return fail(PPCA_ERR_INVALID, "batch = %lld must be > 0", (long long)prm.batch);
+        if (!(prm.lr > 0.0)) return fail(PPCA_ERR_INVALID, "lr must be > 0");
+        if (method == PPCA_OJA && !(prm.lr_offset + (double)prm.t0 > 0.0))
+            return fail(PPCA_ERR_INVALID, "lr_offset + t0 must be > 0");
+        if (prm.t0 < 0) return fail(PPCA_ERR_INVALID, "t0 < 0");
+    }
+    PPCA_TRY(ensure_workspace(h, m));
+    h->method = method;
+    h->m = m;
+    h->params = prm;
+    h->t = prm.t0;
+    h->iters = 0;
+    const int64_t d = h->x.d;
+    if (prm.V0) {
+        CUDA_TRY(cudaMemcpyAsync(h->V, prm.V0, (size_t)d * m * sizeof(float), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        CUDA_TRY(init_gaussian(h->V, d, m, prm.seed, h->stream));
+    }
+    CUDA_TRY(cudaMemsetAsync(h->buf, 0, (size_t)d * m * sizeof(float), h->stream));
+    PPCA_TRY(run_orth(h, h->V, h->V, m));
+    h->params.V0 = nullptr;   // not retained
+    return run_steps(h, T);
+}
+
+ppca_status ppca_prime_continue(ppca_handle* h, int64_t T) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "ppca_prime was not called");
+    if (T < 0) return fail(PPCA_ERR_INVALID, "T < 0");
+    return run_steps(h, T);
+}
+
+ppca_status ppca_finalize(ppca_handle* h, int32_t k, float* E, double* lambda, ppca_precision precision) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "finalize before prime");
+    const int m = h->m;
+    if (k < 1 || k > m) return fail(PPCA_ERR_INVALID, "k = %d out of range [1, m = %d]", k, m);
+    if (!E || !lambda) return fail(PPCA_ERR_INVALID, "E or lambda is NULL");
+    if (precision < PPCA_PREC_AUTO || precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", (int)precision);
+    const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_ACCURATE : precision;
+    const int64_t d = h->x.d, n = h->x.n;
+    PPCA_TRY(run_orth(h, h->V, h->Q, m));                                          // step 2: span
+    const XView& xf = h->has_ref ? h->xref : h->x;
+    PPCA_TRY(run_xpass(h, xf, h->Q, m, 0, n, h->T, prec));                         // step 3: X^T X Q
+    CUDA_TRY(gram_df(h->Q, h->T, d, m, h->G, h->gram_part, h->stream));            // G = (XQ)^T (XQ)
+    CUDA_TRY(eigh_small(h->G, m, h->w, h->U, h->jac, h->status, h->stream));       // step 4: full-PCA
+    CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)n, E, lambda, h->stream));   // step 5
+    return PPCA_OK;
+}
+
+ppca_status ppca_get_basis(const ppca_handle* h, float* V_out) {
+    if (!h || !V_out) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "no primed basis");
+    CUDA_TRY(cudaMemcpyAsync(V_out, h->V, (size_t)h->x.d * h->m * sizeof(float), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_sync(ppca_handle* h) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != kDevOk) {
+        CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)));
+        switch (st) {
+        case kDevCholeskyBreakdown:
+            return fail(PPCA_ERR_NUMERICAL, "CholeskyQR2: non-positive pivot (basis numerically rank-deficient)");
+        case kDevJacobiNoConverge:
+            return fail(PPCA_ERR_NUMERICAL, "Jacobi eigensolver did not converge within its sweep cap");
+        case kDevWaitTimeout:
+            return fail(PPCA_ERR_TIMEOUT, "a bounded device-side wait ran out");
+        default:
+            return fail(PPCA_ERR_NUMERICAL, "device status %d", st);
+        }
+    }
+    return PPCA_OK;
+}
+
+ppca_status ppca_get_state(ppca_handle* h, void* buf, int64_t* bytes) {
+    if (!h || !bytes) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "no priming state");
+    const size_t dm = (size_t)h->x.d * h->m * sizeof(float);
+    const int64_t need = (int64_t)(sizeof(StateHeader) + 2 * dm);
+    if (!buf) {
+        *bytes = need;
+        return PPCA_OK;
+    }
+    if (*bytes < need) return fail(PPCA_ERR_INVALID, "state buffer too small (%lld < %lld)", (long long)*bytes,
+                                   (long long)need);
+    StateHeader hd{};
+    hd.magic = kStateMagic;
+    hd.version = 1;
+    hd.n = h->x.n;
+    hd.d = h->x.d;
+    hd.method = h->method;
+    hd.m = h->m;
+    hd.t = h->t;
+    hd.iters = h->iters;
+    hd.params = h->params;
+    hd.params.V0 = nullptr;
+    std::memcpy(buf, &hd, sizeof hd);
+    char* p = static_cast<char*>(buf) + sizeof hd;
+    CUDA_TRY(cudaMemcpyAsync(p, h->V, dm, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + dm, h->buf, dm, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *bytes = need;
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
+    if (!h || !buf) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (bytes < (int64_t)sizeof(StateHeader)) return fail(PPCA_ERR_INVALID, "state buffer too small");
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != kStateMagic || hd.version != 1) return fail(PPCA_ERR_INVALID, "not a ppca state buffer");
+    if (hd.n != h->x.n || hd.d != h->x.d) return fail(PPCA_ERR_INVALID, "state is for another (n, d)");
+    PPCA_TRY(check_m(h, hd.m));
+    const size_t dm = (size_t)h->x.d * hd.m * sizeof(float);
+    if (bytes < (int64_t)(sizeof hd + 2 * dm)) return fail(PPCA_ERR_INVALID, "state buffer truncated");
+    PPCA_TRY(ensure_workspace(h, hd.m));
+    h->method = hd.method;
+    h->m = hd.m;
+    h->t = hd.t;
+    h->iters = hd.iters;
+    h->params = hd.params;
+    const char* p = static_cast<const char*>(buf) + sizeof hd;
+    CUDA_TRY(cudaMemcpyAsync(h->V, p, dm, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->buf, p + dm, dm, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_timing(ppca_handle* h, int32_t enable) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    h->timing = enable != 0;
+    h->events_used = 0;
+    for (int i = 0; i < 3; ++i) {
+        h->timed_passes[i] = 0;
+        h->timed_rows[i] = 0;
+    }
+    h->launch_base = launches_so_far();
+    return PPCA_OK;
+}
+
+ppca_status ppca_get_timing(ppca_handle* h, ppca_timing* out) {
+    if (!h || !out) return fail(PPCA_ERR_INVALID, "NULL argument");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double ms[3] = {0.0, 0.0, 0.0};
+    for (size_t i = 0; i < h->events_used; ++i) {
+        float e = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&e, h->events[i].first, h->events[i].second));
+        ms[h->event_prec[i]] += e;
+    }
+    for (int i = 0; i < 3; ++i) {
+        out->pass_ms[i] = ms[i];
+        out->passes[i] = h->timed_passes[i];
+        out->pass_rows[i] = h->timed_rows[i];
+    }
+    out->launches = launches_so_far() - h->launch_base;
+    return PPCA_OK;
+}
+
+ppca_status ppca_destroy(ppca_handle* h) {
+    if (!h) return PPCA_OK;
+    cudaStreamSynchronize(h->stream);
+    for (auto& pr : h->events) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    if (h->ws) cudaFree(h->ws);
+    if (h->status) cudaFree(h->status);
+    delete h;
+    return PPCA_OK;
+}
+
+ppca_status ppca_xpass(ppca_handle* h, const float* V, int32_t m, int64_t r0, int64_t r1, float* Z,
+                       ppca_precision precision) {
+    if (!h || !V || !Z) return fail(PPCA_ERR_INVALID, "NULL argument");
+    PPCA_TRY(check_m(h, m));
+    if (r0 < 0 || r1 > h->x.n || r0 >= r1)
+        return fail(PPCA_ERR_INVALID, "row range [%lld, %lld) invalid for n = %lld", (long long)r0, (long long)r1,
+                    (long long)h->x.n);
+    if (precision < PPCA_PREC_AUTO || precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", (int)precision);
+    PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
+    const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_FAST : precision;
+    return run_xpass(h, h->x, V, m, r0, r1, Z, prec);
+}
+
+ppca_status ppca_orthonormalize(ppca_handle* h, const float* V, float* Q, int32_t m) {
+    if (!h || !V || !Q) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (m < 1 || m > kMaxM || m > h->x.d) return fail(PPCA_ERR_INVALID, "m = %d out of range", m);
+    PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
+    return run_orth(h, V, Q, m);
+}
+
+ppca_status ppca_eigh(ppca_handle* h, const double* G, int32_t m, double* w, double* U) {
+    if (!h || !G || !w || !U) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (m < 1 || m > kMaxM) return fail(PPCA_ERR_INVALID, "m = %d out of range [1, %d]", m, kMaxM);
+    PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
+    CUDA_TRY(eigh_small(G, m, w, U, h->jac, h->status, h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_quantize_bf16(const float* X, int64_t n, int64_t d, int64_t ld_in, uint16_t* out, int64_t ld_out,
+                               void* stream) {
+    if (!X || !out) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (n < 0 || d < 0 || ld_in < d || ld_out < d) return fail(PPCA_ERR_INVALID, "bad shape");
+    CUDA_TRY(quantize_bf16(X, n, d, ld_in, out, ld_out, static_cast<cudaStream_t>(stream)));
+    return PPCA_OK;
+}
+
+ppca_status ppca_quantize_fp8(const float* X, int64_t n, int64_t d, int64_t ld_in, uint8_t* out, int64_t ld_out,
+                              float* scales, void* stream) {
+    if (!X || !out || !scales) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (n < 0 || d < 0 || ld_in < d || ld_out < d) return fail(PPCA_ERR_INVALID, "bad shape");
+    CUDA_TRY(quantize_fp8(X, n, d, ld_in, out, ld_out, scales, static_cast<cudaStream_t>(stream)));
+    return PPCA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,71 @@
+// common.cuh -- shared definitions of the pPCA CUDA library (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/ppca.h"
+
+namespace ppca {
+
+// Device status word codes (written by kernels, read by ppca_sync).
+enum DevStatus : int {
+    kDevOk = 0,
+    kDevCholeskyBreakdown = 1,   // non-positive pivot in CholeskyQR2
+    kDevJacobiNoConverge = 2,    // Jacobi hit its sweep cap
+    kDevWaitTimeout = 3,         // a bounded spin-wait ran out
+    kDevBadArgument = 4,         // a kernel found an argument out of range
+};
+
+constexpr int kMaxM = 128;       // largest supported m = k + l
+
+inline int ceil_div_i(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// X as the kernels see it.
+struct XView {
+    const void* ptr = nullptr;
+    int64_t n = 0, d = 0, ld = 0;
+    ppca_dtype dtype = PPCA_F32;
+    const float* scales = nullptr;   // FP8 per-row scales
+};
+
+__device__ __forceinline__ float load_x(const XView& x, int64_t r, int64_t j) {
+    switch (x.dtype) {
+    case PPCA_F32:
+        return static_cast<const float*>(x.ptr)[r * x.ld + j];
+    case PPCA_BF16:
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(x.ptr)[r * x.ld + j]);
+    default: {
+        __nv_fp8_e4m3 c;
+        c.__x = static_cast<const uint8_t*>(x.ptr)[r * x.ld + j];
+        return static_cast<float>(c) * x.scales[r];
+    }
+    }
+}
+
+// Error-free transformations for compensated ("double-float") FP32 sums.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    e = __fadd_rn(e, lo);
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+// Host-side count of kernel launches made by the library (measurement only).
+void note_launch();
+int64_t launches_so_far();
+
+}  // namespace ppca

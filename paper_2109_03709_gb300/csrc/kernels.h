@@ -1,0 +1,72 @@
+// kernels.h -- internal launchers of the pPCA CUDA library.
+//
+// Every launcher enqueues on the given stream and returns the launch error.
+// Matrices named V, Q, Z, W, E are d x m column-major FP32 (column j at
+// offset j * d).  Small m x m matrices are row-major FP64 unless noted.
+#pragma once
+
+#include "common.cuh"
+
+namespace ppca {
+
+// ---- X-pass, SIMT reference kernels (pass_simt.cu) --------------------------
+// Z = X[r0:r1]^T (X[r0:r1] V).  Ybuf: (r1 - r0) x m FP32 scratch.
+// Zpart: nsplit * d * m * 2 floats of scratch.
+struct SimtPassScratch {
+    float* Y = nullptr;
+    float* Zpart = nullptr;
+    int nsplit = 1;
+};
+size_t simt_pass_scratch_floats(int64_t rows, int64_t d, int m, int nsplit);
+int simt_pass_nsplit(int64_t rows, int64_t d, int m, int num_sms);
+cudaError_t xpass_simt(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
+                       const SimtPassScratch& s, cudaStream_t st);
+
+// ---- small dense kernels (small.cu) -------------------------------------------
+// G = A^T B in double-float accumulation, A, B d x m column-major FP32,
+// G m x m row-major FP64 (exact sum of the hi/lo pair).  part: scratch of
+// gram_part_doubles(d, m) doubles.
+size_t gram_part_floats(int64_t d, int m);
+cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part,
+                    cudaStream_t st);
+
+// Cholesky G = R^T R (FP64, one CTA); R upper, written as FP32 (Rf) and FP64 (Rd).
+cudaError_t cholesky(const double* G, int m, float* Rf, int* status, cudaStream_t st);
+// Q = V R^-1 by row-wise forward substitution (FP32); Q may alias V.
+cudaError_t apply_rinv(const float* V, const float* Rf, int64_t d, int m, float* Q, cudaStream_t st);
+
+// Symmetric eigensolve (FP32 Jacobi + FP64 Rayleigh quotients), descending.
+// G m x m FP64 row-major; w (m) FP64; U m x m column-major FP64.
+// scratch: jacobi_scratch_bytes(m).
+size_t jacobi_scratch_bytes(int m);
+cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scratch, int* status,
+                       cudaStream_t st);
+
+// E[:, j] = Q U[:, j], j < k, signed by the largest-|entry| rule; lambda = w[:k] * inv_n.
+cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, const double* w, int k,
+                            double inv_n, float* E, double* lambda, cudaStream_t st);
+
+// Oja/Sanger update: W += c (Z - W triu(S)), S = W^T Z (m x m FP64 row-major), c = lr / b.
+cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c,
+                       cudaStream_t st);
+
+// EigenGame update from Z = X_b^T X_b V and C = V^T Z (both unnormalised by b):
+// MV = Z / b, Riemannian gradient, Nesterov momentum (buf), step lr, renormalise.
+// colnorm: m doubles of scratch.
+size_t eigengame_scratch_bytes(int64_t d, int m);
+cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double* C, int64_t d, int m,
+                             double inv_b, double lr, double mu, double* colnorm, cudaStream_t st);
+
+// Gaussian d x m basis from Philox4x32-10 (counter = element index, key = seed) + Box-Muller.
+cudaError_t init_gaussian(float* V, int64_t d, int m, uint64_t seed, cudaStream_t st);
+
+// Quantisers (data-format step).
+cudaError_t quantize_bf16(const float* X, int64_t n, int64_t d, int64_t ld_in, uint16_t* out,
+                          int64_t ld_out, cudaStream_t st);
+cudaError_t quantize_fp8(const float* X, int64_t n, int64_t d, int64_t ld_in, uint8_t* out,
+                         int64_t ld_out, float* scales, cudaStream_t st);
+
+// Copy / zero helpers.
+cudaError_t copy_f32(const float* src, float* dst, int64_t count, cudaStream_t st);
+
+}  // namespace ppca

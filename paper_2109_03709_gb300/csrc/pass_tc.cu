@@ -1,0 +1,530 @@
+// pass_tc.cu -- tensor-core X-pass for BF16 data: Z = X^T (X V) on tcgen05 + TMA.
+//
+// The product X^T X V (Section 2.1's M x with M = X^T X; the minibatch sums
+// of Sections 2.2-2.3; the projection of Algorithm 1, step 3) is computed as
+//
+//   xv_tc   Y = X V     persistent over 128-row tiles of X; A = X tile
+//                       (K-major, TMA, 128B swizzle), B = V pieces (K-major),
+//                       FP32 accumulator in TMEM (double-buffered), epilogue
+//                       splits Y into S BF16 pieces written column-major (Y^T).
+//   xty_tc  Z = X^T Y   one CTA per (128-column slice of d, row group); A = the
+//                       same X tiles read MN-major, B = Y^T pieces; the FP32
+//                       accumulator lives in TMEM for a block of rows and is then
+//                       folded into a double-float partial in global memory.
+//   reduce  Z = sum over row groups of the double-float partials.
+//
+// Split precision: with S = 3, V (and Y) are split into hi + mid + lo BF16
+// pieces (24 significand bits); X is exact in BF16, so the products carry
+// FP32-level accuracy ("BF16x3").  S = 1 is the fast priming pass.
+//
+// Warp roles (192 threads): warp 0 issues TMA, warp 1 owns TMEM and issues the
+// MMAs (one thread), warps 2-5 are the epilogue (TMEM lane quarter = warp % 4).
+// Every wait is bounded by a 2 s clock; on timeout the kernel records
+// kDevWaitTimeout, drains its copies, frees TMEM and returns.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "pass_tc.h"
+#include "tc_ptx.cuh"
+
+namespace ppca {
+
+namespace {
+
+constexpr int kThreads = 192;
+constexpr int kMaxStages = 8;
+constexpr int kSmemBudget = 200 * 1024;
+constexpr int kBK = 64;                 // K extent of one stage (64 BF16 = 128 B)
+
+struct SmemHeader {
+    uint64_t full[kMaxStages];
+    uint64_t empty[kMaxStages];
+    uint64_t tfull[2];
+    uint64_t tempty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__host__ __device__ inline uint32_t tmem_cols_for(int m_pad) {
+    uint32_t need = 2u * (uint32_t)m_pad, c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+__device__ inline uint8_t* align1024(uint8_t* p) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+template <int S>
+__device__ __forceinline__ void split_store(float y, __nv_bfloat16* dst, int64_t piece_stride) {
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(y);
+    dst[0] = h1;
+    if (S >= 2) {
+        const float r1 = y - __bfloat162float(h1);
+        const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+        dst[piece_stride] = h2;
+        if (S >= 3) {
+            const float r2 = r1 - __bfloat162float(h2);
+            dst[2 * piece_stride] = __float2bfloat16_rn(r2);
+        }
+    }
+}
+
+// Common prologue: barriers, TMEM allocation.
+__device__ inline void tc_prologue(SmemHeader* hd, int stages, uint32_t tmem_cols, const CUtensorMap* m0,
+                                   const CUtensorMap* m1) {
+    const int warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) {
+            tc::mbar_init(&hd->full[i], 1);
+            tc::mbar_init(&hd->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&hd->tfull[i], 1);
+            tc::mbar_init(&hd->tempty[i], 128);
+        }
+        hd->abort = 0;
+        tc::mbar_init_fence();
+        tc::tma_prefetch(m0);
+        tc::tma_prefetch(m1);
+    }
+    if (warp == 1) tc::tmem_alloc(&hd->tmem_base, tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ inline void tc_epilogue_teardown(SmemHeader* hd, uint32_t tmem_cols) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x / 32 == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(hd->tmem_base, tmem_cols);
+    }
+}
+
+// After an abort the producer waits (briefly, bounded) for its last copies.
+__device__ inline void drain_copies(SmemHeader* hd, uint32_t issued, int stages, int* status) {
+    const uint32_t first = issued > (uint32_t)stages ? issued - (uint32_t)stages : 0u;
+    for (uint32_t it = first; it < issued; ++it)
+        tc::mbar_wait(&hd->full[it % stages], (it / stages) & 1u, status, 100000000ull);
+}
+
+// ---------------------------------------------------------------- Y = X V
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    xv_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
+                 int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 128u * 128u;
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = a_bytes + S * b_piece;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(m_pad);
+    tc_prologue(hd, stages, tmem_cols, &tmX, &tmV);
+    const uint32_t tmem = hd->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[s], stage_bytes);
+                    uint8_t* st = tiles + (size_t)s * stage_bytes;
+                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK, t * 128);
+#pragma unroll
+                    for (int p = 0; p < S; ++p)
+                        tc::tma_load_2d(st + a_bytes + p * b_piece, &tmV, &hd->full[s], k * kBK, p * m_pad);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
+            uint32_t it = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 32, 16, 1024);
+#pragma unroll
+                        for (int p = 0; p < S; ++p) {
+                            const uint64_t bdesc =
+                                tc::smem_desc_sw128(a_addr + a_bytes + p * b_piece + kk * 32, 16, 1024);
+                            tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k | kk | p) != 0);
+                        }
+                    }
+                    tc::mma_commit(&hd->empty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->tfull[b]);
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+            if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                hd->abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+            for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    split_store<S>(__uint_as_float(r[j]), Yt + (int64_t)(c0 + j) * ldy + row, (int64_t)m_pad * ldy);
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&hd->tempty[b]);
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols);
+}
+
+// ---------------------------------------------------------------- Z = X^T Y
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    xty_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
+                  int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 2u * 64u * 128u;     // two 64-row x 64-col boxes
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = a_bytes + S * b_piece;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(m_pad);
+    tc_prologue(hd, stages, tmem_cols, &tmX, &tmY);
+    const uint32_t tmem = hd->tmem_base;
+    const int ntask = Dt * Sg;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int s = task % Dt, g = task / Dt;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int k = k0; k < k1; ++k, ++it) {
+                    const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[st_i], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[st_i], stage_bytes);
+                    uint8_t* st = tiles + (size_t)st_i * stage_bytes;
+                    tc::tma_load_2d(st, &tmX, &hd->full[st_i], s * 128, k * kBK);
+                    tc::tma_load_2d(st + 8192, &tmX, &hd->full[st_i], s * 128 + 64, k * kBK);
+#pragma unroll
+                    for (int p = 0; p < S; ++p)
+                        tc::tma_load_2d(st + a_bytes + p * b_piece, &tmY, &hd->full[st_i], k * kBK, p * m_pad);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, true, false);
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int g = task / Dt;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int kb = k0; kb < k1 && ok; kb += flush, ++fb) {
+                    const int ke = kb + flush < k1 ? kb + flush : k1;
+                    const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                    if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
+                    for (int k = kb; k < ke; ++k, ++it) {
+                        const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                        if (!tc::mbar_wait(&hd->full[st_i], ph, status) || *(volatile int*)&hd->abort) {
+                            hd->abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a_addr = tc::smem_u32(tiles + (size_t)st_i * stage_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 2048, 8192, 1024);
+#pragma unroll
+                            for (int p = 0; p < S; ++p) {
+                                const uint64_t bdesc =
+                                    tc::smem_desc_sw128(a_addr + a_bytes + p * b_piece + kk * 32, 16, 1024);
+                                tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k != kb) || kk != 0 || p != 0);
+                            }
+                        }
+                        tc::mma_commit(&hd->empty[st_i]);
+                    }
+                    if (ok) tc::mma_commit(&hd->tfull[b]);
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t fb = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            const int s = task % Dt, g = task / Dt;
+            const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+            const int64_t j = (int64_t)s * 128 + q * 32 + lane;
+            float* z = Zacc + (((int64_t)g * Dt * 128 + j) * m_pad) * 2;
+            for (int kb = k0; kb < k1; kb += flush, ++fb) {
+                const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+                    float2* zz = reinterpret_cast<float2*>(z) + c0;
+                    if (kb == k0) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) zz[jj] = make_float2(__uint_as_float(r[jj]), 0.f);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            float2 v = zz[jj];
+                            df_add(v.x, v.y, __uint_as_float(r[jj]));
+                            zz[jj] = v;
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols);
+}
+
+// V (d x m column-major FP32) -> S BF16 pieces, [S][m_pad][ldv], zero padded.
+template <int S>
+__global__ void split_v_kernel(const float* __restrict__ V, int64_t d, int m, int m_pad, int64_t ldv,
+                               __nv_bfloat16* __restrict__ Vp) {
+    const int64_t total = (int64_t)m_pad * ldv;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / ldv);
+        const int64_t j = e % ldv;
+        const float v = (c < m && j < d) ? V[(int64_t)c * d + j] : 0.f;
+        split_store<S>(v, Vp + e, total);
+    }
+}
+
+__global__ void zreduce_kernel(const float* __restrict__ Zacc, int Sg, int Dt, int64_t d, int m, int m_pad,
+                               float* __restrict__ Z) {
+    const int64_t total = d * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / d);
+        const int64_t j = e % d;
+        float hi = 0.f, lo = 0.f;
+        for (int g = 0; g < Sg; ++g) {
+            const float2 v = reinterpret_cast<const float2*>(Zacc)[((int64_t)g * Dt * 128 + j) * m_pad + c];
+            df_add(hi, lo, v.x);
+            df_add(hi, lo, v.y);
+        }
+        Z[e] = hi + lo;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+                    uint32_t box_inner, uint32_t box_outer) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {pitch_bytes};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int stages_for(uint32_t stage_bytes) {
+    int s = (int)((kSmemBudget - 2048) / stage_bytes);
+    return s < 2 ? 2 : (s > kMaxStages ? kMaxStages : s);
+}
+
+size_t smem_bytes(int stages, uint32_t stage_bytes) { return 1024 + (size_t)stages * stage_bytes + sizeof(SmemHeader); }
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int m_pad_of(int m) { return (int)round_up(m, 32); }
+
+struct Layout {
+    int64_t ldv, ldy, rows_pad_max;
+    int m_pad, Dt;
+    size_t vp_bytes, yt_bytes, z_bytes;
+};
+
+Layout layout_of(int64_t n, int64_t d, int m, int num_sms) {
+    Layout L;
+    L.m_pad = 128;                                   // scratch sized for the largest m
+    L.ldv = round_up(d, 8);
+    L.rows_pad_max = round_up(n, 128);
+    L.Dt = (int)((d + 127) / 128);
+    L.vp_bytes = (size_t)3 * L.m_pad * L.ldv * 2;
+    L.yt_bytes = (size_t)3 * L.m_pad * L.rows_pad_max * 2;
+    L.z_bytes = (size_t)(num_sms + L.Dt) * 128 * L.m_pad * 8;
+    (void)m;
+    return L;
+}
+
+template <int S>
+cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
+                     const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+    const int64_t d = x.d, rows = r1 - r0;
+    const int m_pad = m_pad_of(m);
+    const int64_t ldv = round_up(d, 8);
+    const int64_t ldy = round_up(rows, 128);
+    const int Dt = (int)((d + 127) / 128);
+    __nv_bfloat16* Vp = static_cast<__nv_bfloat16*>(sc.vp);
+    __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
+    float* Zacc = static_cast<float*>(sc.zacc);
+
+    // V -> BF16 pieces
+    {
+        const int64_t total = (int64_t)m_pad * ldv;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        note_launch();
+        split_v_kernel<S><<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv, Vp);
+    }
+    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * 2;
+    CUtensorMap tmXa, tmXb, tmV, tmY;
+    if (!encode_bf16_2d(&tmXa, xbase, d, rows, x.ld * 2, 64, 128) ||
+        !encode_bf16_2d(&tmXb, xbase, d, rows, x.ld * 2, 64, 64) ||
+        !encode_bf16_2d(&tmV, Vp, d, (uint64_t)S * m_pad, ldv * 2, 64, m_pad) ||
+        !encode_bf16_2d(&tmY, Yt, ldy, (uint64_t)S * m_pad, ldy * 2, 64, m_pad))
+        return cudaErrorInvalidValue;
+
+    // Y = X V
+    {
+        const uint32_t stage_bytes = 128u * 128u + S * (uint32_t)m_pad * 128u;
+        const int stages = stages_for(stage_bytes);
+        const size_t smem = smem_bytes(stages, stage_bytes);
+        cudaError_t e = cudaFuncSetAttribute(xv_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int ntiles = (int)(ldy / 128);
+        const int nk = (int)((d + kBK - 1) / kBK);
+        const int grid = ntiles < num_sms ? ntiles : num_sms;
+        note_launch();
+        xv_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXa, tmV, ntiles, nk, m_pad, stages, Yt, ldy, status);
+    }
+    // Z = X^T Y
+    int Sg;
+    {
+        const uint32_t stage_bytes = 2u * 64u * 128u + S * (uint32_t)m_pad * 128u;
+        const int stages = stages_for(stage_bytes);
+        const size_t smem = smem_bytes(stages, stage_bytes);
+        cudaError_t e = cudaFuncSetAttribute(xty_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int kst = (int)(ldy / kBK);
+        Sg = Dt >= num_sms ? 1 : num_sms / Dt;
+        if (Sg > kst) Sg = kst;
+        if (Sg < 1) Sg = 1;
+        const int ntask = Dt * Sg;
+        const int grid = ntask < num_sms ? ntask : num_sms;
+        note_launch();
+        xty_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXb, tmY, Dt, Sg, kst, flush, m_pad, stages, Zacc, status);
+    }
+    {
+        const int64_t total = d * m;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 8192) blocks = 8192;
+        note_launch();
+        zreduce_kernel<<<blocks, 256, 0, st>>>(Zacc, Sg, Dt, d, m, m_pad, Z);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms) {
+    const Layout L = layout_of(n, d, m, num_sms);
+    return L.vp_bytes + L.yt_bytes + L.z_bytes + 3 * 256;
+}
+
+TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int num_sms) {
+    const Layout L = layout_of(n, d, m, num_sms);
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    TcPassScratch s;
+    char* p = static_cast<char*>(base);
+    s.vp = p;
+    p += al(L.vp_bytes);
+    s.yt = p;
+    p += al(L.yt_bytes);
+    s.zacc = p;
+    return s;
+}
+
+bool tc_pass_supported(const XView& x, int m) {
+    return x.dtype == PPCA_BF16 && m >= 1 && m <= kMaxM && encode_fn() != nullptr;
+}
+
+cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
+                     const TcPassScratch& s, int* status, int num_sms, cudaStream_t st) {
+    if (r1 <= r0) return cudaErrorInvalidValue;
+    if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
+    return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
+}
+
+}  // namespace ppca

@@ -1,0 +1,20 @@
+// pass_tc.h -- tensor-core (tcgen05 + TMA) X-pass for BF16 data (internal).
+#pragma once
+
+#include "common.cuh"
+
+namespace ppca {
+
+struct TcPassScratch {
+    void* vp = nullptr;     // V pieces, [3][128][round_up(d, 8)] BF16
+    void* yt = nullptr;     // Y^T pieces, [3][128][round_up(n, 128)] BF16
+    void* zacc = nullptr;   // double-float Z partials, [row group][d slice * 128][128] x 2 FP32
+};
+
+size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms);
+TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int num_sms);
+bool tc_pass_supported(const XView& x, int m);
+cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
+                     const TcPassScratch& s, int* status, int num_sms, cudaStream_t st);
+
+}  // namespace ppca

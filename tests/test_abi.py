@@ -1,0 +1,73 @@
+"""The C-ABI library loads and exports every entry point include/ppca.h declares.
+
+Runs without a GPU: only calls that the library answers from argument checks
+alone (before any CUDA call) are made here.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ppca.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2109_03709_gb300 import build as b
+    b.build()
+    import paper_2109_03709_gb300 as P
+    return P.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^PPCA_API\s+[\w\s\*]*?\b(ppca_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_expected_entry_points():
+    import paper_2109_03709_gb300 as P
+    assert declared_functions() == sorted(P.EXPORTED_SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults(lib):
+    import paper_2109_03709_gb300 as P
+    assert P.ppca_version() >> 16 == 1
+    oja = P.ppca_prime_params_default(P.PPCA_OJA)
+    assert oja.batch == 256 and oja.lr == 1.0 and oja.lr_offset == 100.0
+    eg = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
+    assert eg.batch == 1024 and eg.momentum == 0.9
+    with pytest.raises(P.PPCAError) as ei:
+        P.ppca_prime_params_default(7)
+    assert ei.value.status_name == "PPCA_ERR_INVALID"
+
+
+def test_argument_checks_need_no_device(lib):
+    import paper_2109_03709_gb300 as P
+    out = ctypes.c_void_p(123)
+    # NULL X
+    assert lib.ppca_create(ctypes.byref(out), None, 10, 4, 4, P.PPCA_F32, None, None) == 1
+    assert out.value is None
+    assert "NULL" in P.ppca_last_error()
+    fake = 1 << 20   # any 16-byte aligned address: rejected before it is touched
+    assert lib.ppca_create(ctypes.byref(out), fake, 1, 4, 4, P.PPCA_F32, None, None) == 1       # n < 2
+    assert lib.ppca_create(ctypes.byref(out), fake, 10, 4, 3, P.PPCA_F32, None, None) == 1      # ld < d
+    assert lib.ppca_create(ctypes.byref(out), fake, 10, 3, 3, P.PPCA_F32, None, None) == 1      # 12-byte pitch
+    assert lib.ppca_create(ctypes.byref(out), fake + 4, 10, 4, 4, P.PPCA_F32, None, None) == 1  # misaligned
+    assert lib.ppca_create(ctypes.byref(out), fake, 10, 16, 16, P.PPCA_FP8_E4M3, None, None) == 1  # no scales
+    assert lib.ppca_create(ctypes.byref(out), fake, 10, 16, 16, P.PPCA_F32, fake, None) == 1    # stray scales
+    assert lib.ppca_create(ctypes.byref(out), fake, 10, 16, 16, 9, None, None) == 1             # dtype
+    # NULL handle everywhere
+    params = P.ppca_prime_params()
+    assert lib.ppca_prime(None, 0, 4, 1, ctypes.byref(params)) == 1
+    assert lib.ppca_finalize(None, 1, fake, fake, 0) == 1
+    assert lib.ppca_sync(None) == 1
+    assert lib.ppca_destroy(None) == 0
+    assert lib.ppca_quantize_bf16(None, 4, 4, 4, fake, 4, None) == 1
+    assert lib.ppca_quantize_fp8(fake, 4, 8, 4, fake, 8, fake, None) == 1   # ld_in < d

@@ -1,0 +1,190 @@
+"""GPU parity of the individual steps, through the C ABI, against the FP64 oracle.
+
+Tolerances (derived from the arithmetic; u = 2^-24):
+* X-pass, FP32 data, ACCURATE: FP32 products, FP32 chunks of <= 256 terms
+  folded into double-float sums: normwise ||dZ|| / ||Z|| <= 2e-5
+  (about u * (sqrt(d) + 16) with a safety factor ~3).
+* X-pass, BF16 data, FAST: V and Y rounded to BF16 (2^-9 relative), so 1e-2.
+* CholeskyQR2 vs the oracle's MGS2 (both the unique thin-QR factor with a
+  positive diagonal): entrywise <= 1e-5 for kappa(V) ~ 10 (about kappa * u * m).
+* eigensolver: eigenvalues are FP64 Rayleigh quotients of FP32 Jacobi vectors,
+  relative error <= 1e-9; vectors <= 2e-5 rad for relative gaps >= 1%.
+* quantisers: bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev_basis, dev_matrix, empty_basis, host_basis, normwise, stored_f64
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P(cuda_device):
+    import paper_2109_03709_gb300 as P
+    P.load_library()
+    return P
+
+
+XPASS_CASES = [
+    # n, d, m, r0, r1, ld
+    (1000, 64, 16, 0, 1000, None),
+    (4099, 200, 64, 3, 4099, None),
+    (777, 256, 128, 100, 612, None),
+    (50, 16, 1, 0, 1, None),
+    (300, 37, 5, 0, 300, 40),           # padded leading dimension, ragged d
+    (2050, 1024, 33, 1, 2050, None),    # ragged m
+]
+
+
+@pytest.mark.parametrize("n,d,m,r0,r1,ld", XPASS_CASES)
+def test_xpass_fp32(P, n, d, m, r0, r1, ld):
+    lam = 0.95 ** np.arange(1, d + 1)
+    X, _ = synth.gaussian_data(n, d, lam, seed=n + d)
+    Xd = dev_matrix(X, "f32", ld)
+    V = synth.initial_basis(d, m, seed=m)
+    Vd = dev_basis(V)
+    Zd = empty_basis(d, m)
+    h = P.ppca_create(Xd)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zd, P.PPCA_PREC_ACCURATE)
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)[r0:r1]
+    Vs = host_basis(Vd)
+    Zref = Xs.T @ (Xs @ Vs)
+    assert normwise(host_basis(Zd), Zref) <= 2e-5
+
+
+BF16_CASES = [
+    # n, d, m, r0, r1
+    (3001, 512, 64, 0, 3001),
+    (1000, 200, 33, 17, 931),        # ragged d (not a multiple of 64), ragged m and rows
+    (257, 64, 1, 0, 257),
+    (5000, 1024, 128, 0, 5000),
+    (600000, 64, 16, 0, 600000),     # many tiles per CTA, several flush blocks per row group
+    (4096, 4096, 128, 0, 4096),
+]
+
+
+@pytest.mark.parametrize("n,d,m,r0,r1", BF16_CASES)
+@pytest.mark.parametrize("prec,tol", [("FAST", 1e-2), ("ACCURATE", 2e-5)])
+def test_xpass_bf16(P, n, d, m, r0, r1, prec, tol):
+    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=9) if n * d <= 5e7 else \
+        (np.random.default_rng(9).standard_normal((n, d)), None)
+    Xd = dev_matrix(X, "bf16")
+    V = synth.initial_basis(d, m, seed=3)
+    Vd = dev_basis(V)
+    Zd = empty_basis(d, m)
+    h = P.ppca_create(Xd)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zd, getattr(P, "PPCA_PREC_" + prec))
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)[r0:r1]
+    Zref = Xs.T @ (Xs @ host_basis(Vd))
+    assert normwise(host_basis(Zd), Zref) <= tol
+    # column by column as well (no column may hide behind the others)
+    Zg = host_basis(Zd)
+    for c in range(m):
+        assert normwise(Zg[:, c], Zref[:, c]) <= 4 * tol
+
+
+@pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (4096, 128)])
+def test_cholesky_qr2_matches_thin_qr(P, d, m):
+    V = synth.initial_basis(d, m, seed=d)
+    Vd = dev_basis(V)
+    Qd = empty_basis(d, m)
+    Xd = dev_matrix(np.zeros((2, d)), "f32", ld=(d + 3) // 4 * 4)
+    h = P.ppca_create(Xd)
+    P.ppca_orthonormalize(h, Vd, Qd, m)
+    P.ppca_sync(h)
+    Q = host_basis(Qd)
+    Qref = oracle.orth(host_basis(Vd))
+    assert np.abs(Q - Qref).max() <= 1e-5
+    assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-5
+
+
+def test_cholesky_qr2_ill_conditioned(P):
+    d, m = 512, 32
+    rng = np.random.default_rng(1)
+    U, _ = np.linalg.qr(rng.standard_normal((d, m)))
+    W, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    V = (U * np.logspace(0, -5, m)[None, :]) @ W.T          # kappa = 1e5
+    Vd = dev_basis(V)
+    Qd = empty_basis(d, m)
+    h = P.ppca_create(dev_matrix(np.zeros((2, d)), "f32"))
+    P.ppca_orthonormalize(h, Vd, Qd, m)
+    P.ppca_sync(h)
+    Q = host_basis(Qd)
+    assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-5
+    # span preserved: principal angles between span(Q) and span(V) small
+    assert oracle.principal_angles(Q, host_basis(Vd)).max() < 1e-2
+
+
+def test_cholesky_breakdown_is_reported(P):
+    d, m = 128, 8
+    V = synth.initial_basis(d, m, seed=2)
+    V[:, 5] = V[:, 2]                                       # rank-deficient
+    h = P.ppca_create(dev_matrix(np.zeros((2, d)), "f32"))
+    Qd = empty_basis(d, m)
+    P.ppca_orthonormalize(h, dev_basis(V), Qd, m)
+    with pytest.raises(P.PPCAError) as ei:
+        P.ppca_sync(h)
+    assert ei.value.status_name == "PPCA_ERR_NUMERICAL"
+    P.ppca_sync(h)                                          # status cleared
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 16, 64, 127, 128])
+def test_eigh_small(P, m):
+    import torch
+    rng = np.random.default_rng(m)
+    Qm = synth.haar_orthogonal(m, rng)
+    lam = np.sort(np.exp(-np.arange(m) / 20.0) * (1 + 0.02 * rng.random(m)))[::-1] * 1e3
+    G = (Qm * lam) @ Qm.T
+    G = 0.5 * (G + G.T)
+    Gd = torch.from_numpy(G).cuda()
+    wd = torch.empty(m, dtype=torch.float64, device="cuda")
+    Ud = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    h = P.ppca_create(dev_matrix(np.zeros((2, 4)), "f32"))
+    P.ppca_eigh(h, Gd, m, wd, Ud)
+    P.ppca_sync(h)
+    w = wd.cpu().numpy()
+    U = Ud.cpu().numpy().T            # column-major m x m -> columns are eigenvectors
+    wref, Uref = oracle.eigh_desc(G)
+    # eigenvalues: FP64 Rayleigh quotients of vectors accurate to ~u*|G|/gap
+    np.testing.assert_allclose(w, wref, rtol=1e-9, atol=1e-9 * wref[0])
+    # vectors: FP32 Jacobi on a dense matrix; its backward error is c(m) u |G| with
+    # c growing slowly with m and the sweep count, so the angle is <~ 16 u |G| / gap_i
+    gaps = np.minimum(np.abs(np.diff(np.r_[np.inf, wref])), np.abs(np.diff(np.r_[wref, -np.inf])))
+    u = 2.0 ** -24
+    for i in range(m):
+        assert oracle.angle(U[:, i], Uref[:, i]) <= 16 * u * wref[0] / gaps[i] + 1e-6
+
+
+def test_quantize_bf16_bit_exact(P):
+    import torch
+    rng = np.random.default_rng(0)
+    X = (rng.standard_normal((257, 300)) * 10.0 ** rng.uniform(-3, 3, (257, 300))).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    out = torch.empty((257, 304), dtype=torch.int16, device="cuda")[:, :300]
+    P.ppca_quantize_bf16(Xd, out)
+    torch.cuda.synchronize()
+    lib = torch.from_numpy(X).to(torch.bfloat16).view(torch.int16).numpy()
+    np.testing.assert_array_equal(out.cpu().numpy(), lib)
+
+
+def test_quantize_fp8_bit_exact(P):
+    import torch
+    rng = np.random.default_rng(1)
+    X = (rng.standard_normal((129, 520)) * 10.0 ** rng.uniform(-2, 2, (129, 1))).astype(np.float32)
+    X[7] = 0.0
+    X[8, 3] = 1e-30
+    Xd = torch.from_numpy(X).cuda()
+    out = torch.empty((129, 528), dtype=torch.uint8, device="cuda")[:, :520]
+    sc = torch.empty(129, dtype=torch.float32, device="cuda")
+    P.ppca_quantize_fp8(Xd, out, sc)
+    torch.cuda.synchronize()
+    qref, sref = oracle.fp8_row_quantize(X)
+    np.testing.assert_array_equal(sc.cpu().numpy(), sref)
+    np.testing.assert_array_equal(out.cpu().numpy(), qref)
