@@ -242,6 +242,33 @@ PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *
 PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, double *w, double *U);
 
 /*
+ * The same symmetric eigensolve as ppca_eigh, for callers that cannot allocate
+ * device memory where they need it -- for example code that runs while its
+ * stream is being captured into a CUDA graph, code on a latency-critical path
+ * that must not call cudaMalloc (which may synchronise the device), or a host
+ * program whose device memory is handed out by its own allocator.  The paper
+ * has no counterpart of this call; it exists for those callers only.
+ *
+ * It takes no handle and allocates nothing: its scratch is a fixed array of
+ * 256 KiB in the library's device memory, which every device that loads the
+ * library holds until the process exits.
+ *   G       device, m x m FP64 symmetric input (not modified)
+ *   m       1 <= m <= 128 (the size the fixed scratch holds); anything else
+ *           returns PPCA_ERR_INVALID with a message, and nothing is enqueued
+ *   w, U    device outputs as in ppca_eigh (descending, column-major, signed)
+ *   status  device int or NULL: set to a nonzero code if the Jacobi sweeps hit
+ *           their cap (left unchanged otherwise); the caller clears it
+ *   stream  cudaStream_t (as void*) the solve is enqueued on
+ * The first call on a device looks up the device address of the scratch array
+ * (with that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind,
+ * so calls that overlap on the same GPU race: order them (one stream, or
+ * events).  The outputs are identical to ppca_eigh's for the same input.
+ */
+PPCA_API ppca_status ppca_eigh_noalloc(const double *G, int32_t m, double *w, double *U, int *status,
+                                       void *stream);
+
+/*
  * Data-format step: quantise FP32 rows (device, n x d, leading dimension ld_in)
  * to BF16 (round to nearest even) or to FP8 E4M3 with one scale per row,
  *   scale[r] = max_j |x[r][j]| / 448 (1 for an all-zero row),

@@ -24,7 +24,7 @@ __all__ = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_timing", "EXPORTED_SYMBOLS",
+    "ppca_timing", "ppca_eigh_noalloc", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -43,6 +43,7 @@ EXPORTED_SYMBOLS = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
+    "ppca_eigh_noalloc",
 ]
 
 
@@ -104,6 +105,7 @@ _SIGS = {
     "ppca_quantize_fp8": (_c_status, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
     "ppca_set_timing": (_c_status, [_vp, _i32]),
     "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
+    "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -279,6 +281,17 @@ def ppca_orthonormalize(h: Handle, V, Q, m: int):
 
 def ppca_eigh(h: Handle, G, m: int, w, U):
     _check(load_library().ppca_eigh(h.ptr, _ptr(G), m, _ptr(w), _ptr(U)), "ppca_eigh")
+
+
+def ppca_eigh_noalloc(G, m: int, w, U, status=None, stream=None):
+    """Eigensolve without any device allocation (fixed library scratch, m <= 128).
+
+    For callers that cannot allocate device memory where they solve (e.g. while
+    capturing a CUDA graph); calls that overlap on the same GPU race on the
+    shared scratch and must be ordered by the caller.
+    """
+    _check(load_library().ppca_eigh_noalloc(_ptr(G), m, _ptr(w), _ptr(U), _ptr(status), _stream_ptr(stream)),
+           "ppca_eigh_noalloc")
 
 
 def ppca_quantize_bf16(X, out, stream=None):

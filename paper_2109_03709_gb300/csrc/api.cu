@@ -583,6 +583,15 @@ ppca_status ppca_eigh(ppca_handle* h, const double* G, int32_t m, double* w, dou
     return PPCA_OK;
 }
 
+ppca_status ppca_eigh_noalloc(const double* G, int32_t m, double* w, double* U, int* status, void* stream) {
+    if (!G || !w || !U) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (m < 1 || m > kMaxM)
+        return fail(PPCA_ERR_INVALID, "m = %d out of range [1, %d]: the fixed %zu-byte scratch holds m <= %d", m,
+                    kMaxM, eigh_noalloc_scratch_bytes(), kMaxM);
+    CUDA_TRY(eigh_small_noalloc(G, m, w, U, status, static_cast<cudaStream_t>(stream)));
+    return PPCA_OK;
+}
+
 ppca_status ppca_quantize_bf16(const float* X, int64_t n, int64_t d, int64_t ld_in, uint16_t* out, int64_t ld_out,
                                void* stream) {
     if (!X || !out) return fail(PPCA_ERR_INVALID, "NULL argument");

@@ -39,6 +39,10 @@ cudaError_t apply_rinv(const float* V, const float* Rf, int64_t d, int m, float*
 // G m x m FP64 row-major; w (m) FP64; U m x m column-major FP64.
 // scratch: jacobi_scratch_bytes(m).
 size_t jacobi_scratch_bytes(int m);
+// Same solve with its scratch in a file-scope device array (no allocation);
+// rejects m outside [1, kMaxM] with cudaErrorInvalidValue.
+size_t eigh_noalloc_scratch_bytes();
+cudaError_t eigh_small_noalloc(const double* G, int m, double* w, double* U, int* status, cudaStream_t st);
 cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scratch, int* status,
                        cudaStream_t st);
 

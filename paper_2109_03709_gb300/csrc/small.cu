@@ -17,6 +17,8 @@
 #include <cuda_fp8.h>
 #include <math.h>
 
+#include <mutex>
+
 namespace ppca {
 
 namespace {
@@ -639,6 +641,50 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
     note_launch();
     sort_desc_kernel<<<1, 256, 0, st>>>(lam, U64, m, w, U);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free eigensolve.  Some callers cannot allocate device memory at
+// the point where they need the small eigensolve: code running while a stream
+// is being captured into a CUDA graph, code on a latency-critical path where a
+// cudaMalloc (which may synchronise the device) is not acceptable, or hosts
+// whose memory is handed out by their own allocator.  For them the solve's
+// scratch is one file-scope device array, sized for the largest m (128), that
+// every device loading this library keeps until the process exits (each device
+// has its own copy).  On one device the array is shared by all calls: calls
+// that overlap on that GPU (e.g. enqueued on different streams) race on it and
+// must be ordered by the caller.  Nothing in it needs to start at zero: every
+// kernel of the solve writes its part of the scratch before reading it.
+constexpr size_t kEighNoallocScratchBytes = 256 * 1024;
+static __device__ __align__(256) unsigned char g_eigh_scratch[kEighNoallocScratchBytes];
+
+size_t eigh_noalloc_scratch_bytes() { return kEighNoallocScratchBytes; }
+
+cudaError_t eigh_small_noalloc(const double* G, int m, double* w, double* U, int* status, cudaStream_t st) {
+    static_assert(kEighNoallocScratchBytes >= 1024 + 6 * 256 + (size_t)kMaxM * kMaxM * 12 + (size_t)kMaxM * 12,
+                  "eigensolve scratch array too small for m = kMaxM");
+    if (m < 1 || m > kMaxM || jacobi_scratch_bytes(m) > kEighNoallocScratchBytes) return cudaErrorInvalidValue;
+    // Set-up, once per device and with that device current: host code may not
+    // use g_eigh_scratch directly (its host-side name is only a stand-in), so
+    // the device address is looked up and cached.
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_eigh_scratch);
+            if (e != cudaSuccess) return e;
+            addr[dev] = p;
+        }
+        scratch = addr[dev];
+    }
+    return eigh_small(G, m, w, U, scratch, status, st);
 }
 
 cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, const double* w, int k, double inv_n,
