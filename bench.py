@@ -42,6 +42,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--rows", type=int, default=0,
+                    help="override n with a smaller row count (for profiler captures of a small case)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-rows", type=int, default=32768, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-passes", type=int, default=8, help=argparse.SUPPRESS)
@@ -174,6 +176,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     cfg = synth.CONFIGS[args.workload]
     n, d, k, m = cfg.n, cfg.d, cfg.k, cfg.m
+    if args.rows:
+        n = args.rows
     T = cfg.primers["power"]["T"]
     tdt = {"bf16": torch.bfloat16, "f32": torch.float32}[cfg.dtype]
     X, _ = synth.gaussian_data_torch(n, d, cfg.lam(), cfg.seed + 1000 * rank, "cuda", tdt,

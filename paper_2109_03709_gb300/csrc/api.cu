@@ -197,15 +197,20 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
     return PPCA_OK;
 }
 
-// CholeskyQR2: Q = orth(V) with positive diagonal, Q may alias V.
+// CholeskyQR2: Q = orth(V) with positive diagonal, Q may alias V (the first
+// pass writes the workspace buffer T, the second writes Q).  The first
+// Cholesky runs in double-float arithmetic (V may be ill-conditioned); the
+// second factors a Gram matrix within rounding of the identity, so FP32
+// suffices there.
 ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     const int64_t d = h->x.d;
     const float* src = V;
     for (int rep = 0; rep < 2; ++rep) {
+        float* dst = rep == 0 ? h->T : Q;
         CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream));
-        CUDA_TRY(cholesky(h->G, m, h->Rf, h->status, h->stream));
-        CUDA_TRY(apply_rinv(src, h->Rf, d, m, Q, h->stream));
-        src = Q;
+        CUDA_TRY(cholesky(h->G, m, h->Rf, rep == 0, h->status, h->stream));
+        CUDA_TRY(apply_rinv(src, h->Rf, d, m, dst, h->stream));
+        src = dst;
     }
     return PPCA_OK;
 }

@@ -60,6 +60,66 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     lo = __fsub_rn(e, __fsub_rn(hi, s));
 }
 
+// Double-float ("df") numbers: an unevaluated sum hi + lo of two floats with
+// |lo| <= ulp(hi)/2, about 48 significand bits.  Knuth's TwoSum, the FMA-based
+// TwoProduct and Dekker/Bailey-style normalisation; used where FP64 accuracy
+// is needed but GB300's FP64 rate is too low.
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_make(double x) {
+    dfloat r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ dfloat df_norm(float s, float e) {
+    dfloat r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ dfloat df_addx(dfloat a, dfloat b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    return df_norm(s, e);
+}
+
+__device__ __forceinline__ dfloat df_neg(dfloat a) {
+    a.hi = -a.hi;
+    a.lo = -a.lo;
+    return a;
+}
+
+__device__ __forceinline__ dfloat df_mulx(dfloat a, dfloat b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return df_norm(p, e);
+}
+
+// a / b: one correction step of the float quotient.
+__device__ __forceinline__ dfloat df_divx(dfloat a, dfloat b) {
+    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const dfloat r = df_addx(a, df_neg(df_mulx(df_norm(q1, 0.f), b)));
+    const float q2 = __fdiv_rn(r.hi, b.hi);
+    return df_norm(q1, q2);
+}
+
+// sqrt(a) for a > 0: one Newton correction of the float root.
+__device__ __forceinline__ dfloat df_sqrtx(dfloat a) {
+    const float s = __fsqrt_rn(a.hi);
+    const float p = __fmul_rn(s, s);
+    const float pe = __fmaf_rn(s, s, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+    return df_norm(s, __fdiv_rn(r, 2.0f * s));
+}
+
 __device__ __forceinline__ void set_status(int* status, int code) {
     if (status) atomicCAS(status, 0, code);
 }

@@ -31,9 +31,12 @@ cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G,
                     cudaStream_t st);
 
 // Cholesky G = R^T R (FP64, one CTA); R upper, written as FP32 (Rf) and FP64 (Rd).
-cudaError_t cholesky(const double* G, int m, float* Rf, int* status, cudaStream_t st);
+// Cholesky G = R^T R (one CTA), in double-float arithmetic or plain FP32;
+// writes X = R^-1 (upper, row-major FP32) to Rinv.
+cudaError_t cholesky(const double* G, int m, float* Rinv, bool double_float, int* status, cudaStream_t st);
 // Q = V R^-1 by row-wise forward substitution (FP32); Q may alias V.
-cudaError_t apply_rinv(const float* V, const float* Rf, int64_t d, int m, float* Q, cudaStream_t st);
+// Q = V R^-1 as a product with the triangular inverse; Q must not alias V.
+cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st);
 
 // Symmetric eigensolve (FP32 Jacobi + FP64 Rayleigh quotients), descending.
 // G m x m FP64 row-major; w (m) FP64; U m x m column-major FP64.

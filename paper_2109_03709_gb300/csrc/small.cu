@@ -42,6 +42,7 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
     __shared__ float As[32][kGramTile + 1];
     __shared__ float Bs[32][kGramTile + 1];
     const int ti = blockIdx.x, tj = blockIdx.y, p = blockIdx.z;
+    if (A == B && ti > tj) return;          // symmetric: the reduction mirrors the upper tiles
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int i0 = ti * kGramTile, j0 = tj * kGramTile;
     const int64_t rbeg = (int64_t)p * slice_rows;
@@ -84,12 +85,14 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
         }
 }
 
-__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, double* __restrict__ G) {
+__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, bool sym, double* __restrict__ G) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
+    const int i = idx / m, j = idx % m;
+    const int src = (sym && i / kGramTile > j / kGramTile) ? j * m + i : idx;
     double s = 0.0;
     for (int p = 0; p < P; ++p) {
-        const float* o = part + ((int64_t)p * m * m + idx) * 2;
+        const float* o = part + ((int64_t)p * m * m + src) * 2;
         s += (double)o[0] + (double)o[1];
     }
     G[idx] = s;
@@ -97,63 +100,139 @@ __global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m,
 
 // ------------------------------------------------------------------ Cholesky
 
-__global__ void cholesky_kernel(const double* __restrict__ G, int m, float* __restrict__ Rf, int* status) {
-    extern __shared__ double a[];   // m x m
+// Right-looking Cholesky G = R^T R (R upper) in one CTA, then the triangular
+// inverse X = R^-1 in FP32, written row-major to Rinv.  DF = true works in
+// double-float arithmetic -- FP64-class accuracy (about 48 significand bits)
+// at FP32-pipe speed, for the first, possibly ill-conditioned CholeskyQR pass;
+// DF = false is plain FP32 for the second pass, whose Gram matrix is within
+// rounding of the identity.  A pivot at or below 1e-15 * trace(G) (also NaN)
+// marks the basis as numerically rank-deficient: the pivot is replaced by that
+// floor (so the outputs stay finite) and kDevCholeskyBreakdown is recorded.
+// Thread layout: warp w handles rows i = k+1+w, k+1+w+W, ...; lanes sweep
+// the columns j >= i of that row (no integer division in the inner loops).
+constexpr int kCholThreads = 512;
+
+template <bool DF>
+__global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ G, int m,
+                                                               float* __restrict__ Rinv, int* status) {
+    extern __shared__ float csm[];
+    float* ah = csm;                       // m x m, hi parts (the FP32 value when !DF)
+    float* al = ah + m * m;                // m x m, lo parts (DF only)
+    float* x = DF ? al + m * m : al;       // m x m: R (row-major), then overwritten by R^-1
+    __shared__ float inv_hi, inv_lo, floor_pivot;
     __shared__ int broke;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) a[e] = G[e];
-    if (threadIdx.x == 0) broke = 0;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32, nw = kCholThreads / 32;
+    for (int e = threadIdx.x; e < m * m; e += kCholThreads) {
+        const dfloat v = df_make(G[e]);
+        ah[e] = v.hi;
+        if (DF) al[e] = v.lo;
+    }
+    if (warp == 0) {
+        double tr = 0.0;
+        for (int i = lane; i < m; i += 32) tr += fabs(G[i * m + i]);
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (lane == 0) {
+            floor_pivot = (float)((tr > 0.0 ? tr : 1.0) * 1e-15);
+            broke = 0;
+        }
+    }
     __syncthreads();
-    double trace = 0.0;
-    for (int i = 0; i < m; ++i) trace += fabs(a[i * m + i]);
-    // a pivot below ~eps * trace means V is numerically rank-deficient
-    const double floor_pivot = (trace > 0.0 ? trace : 1.0) * 1e-15;
     for (int k = 0; k < m; ++k) {
         if (threadIdx.x == 0) {
-            double piv = a[k * m + k];
-            if (!(piv > floor_pivot)) {      // also catches NaN
+            dfloat pv{ah[k * m + k], DF ? al[k * m + k] : 0.f};
+            if (!(pv.hi > floor_pivot)) {   // also catches NaN
                 broke = 1;
-                piv = floor_pivot;
+                pv = dfloat{floor_pivot, 0.f};
             }
-            a[k * m + k] = sqrt(piv);
+            if (DF) {
+                const dfloat r = df_sqrtx(pv);
+                x[k * m + k] = r.hi;
+                const dfloat inv = df_divx(dfloat{1.f, 0.f}, r);
+                inv_hi = inv.hi;
+                inv_lo = inv.lo;
+            } else {
+                const float r = sqrtf(pv.hi);
+                x[k * m + k] = r;
+                inv_hi = 1.0f / r;
+                inv_lo = 0.f;
+            }
         }
         __syncthreads();
-        const double rkk = a[k * m + k];
-        for (int j = k + 1 + threadIdx.x; j < m; j += blockDim.x) a[k * m + j] /= rkk;
-        __syncthreads();
-        const int rem = m - k - 1;
-        for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-            const int i = k + 1 + e / rem, j = k + 1 + e % rem;
-            if (j >= i) a[i * m + j] -= a[k * m + i] * a[k * m + j];
+        // row k of R (scaled copy, written to x) and the trailing update
+        // a_ij -= r_ki r_kj, k < i <= j, with r_k* = a_k* / r_kk on the fly
+        const dfloat inv{inv_hi, inv_lo};
+        if (warp == nw - 1)
+            for (int j = k + 1 + lane; j < m; j += 32)
+                x[k * m + j] = DF ? df_mulx(dfloat{ah[k * m + j], al[k * m + j]}, inv).hi : ah[k * m + j] * inv_hi;
+        for (int i = k + 1 + warp; i < m; i += nw) {
+            const dfloat rki = DF ? df_mulx(dfloat{ah[k * m + i], al[k * m + i]}, inv)
+                                  : dfloat{ah[k * m + i] * inv_hi, 0.f};
+            for (int j = i + lane; j < m; j += 32) {
+                if (DF) {
+                    const dfloat rkj = df_mulx(dfloat{ah[k * m + j], al[k * m + j]}, inv);
+                    const dfloat v = df_addx(dfloat{ah[i * m + j], al[i * m + j]}, df_neg(df_mulx(rki, rkj)));
+                    ah[i * m + j] = v.hi;
+                    al[i * m + j] = v.lo;
+                } else {
+                    ah[i * m + j] = __fmaf_rn(-rki.hi, ah[k * m + j] * inv_hi, ah[i * m + j]);
+                }
+            }
         }
         __syncthreads();
     }
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        Rf[e] = (j >= i) ? (float)a[e] : 0.f;
+    // R (FP32, upper, in x) -> R^-1 in place of ah, row by row from the bottom:
+    // row i of X = (e_i - sum_{l>i} r_il X[l, :]) / r_ii; columns in parallel.
+    float* X = ah;
+    for (int i = m - 1; i >= 0; --i) {
+        const float rii = x[i * m + i];
+        for (int j = threadIdx.x; j < m; j += kCholThreads) {
+            float s = (j == i) ? 1.f : 0.f;
+            if (j > i) {
+                float s0 = 0.f, s1 = 0.f;
+                int l = i + 1;
+                for (; l + 1 <= j; l += 2) {
+                    s0 = __fmaf_rn(-x[i * m + l], X[l * m + j], s0);
+                    s1 = __fmaf_rn(-x[i * m + l + 1], X[(l + 1) * m + j], s1);
+                }
+                if (l <= j) s0 = __fmaf_rn(-x[i * m + l], X[l * m + j], s0);
+                s = s0 + s1;
+            }
+            X[i * m + j] = (j >= i) ? s / rii : 0.f;
+        }
+        __syncthreads();
     }
+    for (int e = threadIdx.x; e < m * m; e += kCholThreads) Rinv[e] = X[e];
     if (threadIdx.x == 0 && broke) set_status(status, kDevCholeskyBreakdown);
 }
 
-// Q = V R^-1: each thread owns one row v of V and solves q R = v left to right.
-constexpr int kRinvThreads = 64;
+// Q = V X with X = R^-1 upper triangular (row-major): thread = one row of V,
+// block column = 32 output columns; Q must not alias V.
+constexpr int kApplyRows = 128;
 
-__global__ void apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rf, int64_t d, int m,
-                                  float* __restrict__ Q) {
-    extern __shared__ float sm[];
-    float* R = sm;                         // m x m
-    float* q = sm + m * m;                 // m x kRinvThreads
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) R[e] = Rf[e];
-    __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d) return;
-    const int t = threadIdx.x;
-    for (int j = 0; j < m; ++j) q[j * kRinvThreads + t] = V[(int64_t)j * d + r];
-    for (int j = 0; j < m; ++j) {
-        float s = q[j * kRinvThreads + t];
-        for (int i = 0; i < j; ++i) s = __fmaf_rn(-q[i * kRinvThreads + t], R[i * m + j], s);
-        q[j * kRinvThreads + t] = s / R[j * m + j];
+__global__ void __launch_bounds__(kApplyRows) apply_rinv_kernel(const float* __restrict__ V,
+                                                                 const float* __restrict__ Rinv, int64_t d, int m,
+                                                                 float* __restrict__ Q) {
+    extern __shared__ float xs[];   // (j0 + 32) x 32 slice of X
+    const int j0 = blockIdx.y * 32;
+    const int lmax = min(m, j0 + 32);
+    for (int e = threadIdx.x; e < lmax * 32; e += blockDim.x) {
+        const int l = e / 32, jj = e % 32;
+        xs[e] = (j0 + jj < m) ? Rinv[l * m + j0 + jj] : 0.f;
     }
-    for (int j = 0; j < m; ++j) Q[(int64_t)j * d + r] = q[j * kRinvThreads + t];
+    __syncthreads();
+    const int64_t r = (int64_t)blockIdx.x * kApplyRows + threadIdx.x;
+    if (r >= d) return;
+    float acc[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.f;
+    for (int l = 0; l < lmax; ++l) {
+        const float v = V[(int64_t)l * d + r];
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) acc[jj] = __fmaf_rn(v, xs[l * 32 + jj], acc[jj]);
+    }
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj)
+        if (j0 + jj < m) Q[(int64_t)(j0 + jj) * d + r] = acc[jj];
 }
 
 // ------------------------------------------------------------------ Jacobi
@@ -182,18 +261,20 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
     extern __shared__ float js[];
     const int N = m + (m & 1);
     const int H = N / 2;
-    float* A = js;                  // N x N
-    float* U = A + N * N;           // N x N (column j = eigenvector j)
-    float* cs = U + N * N;          // H cosines
+    const int S = N + 1;            // padded row stride: row and column sweeps are bank-conflict free
+    float* A = js;                  // N x S
+    float* U = A + N * S;           // N x S (column j = eigenvector j)
+    float* cs = U + N * S;          // H cosines
     float* sn = cs + H;             // H sines
-    float* tn = sn + H;             // H tangents
-    int* pp = reinterpret_cast<int*>(tn + H);
+    float* dp = sn + H;             // H new a_pp
+    float* dq = dp + H;             // H new a_qq
+    int* pp = reinterpret_cast<int*>(dq + H);
     int* qq = pp + H;
     __shared__ int rotated;
     for (int e = threadIdx.x; e < N * N; e += NT) {
         const int i = e / N, j = e % N;
-        A[e] = (i < m && j < m) ? (float)(0.5 * (G[i * m + j] + G[j * m + i])) : 0.f;
-        U[e] = (i == j) ? 1.f : 0.f;
+        A[i * S + j] = (i < m && j < m) ? (float)(0.5 * (G[i * m + j] + G[j * m + i])) : 0.f;
+        U[i * S + j] = (i == j) ? 1.f : 0.f;
     }
     jbar<NT>();
     const float tol = 4.0f * 5.96e-8f;
@@ -202,12 +283,13 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
         if (threadIdx.x == 0) rotated = 0;
         jbar<NT>();
         for (int step = 0; step < N - 1; ++step) {
+            // rotations of the N/2 disjoint pairs of this step (classical angle)
             for (int t = threadIdx.x; t < H; t += NT) {
                 int p = rr_player(t, step, N), q = rr_player(N - 1 - t, step, N);
                 if (p > q) { const int x = p; p = q; q = x; }
                 pp[t] = p;
                 qq[t] = q;
-                const float apq = A[p * N + q], app = A[p * N + p], aqq = A[q * N + q];
+                const float apq = A[p * S + q], app = A[p * S + p], aqq = A[q * S + q];
                 float c = 1.f, s = 0.f, tt = 0.f;
                 if (fabsf(apq) > 1e-30f && fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
                     const float tau = (aqq - app) / (2.0f * apq);
@@ -222,42 +304,46 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
                 }
                 cs[t] = c;
                 sn[t] = s;
-                tn[t] = tt;
+                dp[t] = app - tt * apq;
+                dq[t] = aqq + tt * apq;
             }
             jbar<NT>();
-            // A <- J^T A J, one 2x2 block per work item
-            for (int b = threadIdx.x; b < H * H; b += NT) {
-                const int t = b / H, u = b % H;
-                const float st = sn[t], su = sn[u];
-                if (st == 0.f && su == 0.f) continue;
-                const int p = pp[t], q = qq[t], pu = pp[u], qu = qq[u];
-                if (t == u) {
-                    const float apq = A[p * N + q];
-                    A[p * N + p] -= tn[t] * apq;
-                    A[q * N + q] += tn[t] * apq;
-                    A[p * N + q] = 0.f;
-                    A[q * N + p] = 0.f;
-                    continue;
+            // rows p, q: A <- J^T A
+            for (int t = threadIdx.x / 32; t < H; t += NT / 32) {      // one warp per pair
+                const float s = sn[t];
+                if (s == 0.f) continue;
+                const float c = cs[t];
+                const int p = pp[t], q = qq[t];
+                for (int j = threadIdx.x % 32; j < N; j += 32) {
+                    const float apj = A[p * S + j], aqj = A[q * S + j];
+                    A[p * S + j] = c * apj - s * aqj;
+                    A[q * S + j] = s * apj + c * aqj;
                 }
-                const float ct = cs[t], cu = cs[u];
-                const float a11 = A[p * N + pu], a12 = A[p * N + qu], a21 = A[q * N + pu], a22 = A[q * N + qu];
-                const float r11 = ct * a11 - st * a21, r12 = ct * a12 - st * a22;
-                const float r21 = st * a11 + ct * a21, r22 = st * a12 + ct * a22;
-                A[p * N + pu] = cu * r11 - su * r12;
-                A[p * N + qu] = su * r11 + cu * r12;
-                A[q * N + pu] = cu * r21 - su * r22;
-                A[q * N + qu] = su * r21 + cu * r22;
             }
-            // U <- U J
-            for (int b = threadIdx.x; b < N * H; b += NT) {
-                const int i = b / H, u = b % H;
-                const float su = sn[u];
-                if (su == 0.f) continue;
-                const float cu = cs[u];
+            jbar<NT>();
+            // columns p, q: A <- A J, U <- U J; the pair's own 2x2 block gets the
+            // exact zero and the tangent-formula diagonal
+            for (int u = threadIdx.x / 32; u < H; u += NT / 32) {      // one warp per pair
+                const float s = sn[u];
+                if (s == 0.f) continue;
+                const float c = cs[u];
                 const int p = pp[u], q = qq[u];
-                const float uip = U[i * N + p], uiq = U[i * N + q];
-                U[i * N + p] = cu * uip - su * uiq;
-                U[i * N + q] = su * uip + cu * uiq;
+                for (int i = threadIdx.x % 32; i < N; i += 32) {
+                    if (i == p) {
+                        A[p * S + p] = dp[u];
+                        A[p * S + q] = 0.f;
+                    } else if (i == q) {
+                        A[q * S + p] = 0.f;
+                        A[q * S + q] = dq[u];
+                    } else {
+                        const float aip = A[i * S + p], aiq = A[i * S + q];
+                        A[i * S + p] = c * aip - s * aiq;
+                        A[i * S + q] = s * aip + c * aiq;
+                    }
+                    const float uip = U[i * S + p], uiq = U[i * S + q];
+                    U[i * S + p] = c * uip - s * uiq;
+                    U[i * S + q] = s * uip + c * uiq;
+                }
             }
             jbar<NT>();
         }
@@ -271,9 +357,9 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
     }
     for (int e = threadIdx.x; e < m * m; e += NT) {
         const int i = e / m, j = e % m;
-        Uf[j * m + i] = U[i * N + j];      // column-major m x m
+        Uf[j * m + i] = U[i * S + j];      // column-major m x m
     }
-    for (int i = threadIdx.x; i < m; i += NT) evals[i] = A[i * N + i];
+    for (int i = threadIdx.x; i < m; i += NT) evals[i] = A[i * S + i];
 }
 
 // FP64 polish: u_j <- u_j / |u_j|, lambda_j = u_j^T G u_j (Rayleigh quotient).
@@ -567,7 +653,7 @@ __global__ void copy_kernel(const float* __restrict__ s, float* __restrict__ d, 
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+    if (bytes <= 32 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
@@ -584,25 +670,34 @@ cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G,
     note_launch();
     gram_df_kernel<<<dim3(T, T, P), 256, 0, st>>>(A, B, d, m, part, slice);
     note_launch();
-    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, G);
+    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G);
     return cudaGetLastError();
 }
 
-cudaError_t cholesky(const double* G, int m, float* Rf, int* status, cudaStream_t st) {
-    const size_t smem = (size_t)m * m * sizeof(double);
-    cudaError_t e = allow_smem(cholesky_kernel, smem);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    cholesky_kernel<<<1, 512, smem, st>>>(G, m, Rf, status);
+cudaError_t cholesky(const double* G, int m, float* Rinv, bool double_float, int* status, cudaStream_t st) {
+    cudaError_t e;
+    if (double_float) {
+        const size_t smem = (size_t)3 * m * m * sizeof(float);
+        e = allow_smem(cholesky_kernel<true>, smem);
+        if (e != cudaSuccess) return e;
+        note_launch();
+        cholesky_kernel<true><<<1, kCholThreads, smem, st>>>(G, m, Rinv, status);
+    } else {
+        const size_t smem = (size_t)2 * m * m * sizeof(float);
+        e = allow_smem(cholesky_kernel<false>, smem);
+        if (e != cudaSuccess) return e;
+        note_launch();
+        cholesky_kernel<false><<<1, kCholThreads, smem, st>>>(G, m, Rinv, status);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t apply_rinv(const float* V, const float* Rf, int64_t d, int m, float* Q, cudaStream_t st) {
-    const size_t smem = (size_t)m * m * sizeof(float) + (size_t)m * kRinvThreads * sizeof(float);
-    cudaError_t e = allow_smem(apply_rinv_kernel, smem);
-    if (e != cudaSuccess) return e;
+cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st) {
+    if (V == Q) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)m * 32 * sizeof(float);
     note_launch();
-    apply_rinv_kernel<<<ceil_div_i(d, kRinvThreads), kRinvThreads, smem, st>>>(V, Rf, d, m, Q);
+    apply_rinv_kernel<<<dim3(ceil_div_i(d, kApplyRows), ceil_div_i(m, 32)), kApplyRows, smem, st>>>(V, Rinv, d, m,
+                                                                                                     Q);
     return cudaGetLastError();
 }
 
@@ -625,16 +720,16 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
     p += al(m * 8);
     int* sweeps = reinterpret_cast<int*>(p);
     const int N = m + (m & 1);
-    const size_t smem = (size_t)2 * N * N * sizeof(float) + (size_t)(N / 2) * (3 * sizeof(float) + 2 * sizeof(int));
+    const size_t smem = (size_t)2 * N * (N + 1) * sizeof(float) + (size_t)(N / 2) * (4 * sizeof(float) + 2 * sizeof(int));
     cudaError_t e;
     if (N <= 32) {
         note_launch();
         jacobi_f32_kernel<32><<<1, 32, smem, st>>>(G, m, evals, Uf, sweeps, status);
     } else {
-        e = allow_smem(jacobi_f32_kernel<256>, smem);
+        e = allow_smem(jacobi_f32_kernel<512>, smem);
         if (e != cudaSuccess) return e;
         note_launch();
-        jacobi_f32_kernel<256><<<1, 256, smem, st>>>(G, m, evals, Uf, sweeps, status);
+        jacobi_f32_kernel<512><<<1, 512, smem, st>>>(G, m, evals, Uf, sweeps, status);
     }
     note_launch();
     rayleigh_f64_kernel<<<m, 128, 0, st>>>(G, m, Uf, U64, lam);
