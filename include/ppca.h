@@ -183,6 +183,25 @@ PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
  * and clear it. */
 PPCA_API ppca_status ppca_sync(ppca_handle *h);
 
+/*
+ * Schedule of the fast X-pass over BF16 data (the knobs an autotuner sets).
+ * The product X^T X V needs every element of X once; the fused form reads each
+ * 128-row tile of X from HBM once: a producer pipeline computes Y = X V for the
+ * tile while consumer pipelines, each owning a 128-column slice of Z for the
+ * whole pass, re-read the tile from L2 for Z += X^T Y.  The unfused form runs
+ * the two products as separate kernels (X read twice).
+ */
+typedef struct ppca_schedule {
+    int32_t fused;            /* 1: fused single-read pass; 0: two kernels; -1: library default */
+    int32_t producers;        /* CTAs running Y = X V in the fused pass (0: one per SM)           */
+    int32_t window;           /* tiles a producer may run ahead of the slowest consumer (0: the  */
+                              /* library keeps about 48 MB of X in flight)                        */
+    int32_t reserved;         /* must be 0                                                        */
+} ppca_schedule;
+
+/* Set the X-pass schedule of a handle (takes effect at its next pass). */
+PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
+
 /* Device-time accounting of the X-passes (the hot step), for measurement. */
 typedef struct ppca_timing {
     double pass_ms[3];        /* summed device time of the X-passes since the reset,     */

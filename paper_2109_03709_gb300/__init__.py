@@ -24,7 +24,7 @@ __all__ = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_timing", "ppca_eigh_noalloc", "EXPORTED_SYMBOLS",
+    "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -43,7 +43,7 @@ EXPORTED_SYMBOLS = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_eigh_noalloc",
+    "ppca_eigh_noalloc", "ppca_set_schedule",
 ]
 
 
@@ -77,6 +77,15 @@ class ppca_timing(ctypes.Structure):
     ]
 
 
+class ppca_schedule(ctypes.Structure):
+    _fields_ = [
+        ("fused", ctypes.c_int32),
+        ("producers", ctypes.c_int32),
+        ("window", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -106,6 +115,7 @@ _SIGS = {
     "ppca_set_timing": (_c_status, [_vp, _i32]),
     "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
     "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
+    "ppca_set_schedule": (_c_status, [_vp, ctypes.POINTER(ppca_schedule)]),
 }
 
 
@@ -281,6 +291,11 @@ def ppca_orthonormalize(h: Handle, V, Q, m: int):
 
 def ppca_eigh(h: Handle, G, m: int, w, U):
     _check(load_library().ppca_eigh(h.ptr, _ptr(G), m, _ptr(w), _ptr(U)), "ppca_eigh")
+
+
+def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0):
+    s = ppca_schedule(fused, producers, window, 0)
+    _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
 
 
 def ppca_eigh_noalloc(G, m: int, w, U, status=None, stream=None):

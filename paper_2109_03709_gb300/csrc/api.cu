@@ -89,6 +89,7 @@ struct ppca_handle {
     double* eg = nullptr;
     SimtPassScratch simt;
     TcPassScratch tc;
+    TcSchedule sched;
 
     // priming state
     int method = -1;
@@ -189,7 +190,7 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
         h->timed_rows[(int)prec] += r1 - r0;
     }
     if (tc_pass_supported(x, m)) {
-        CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->status, h->num_sms, h->stream));
+        CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->sched, h->status, h->num_sms, h->stream));
     } else {
         CUDA_TRY(xpass_simt(x, V, m, r0, r1, Z, h->simt, h->stream));
     }
@@ -513,6 +514,16 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
     CUDA_TRY(cudaMemcpyAsync(h->V, p, dm, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaMemcpyAsync(h->buf, p + dm, dm, cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
+    if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->reserved != 0)
+        return fail(PPCA_ERR_INVALID, "schedule out of range");
+    h->sched.fused = s->fused;
+    h->sched.producers = s->producers;
+    h->sched.window = s->window;
     return PPCA_OK;
 }
 

@@ -341,6 +341,291 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_epilogue_teardown(hd, tmem_cols);
 }
 
+// ---------------------------------------------------------------- fused single-read pass
+//
+// One persistent, cooperatively launched kernel; every CTA runs two
+// warp-specialised pipelines that share the tensor core and TMEM:
+//   producer (warps 0-5)   Y_t = X_t V for 128-row tiles t = p, p + NP, ...
+//                          (X streamed from HBM), Y_t written as BF16, then
+//                          ready[t] released (one add per epilogue warp);
+//   consumer (warps 6-11)  CTA (sp, g) owns the 256-column slice pair sp of Z
+//                          for the whole pass (two M = 128 accumulators in
+//                          TMEM) and consumes the tiles t = g, g + Sg, ...: it
+//                          acquires ready[t] and reads X_t[:, pair] and Y_t --
+//                          X_t was loaded by its producer moments earlier, so
+//                          the re-read hits L2 -- then counts consumed[t].
+// A producer starts tile t only when tile t - window has been consumed by all
+// Dt2 slice-pair owners (a guard against runaway, set above the producer
+// count).  All waits are bounded (kDevWaitTimeout).
+struct FusedHeader {
+    uint64_t pfull[kMaxStages], pempty[kMaxStages], ptfull[2], ptempty[2];
+    uint64_t cfull[kMaxStages], cempty[kMaxStages], ctfull, ctempty;
+    uint32_t tmem_base;
+    int abort;
+};
+
+constexpr int kFusedThreads = 384;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+    xpass_fused_kernel(const __grid_constant__ CUtensorMap tmXa, const __grid_constant__ CUtensorMap tmV,
+                       const __grid_constant__ CUtensorMap tmXb, const __grid_constant__ CUtensorMap tmY, int ntiles,
+                       int nk, int Dt2, int Sg, int NP, int window, int flush_tiles, int m_pad, int p_stages,
+                       int c_stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, float* __restrict__ Zacc,
+                       int* __restrict__ ready, int* __restrict__ consumed, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t p_a = 128u * 128u;            // 128 rows x 64 columns
+    const uint32_t c_a = 4u * 64u * 128u;        // 64 rows x 256 columns, four 64-column boxes
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t p_stage = p_a + b_piece, c_stage = c_a + b_piece;
+    uint8_t* ptiles = tiles;
+    uint8_t* ctiles = tiles + (size_t)p_stages * p_stage;
+    FusedHeader* hd = reinterpret_cast<FusedHeader*>(ctiles + (size_t)c_stages * c_stage);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < p_stages; ++i) {
+            tc::mbar_init(&hd->pfull[i], 1);
+            tc::mbar_init(&hd->pempty[i], 1);
+        }
+        for (int i = 0; i < c_stages; ++i) {
+            tc::mbar_init(&hd->cfull[i], 1);
+            tc::mbar_init(&hd->cempty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&hd->ptfull[i], 1);
+            tc::mbar_init(&hd->ptempty[i], 128);
+        }
+        tc::mbar_init(&hd->ctfull, 1);
+        tc::mbar_init(&hd->ctempty, 128);
+        hd->abort = 0;
+        tc::mbar_init_fence();
+        tc::tma_prefetch(&tmXa);
+        tc::tma_prefetch(&tmV);
+        tc::tma_prefetch(&tmXb);
+        tc::tma_prefetch(&tmY);
+    }
+    if (warp == 1) tc::tmem_alloc(&hd->tmem_base, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = hd->tmem_base;
+    const uint32_t ptmem = tmem, ctmem = tmem + 2u * (uint32_t)m_pad;
+    const bool producer = (int)blockIdx.x < NP;
+    const int task = blockIdx.x;
+    const bool consumer = task < Dt2 * Sg;
+    const int sp = consumer ? task % Dt2 : 0, cg = consumer ? task / Dt2 : 0;
+    volatile int* abort_flag = &hd->abort;
+
+    if (warp == 0) {
+        // ---------------- producer TMA
+        if (lane == 0 && producer) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += NP) {
+                if (t >= window && !tc::wait_flag_geq(consumed + (t - window), Dt2, status)) {
+                    *abort_flag = 1;
+                    break;
+                }
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % p_stages, ph = (it / p_stages) & 1u;
+                    if (!tc::mbar_wait(&hd->pempty[s], ph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->pfull[s], p_stage);
+                    uint8_t* st = ptiles + (size_t)s * p_stage;
+                    tc::tma_load_2d(st, &tmXa, &hd->pfull[s], k * kBK, t * 128);
+                    tc::tma_load_2d(st + p_a, &tmV, &hd->pfull[s], k * kBK, 0);
+                }
+            }
+            const uint32_t first = it > (uint32_t)p_stages ? it - (uint32_t)p_stages : 0u;
+            if (*abort_flag)
+                for (uint32_t j = first; j < it; ++j)
+                    tc::mbar_wait(&hd->pfull[j % p_stages], (j / p_stages) & 1u, status, 100000000ull);
+        }
+    } else if (warp == 1) {
+        // ---------------- producer MMA
+        if (lane == 0 && producer) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
+            uint32_t it = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += NP, ++tl) {
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->ptempty[b], tph ^ 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = ptmem + b * (uint32_t)m_pad;
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % p_stages, ph = (it / p_stages) & 1u;
+                    if (!tc::mbar_wait(&hd->pfull[s], ph, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(ptiles + (size_t)s * p_stage);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 32, 16, 1024);
+                        const uint64_t bdesc = tc::smem_desc_sw128(a_addr + p_a + kk * 32, 16, 1024);
+                        tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k | kk) != 0);
+                    }
+                    tc::mma_commit(&hd->pempty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->ptfull[b]);
+            }
+        }
+    } else if (warp < 6) {
+        // ---------------- producer epilogue: Y_t -> BF16, then release ready[t]
+        if (producer) {
+            const int q = warp & 3;
+            uint32_t tl = 0;
+            for (int t = blockIdx.x; t < ntiles; t += NP, ++tl) {
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->ptfull[b], tph, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(ptmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        Yt[(int64_t)(c0 + j) * ldy + row] = __float2bfloat16_rn(__uint_as_float(r[j]));
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->ptempty[b]);
+                // publish: every lane fences its stores, the warp syncs, and one
+                // lane adds a release to ready[t]; consumers wait for all 4 warps
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) tc::red_release_add_gpu(ready + t, 1);
+            }
+        }
+    } else if (warp == 6) {
+        // ---------------- consumer TMA
+        if (lane == 0 && consumer) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = cg; t < ntiles && ok; t += Sg) {
+                if (!tc::wait_flag_geq(ready + t, 4, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_proxy_async_global();
+                for (int kk2 = 0; kk2 < 2; ++kk2, ++it) {
+                    const uint32_t s = it % c_stages, ph = (it / c_stages) & 1u;
+                    if (!tc::mbar_wait(&hd->cempty[s], ph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->cfull[s], c_stage);
+                    uint8_t* st = ctiles + (size_t)s * c_stage;
+                    const int y = t * 128 + kk2 * 64;
+#pragma unroll
+                    for (int bx = 0; bx < 4; ++bx)
+                        tc::tma_load_2d(st + bx * 8192, &tmXb, &hd->cfull[s], sp * 256 + bx * 64, y);
+                    tc::tma_load_2d(st + c_a, &tmY, &hd->cfull[s], y, 0);
+                }
+            }
+            const uint32_t first = it > (uint32_t)c_stages ? it - (uint32_t)c_stages : 0u;
+            if (*abort_flag)
+                for (uint32_t j = first; j < it; ++j)
+                    tc::mbar_wait(&hd->cfull[j % c_stages], (j / c_stages) & 1u, status, 100000000ull);
+        }
+    } else if (warp == 7) {
+        // ---------------- consumer MMA: Z[pair] accumulates across tiles, two M = 128 halves
+        if (lane == 0 && consumer) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, true, false);
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            int t = cg;
+            while (t < ntiles && ok) {
+                if (!tc::mbar_wait(&hd->ctempty, (fb & 1u) ^ 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int nt = 0; nt < flush_tiles && t < ntiles && ok; ++nt, t += Sg) {
+                    for (int kk2 = 0; kk2 < 2; ++kk2, ++it) {
+                        const uint32_t s = it % c_stages, ph = (it / c_stages) & 1u;
+                        if (!tc::mbar_wait(&hd->cfull[s], ph, status) || *abort_flag) {
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a_addr = tc::smem_u32(ctiles + (size_t)s * c_stage);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint64_t bdesc = tc::smem_desc_sw128(a_addr + c_a + kk * 32, 16, 1024);
+#pragma unroll
+                            for (int hh = 0; hh < 2; ++hh) {
+                                const uint64_t adesc =
+                                    tc::smem_desc_sw128(a_addr + hh * 16384 + kk * 2048, 8192, 1024);
+                                tc::mma_f16(ctmem + hh * (uint32_t)m_pad, adesc, bdesc, idesc, (nt | kk2 | kk) != 0);
+                            }
+                        }
+                        tc::mma_commit(&hd->cempty[s]);
+                    }
+                    if (ok) atomicAdd(consumed + t, 1);     // tile t's column pair has been read
+                }
+                if (ok) tc::mma_commit(&hd->ctfull);
+                ++fb;
+            }
+        }
+    } else {
+        // ---------------- consumer epilogue: fold the block sums into the double-float partials
+        if (consumer) {
+            const int q = warp & 3;
+            uint32_t fb = 0;
+            for (int t = cg; t < ntiles; t += Sg * flush_tiles, ++fb) {
+                if (!tc::mbar_wait(&hd->ctfull, fb & 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int64_t j = (int64_t)sp * 256 + hh * 128 + q * 32 + lane;
+                    float* z = Zacc + (((int64_t)cg * Dt2 * 256 + j) * m_pad) * 2;
+                    for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(ctmem + ((uint32_t)(q * 32) << 16) + hh * (uint32_t)m_pad + (uint32_t)c0, r);
+                        tc::tmem_ld_wait();
+                        float2* zz = reinterpret_cast<float2*>(z) + c0;
+                        if (fb == 0) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) zz[jj] = make_float2(__uint_as_float(r[jj]), 0.f);
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) {
+                                float2 v = zz[jj];
+                                df_add(v.x, v.y, __uint_as_float(r[jj]));
+                                zz[jj] = v;
+                            }
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->ctempty);
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, 512);
+    }
+}
+
 // V (d x m column-major FP32) -> S BF16 pieces, [S][m_pad][ldv], zero padded.
 template <int S>
 __global__ void split_v_kernel(const float* __restrict__ V, int64_t d, int m, int m_pad, int64_t ldv,
@@ -412,7 +697,7 @@ inline int m_pad_of(int m) { return (int)round_up(m, 32); }
 struct Layout {
     int64_t ldv, ldy, rows_pad_max;
     int m_pad, Dt;
-    size_t vp_bytes, yt_bytes, z_bytes;
+    size_t vp_bytes, yt_bytes, z_bytes, flag_bytes;
 };
 
 Layout layout_of(int64_t n, int64_t d, int m, int num_sms) {
@@ -423,84 +708,151 @@ Layout layout_of(int64_t n, int64_t d, int m, int num_sms) {
     L.Dt = (int)((d + 127) / 128);
     L.vp_bytes = (size_t)3 * L.m_pad * L.ldv * 2;
     L.yt_bytes = (size_t)3 * L.m_pad * L.rows_pad_max * 2;
-    L.z_bytes = (size_t)(num_sms + L.Dt) * 128 * L.m_pad * 8;
+    L.z_bytes = (size_t)(2 * num_sms + L.Dt + 2) * 128 * L.m_pad * 8;
+    L.flag_bytes = (size_t)2 * (L.rows_pad_max / 128 + 1) * sizeof(int);
     (void)m;
     return L;
 }
 
+struct PassShape {
+    int64_t d, rows, ldv, ldy;
+    int m_pad, Dt, ntiles, nk;
+};
+
 template <int S>
-cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
-                     const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
-    const int64_t d = x.d, rows = r1 - r0;
-    const int m_pad = m_pad_of(m);
-    const int64_t ldv = round_up(d, 8);
-    const int64_t ldy = round_up(rows, 128);
-    const int Dt = (int)((d + 127) / 128);
+cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, const TcPassScratch& sc,
+                         PassShape& ps, CUtensorMap& tmXa, CUtensorMap& tmXb, CUtensorMap& tmV, CUtensorMap& tmY,
+                         cudaStream_t st) {
+    ps.d = x.d;
+    ps.rows = r1 - r0;
+    ps.m_pad = m_pad_of(m);
+    ps.ldv = round_up(ps.d, 8);
+    ps.ldy = round_up(ps.rows, 128);
+    ps.Dt = (int)((ps.d + 127) / 128);
+    ps.ntiles = (int)(ps.ldy / 128);
+    ps.nk = (int)((ps.d + kBK - 1) / kBK);
     __nv_bfloat16* Vp = static_cast<__nv_bfloat16*>(sc.vp);
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
-    float* Zacc = static_cast<float*>(sc.zacc);
-
-    // V -> BF16 pieces
     {
-        const int64_t total = (int64_t)m_pad * ldv;
+        const int64_t total = (int64_t)ps.m_pad * ps.ldv;
         int blocks = (int)((total + 255) / 256);
         if (blocks > 4096) blocks = 4096;
         note_launch();
-        split_v_kernel<S><<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv, Vp);
+        split_v_kernel<S><<<blocks, 256, 0, st>>>(V, ps.d, m, ps.m_pad, ps.ldv, Vp);
     }
     const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * 2;
-    CUtensorMap tmXa, tmXb, tmV, tmY;
-    if (!encode_bf16_2d(&tmXa, xbase, d, rows, x.ld * 2, 64, 128) ||
-        !encode_bf16_2d(&tmXb, xbase, d, rows, x.ld * 2, 64, 64) ||
-        !encode_bf16_2d(&tmV, Vp, d, (uint64_t)S * m_pad, ldv * 2, 64, m_pad) ||
-        !encode_bf16_2d(&tmY, Yt, ldy, (uint64_t)S * m_pad, ldy * 2, 64, m_pad))
+    if (!encode_bf16_2d(&tmXa, xbase, ps.d, ps.rows, x.ld * 2, 64, 128) ||
+        !encode_bf16_2d(&tmXb, xbase, ps.d, ps.rows, x.ld * 2, 64, 64) ||
+        !encode_bf16_2d(&tmV, Vp, ps.d, (uint64_t)S * ps.m_pad, ps.ldv * 2, 64, ps.m_pad) ||
+        !encode_bf16_2d(&tmY, Yt, ps.ldy, (uint64_t)S * ps.m_pad, ps.ldy * 2, 64, ps.m_pad))
         return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
-    // Y = X V
+cudaError_t launch_zreduce(const float* Zacc, int Sg, int Dt, int64_t d, int m, int m_pad, float* Z, cudaStream_t st) {
+    const int64_t total = d * m;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    note_launch();
+    zreduce_kernel<<<blocks, 256, 0, st>>>(Zacc, Sg, Dt, d, m, m_pad, Z);
+    return cudaGetLastError();
+}
+
+// Two GEMM kernels: Y = X V, then Z = X^T Y (X is read twice).
+template <int S>
+cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
+                     const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+    PassShape ps;
+    CUtensorMap tmXa, tmXb, tmV, tmY;
+    cudaError_t e = prepare_pass<S>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
+    if (e != cudaSuccess) return e;
+    __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
+    float* Zacc = static_cast<float*>(sc.zacc);
     {
-        const uint32_t stage_bytes = 128u * 128u + S * (uint32_t)m_pad * 128u;
+        const uint32_t stage_bytes = 128u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        cudaError_t e = cudaFuncSetAttribute(xv_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(xv_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int ntiles = (int)(ldy / 128);
-        const int nk = (int)((d + kBK - 1) / kBK);
-        const int grid = ntiles < num_sms ? ntiles : num_sms;
+        const int grid = ps.ntiles < num_sms ? ps.ntiles : num_sms;
         note_launch();
-        xv_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXa, tmV, ntiles, nk, m_pad, stages, Yt, ldy, status);
+        xv_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXa, tmV, ps.ntiles, ps.nk, ps.m_pad, stages, Yt, ps.ldy,
+                                                       status);
     }
-    // Z = X^T Y
     int Sg;
     {
-        const uint32_t stage_bytes = 2u * 64u * 128u + S * (uint32_t)m_pad * 128u;
+        const uint32_t stage_bytes = 2u * 64u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        cudaError_t e = cudaFuncSetAttribute(xty_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(xty_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int kst = (int)(ldy / kBK);
-        Sg = Dt >= num_sms ? 1 : num_sms / Dt;
+        const int kst = (int)(ps.ldy / kBK);
+        Sg = ps.Dt >= num_sms ? 1 : num_sms / ps.Dt;
         if (Sg > kst) Sg = kst;
         if (Sg < 1) Sg = 1;
-        const int ntask = Dt * Sg;
+        const int ntask = ps.Dt * Sg;
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
-        xty_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXb, tmY, Dt, Sg, kst, flush, m_pad, stages, Zacc, status);
+        xty_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXb, tmY, ps.Dt, Sg, kst, flush, ps.m_pad, stages, Zacc,
+                                                        status);
     }
-    {
-        const int64_t total = d * m;
-        int blocks = (int)((total + 255) / 256);
-        if (blocks > 8192) blocks = 8192;
-        note_launch();
-        zreduce_kernel<<<blocks, 256, 0, st>>>(Zacc, Sg, Dt, d, m, m_pad, Z);
-    }
-    return cudaGetLastError();
+    return launch_zreduce(Zacc, Sg, ps.Dt, ps.d, m, ps.m_pad, Z, st);
+}
+
+// Fused single-read pass (one piece, BF16): see xpass_fused_kernel.
+cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
+                      const TcPassScratch& sc, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
+    PassShape ps;
+    CUtensorMap tmXa, tmXb, tmV, tmY;
+    cudaError_t e = prepare_pass<1>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
+    if (e != cudaSuccess) return e;
+    const int Dt2 = (ps.Dt + 1) / 2;
+    int Sg = num_sms / Dt2;
+    if (Sg > ps.ntiles) Sg = ps.ntiles;
+    int NP = sched.producers > 0 ? sched.producers : num_sms;
+    if (NP > num_sms) NP = num_sms;
+    if (NP > ps.ntiles) NP = ps.ntiles;
+    int window = sched.window > 0 ? sched.window : NP + 4 * Sg;
+    if (window < 1) window = 1;
+    const int grid = NP > Dt2 * Sg ? NP : Dt2 * Sg;
+    const uint32_t b_piece = (uint32_t)ps.m_pad * 128u;
+    const uint32_t p_stage = 128u * 128u + b_piece, c_stage = 4u * 64u * 128u + b_piece;
+    const int c_stages = 2;
+    int p_stages = (int)((kSmemBudget - 2048 - c_stages * c_stage) / p_stage);
+    if (p_stages > kMaxStages) p_stages = kMaxStages;
+    if (p_stages < 2) return cudaErrorInvalidValue;
+    const size_t smem =
+        1024 + (size_t)p_stages * p_stage + (size_t)c_stages * c_stage + sizeof(FusedHeader);
+    e = cudaFuncSetAttribute(xpass_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int* ready = sc.flags;
+    int* consumed = sc.flags + ps.ntiles + 1;
+    e = cudaMemsetAsync(sc.flags, 0, (size_t)2 * (ps.ntiles + 1) * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int flush_tiles = 64;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kFusedThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    note_launch();
+    e = cudaLaunchKernelEx(&cfg, xpass_fused_kernel, tmXa, tmV, tmXb, tmY, ps.ntiles, ps.nk, Dt2, Sg, NP, window,
+                           flush_tiles, ps.m_pad, p_stages, c_stages, static_cast<__nv_bfloat16*>(sc.yt), ps.ldy,
+                           static_cast<float*>(sc.zacc), ready, consumed, status);
+    if (e != cudaSuccess) return e;
+    return launch_zreduce(static_cast<float*>(sc.zacc), Sg, 2 * Dt2, ps.d, m, ps.m_pad, Z, st);
 }
 
 }  // namespace
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms) {
     const Layout L = layout_of(n, d, m, num_sms);
-    return L.vp_bytes + L.yt_bytes + L.z_bytes + 3 * 256;
+    return L.vp_bytes + L.yt_bytes + L.z_bytes + L.flag_bytes + 4 * 256;
 }
 
 TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int num_sms) {
@@ -513,6 +865,8 @@ TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int
     s.yt = p;
     p += al(L.yt_bytes);
     s.zacc = p;
+    p += al(L.z_bytes);
+    s.flags = reinterpret_cast<int*>(p);
     return s;
 }
 
@@ -521,9 +875,14 @@ bool tc_pass_supported(const XView& x, int m) {
 }
 
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
-                     const TcPassScratch& s, int* status, int num_sms, cudaStream_t st) {
+                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
     if (r1 <= r0) return cudaErrorInvalidValue;
     if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
+    // The fused pass needs every 128-column slice of d owned by a resident CTA.
+    const int Dt = (int)((x.d + 127) / 128);
+    const bool can_fuse = (Dt + 1) / 2 <= num_sms && (r1 - r0) >= 128 * 4;
+    const bool fuse = sched.fused != 0 && can_fuse;
+    if (fuse) return run_fused(x, V, m, r0, r1, Z, s, sched, status, num_sms, st);
     return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
 }
 

@@ -9,12 +9,20 @@ struct TcPassScratch {
     void* vp = nullptr;     // V pieces, [3][128][round_up(d, 8)] BF16
     void* yt = nullptr;     // Y^T pieces, [3][128][round_up(n, 128)] BF16
     void* zacc = nullptr;   // double-float Z partials, [row group][d slice * 128][128] x 2 FP32
+    int* flags = nullptr;   // fused pass: ready[tiles], consumed[tiles]
+};
+
+// Schedule of the fast (one-piece) pass; zero fields mean "library choice".
+struct TcSchedule {
+    int fused = -1;         // 1: fused single-read kernel, 0: two GEMM kernels, -1: choose
+    int producers = 0;      // CTAs running the Y = X V pipeline in the fused kernel
+    int window = 0;         // tiles a producer may run ahead of the slowest consumer
 };
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms);
 TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int num_sms);
 bool tc_pass_supported(const XView& x, int m);
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
-                     const TcPassScratch& s, int* status, int num_sms, cudaStream_t st);
+                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st);
 
 }  // namespace ppca

@@ -90,6 +90,41 @@ def test_xpass_bf16(P, n, d, m, r0, r1, prec, tol):
         assert normwise(Zg[:, c], Zref[:, c]) <= 4 * tol
 
 
+FUSED_CASES = [
+    # n, d, m, r0, r1, producers, window
+    (3001, 512, 64, 0, 3001, 0, 0),
+    (5000, 1024, 128, 0, 5000, 0, 0),
+    (600000, 64, 16, 0, 600000, 0, 0),      # d = 64: one slice, 152 row groups
+    (4096, 4096, 128, 0, 4096, 0, 0),       # 32 slices x 4 row groups, one tile each
+    (70000, 2048, 96, 5, 69000, 13, 5),     # few producers, short window: throttling
+    (9000, 200, 33, 100, 8999, 3, 1),
+]
+
+
+@pytest.mark.parametrize("n,d,m,r0,r1,producers,window", FUSED_CASES)
+def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window):
+    X = np.random.default_rng(n + d).standard_normal((n, d)) * (0.97 ** np.arange(1, d + 1))[None, :] ** 0.5
+    Xd = dev_matrix(X, "bf16")
+    V = synth.initial_basis(d, m, seed=4)
+    Vd = dev_basis(V)
+    Zf, Zu = empty_basis(d, m), empty_basis(d, m)
+    h = P.ppca_create(Xd)
+    P.ppca_set_schedule(h, fused=1, producers=producers, window=window)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zf, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    P.ppca_set_schedule(h, fused=0)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zu, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)[r0:r1]
+    Zref = Xs.T @ (Xs @ host_basis(Vd))
+    Zg = host_basis(Zf)
+    assert normwise(Zg, Zref) <= 1e-2
+    for c in range(m):
+        assert normwise(Zg[:, c], Zref[:, c]) <= 4e-2
+    # same Y rounding as the two-kernel pass: only the FP32 summation order differs
+    assert normwise(Zg, host_basis(Zu)) <= 1e-5
+
+
 @pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (4096, 128)])
 def test_cholesky_qr2_matches_thin_qr(P, d, m):
     V = synth.initial_basis(d, m, seed=d)
