@@ -41,6 +41,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the per-step measurements")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--rows", type=int, default=0,
                     help="override n with a smaller row count (for profiler captures of a small case)")
@@ -161,6 +162,142 @@ def run_cpu_leg(workload: str, rows: int, passes: int):
 
 # --------------------------------------------------------------------------- GPU arm
 
+def _events_ms(fn, reps, stream):
+    """Mean device time of fn() over reps calls (CUDA events on `stream`), after one warm-up call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def measure_rows(peaks):
+    """Each step of the hot path timed alone on the shape of the workload it belongs to."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    stream = torch.cuda.current_stream()
+    rows = {}
+    hbm = peaks["hbm_gbs"]
+    # FP32 data, 1e5 x 1024, m = 64 (the three-primer workload)
+    cfg = synth.CONFIGS["primers_fp32_100000x1024"]
+    n, d, m = cfg.n, cfg.d, cfg.m
+    X, _ = synth.gaussian_data_torch(n, d, cfg.lam(), cfg.seed, "cuda", torch.float32)
+    V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, cfg.seed).T, dtype=np.float32)).cuda()
+    Z = torch.empty_like(V0)
+    h = P.ppca_create(X, stream=stream)
+    ms = _events_ms(lambda: P.ppca_xpass(h, V0, m, 0, n, Z, P.PPCA_PREC_ACCURATE), 5, stream)
+    rows["xpass_fp32_100000x1024_m64"] = {"ms": round(ms, 4), "gbs": round(n * d * 4 / ms / 1e6, 1),
+                                          "frac_hbm": round(n * d * 4 / ms / 1e6 / hbm, 4),
+                                          "kernel": "CUDA-core FP32 (pass_simt)"}
+    ms = _events_ms(lambda: P.ppca_prime(h, P.PPCA_POWER, m, 1, None, V0=V0), 5, stream)
+    rows["power_iteration_fp32_100000x1024_m64"] = {"ms": round(ms, 4), "note": "orth(V0) + one pass + CholeskyQR2"}
+    oja = P.ppca_prime_params_default(P.PPCA_OJA)
+    steps = 50
+    ms = _events_ms(lambda: P.ppca_prime(h, P.PPCA_OJA, m, steps, oja, V0=V0), 2, stream)
+    rows["oja_step_fp32_b256"] = {"us_per_step": round(ms * 1e3 / steps, 2), "batch": 256}
+    eg = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
+    ms = _events_ms(lambda: P.ppca_prime(h, P.PPCA_EIGENGAME, m, steps, eg, V0=V0), 2, stream)
+    rows["eigengame_step_fp32_b1024"] = {"us_per_step": round(ms * 1e3 / steps, 2), "batch": 1024}
+    Eo = torch.empty((cfg.k, d), dtype=torch.float32, device="cuda")
+    lo = torch.empty(cfg.k, dtype=torch.float64, device="cuda")
+    P.ppca_prime(h, P.PPCA_POWER, m, 2, None, V0=V0)
+    ms = _events_ms(lambda: P.ppca_finalize(h, cfg.k, Eo, lo, P.PPCA_PREC_ACCURATE), 3, stream)
+    rows["finalize_fp32_100000x1024_m64"] = {"ms": round(ms, 4)}
+    Xb = torch.empty((n, d), dtype=torch.bfloat16, device="cuda")
+    ms = _events_ms(lambda: P.ppca_quantize_bf16(X, Xb, stream), 5, stream)
+    rows["quantize_bf16"] = {"gbs": round(n * d * 6 / ms / 1e6, 1), "frac_hbm": round(n * d * 6 / ms / 1e6 / hbm, 4)}
+    Xq = torch.empty((n, d), dtype=torch.uint8, device="cuda")
+    sc = torch.empty(n, dtype=torch.float32, device="cuda")
+    ms = _events_ms(lambda: P.ppca_quantize_fp8(X, Xq, sc, stream), 5, stream)
+    rows["quantize_fp8"] = {"gbs": round(n * (d * 5 + 4) / ms / 1e6, 1),
+                            "frac_hbm": round(n * (d * 5 + 4) / ms / 1e6 / hbm, 4)}
+    P.ppca_sync(h)
+    del X, Xb, Xq, h
+    # small m x m work at m = 128 (the 1e6 x 4096 workload)
+    d, m = 4096, 128
+    Xs = torch.zeros((2, d), dtype=torch.float32, device="cuda")
+    h = P.ppca_create(Xs, stream=stream)
+    V = torch.randn((m, d), device="cuda")
+    Q = torch.empty_like(V)
+    ms = _events_ms(lambda: P.ppca_orthonormalize(h, V, Q, m), 5, stream)
+    rows["cholesky_qr2_4096x128"] = {"ms": round(ms, 4)}
+    G = torch.randn((m, m), dtype=torch.float64, device="cuda")
+    G = G @ G.T + m * torch.eye(m, dtype=torch.float64, device="cuda")
+    w = torch.empty(m, dtype=torch.float64, device="cuda")
+    U = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    ms = _events_ms(lambda: P.ppca_eigh(h, G, m, w, U), 3, stream)
+    rows["eigh_jacobi_m128_dense"] = {"ms": round(ms, 4)}
+    P.ppca_sync(h)
+    return rows
+
+
+def run_batch(args):
+    """The ragged batch workload: 512 independent problems, one graph launch per step."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    cfg = synth.CONFIGS[args.workload]
+    T = cfg.primers["power"]["T"]
+    shapes = synth.batch_instances(512, cfg.seed + 1000 * rank)
+    if args.rows:
+        shapes = shapes[:args.rows]
+    inst = []
+    total_bytes = 0
+    for s in shapes:
+        n, d, k, m = s["n"], s["d"], s["k"], s["m"]
+        X = synth.instance_data_torch(n, d, s["rho"] ** np.arange(1, d + 1), s["seed"], "cuda", torch.float32)
+        V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, s["seed"]).T, dtype=np.float32)).cuda()
+        inst.append({"X": X, "k": k, "m": m, "T": T, "V0": V0,
+                     "E": torch.empty((k, d), dtype=torch.float32, device="cuda"),
+                     "lam": torch.empty(k, dtype=torch.float64, device="cuda")})
+        total_bytes += (T + 1) * n * d * 4
+    stream = torch.cuda.current_stream()
+    b = P.ppca_batch_create(inst, slots=8, stream=stream)
+    for _ in range(max(args.warmup, 1)):
+        P.ppca_batch_run(b)
+    P.ppca_batch_sync(b)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        P.ppca_batch_run(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    P.ppca_batch_sync(b)
+    ms = e0.elapsed_time(e1)
+    peaks, peak_kind = measured_peaks()
+    value = total_bytes * args.steps / (ms / 1e3) / 1e9
+    line = {"metric": "X-pass HBM GB/s; time to LCES=k (BF16 vs FP32, same GPU, angle tol)",
+            "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": 8,
+                       "bytes_per_step": total_bytes, "form": "one CUDA-graph launch per step",
+                       "l2": "inputs (142 GB) larger than L2, no flush"},
+            "roofline": {"bound": "hbm", "achieved": round(value, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(value / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": peak_kind,
+                         "kernel": "whole batch step (FP32 CUDA-core X-passes dominate)"},
+            "clocks": clk, "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -269,6 +406,12 @@ def run_ours(args):
                "ms_per_step": round(dt * 1e3, 3)}
         del Xh
 
+    row_times = None
+    if rank == 0 and not args.no_rows:
+        del X
+        torch.cuda.empty_cache()
+        row_times = measure_rows(peaks)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         out, cores, err = run_cpu_leg(args.workload, args.cpu_rows, args.cpu_passes)
@@ -291,6 +434,7 @@ def run_ours(args):
                        "l2": f"inputs ({bytes_per_pass / 1e9:.1f} GB) larger than L2, no flush"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": tm.launches,
+            "rows": row_times,
         }
         print(json.dumps(line))
     if dist:
@@ -344,6 +488,8 @@ def main(argv=None):
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("batch"):
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -231,6 +231,51 @@ PPCA_API ppca_status ppca_set_state(ppca_handle *h, const void *buf, int64_t byt
 PPCA_API ppca_status ppca_destroy(ppca_handle *h);
 
 /* ---------------------------------------------------------------------------
+ * Batches: many independent primed-PCA problems of uneven size (each one
+ * Algorithm 1 with block power priming), run as a single CUDA-graph launch.
+ * ------------------------------------------------------------------------- */
+
+typedef struct ppca_instance_desc {
+    const void *X;            /* device, n x d row-major, leading dimension ld (as in ppca_create) */
+    int64_t n, d, ld;
+    int32_t dtype;            /* ppca_dtype                                                      */
+    int32_t k;                /* components returned, 1 <= k <= m                                */
+    int32_t m;                /* k + l, 1 <= m <= min(d, n - 1, 128)                             */
+    int32_t T;                /* power iterations of the priming, >= 0                           */
+    const float *row_scales;  /* FP8 only, else NULL                                             */
+    const float *V0;          /* device d x m starting basis, or NULL: drawn from `seed`         */
+    uint64_t seed;
+    float *E;                 /* device output, d x k column-major                               */
+    double *lambda;           /* device output, k eigenvalues / n, descending                    */
+    float *V_out;             /* device output d x m, the primed basis (optional, NULL = none)   */
+} ppca_instance_desc;
+
+typedef struct ppca_batch ppca_batch;
+
+/*
+ * Validate `count` instance descriptors (copied; the buffers they point to are
+ * borrowed and must stay valid) and set up `slots` concurrent slots (0 = 8),
+ * each with a workspace sized for the largest instance it runs.  No device
+ * work is enqueued.
+ */
+PPCA_API ppca_status ppca_batch_create(ppca_batch **out, const ppca_instance_desc *descs, int32_t count,
+                                       int32_t slots, void *stream);
+
+/*
+ * Run every instance: block power priming (T iterations, FAST precision)
+ * then the pPCA step (ACCURATE), writing each instance's E and lambda.  The
+ * first call captures the whole batch -- instances spread round-robin over
+ * the slots' streams -- into a CUDA graph; every call launches that graph on
+ * the batch's stream (asynchronous).
+ */
+PPCA_API ppca_status ppca_batch_run(ppca_batch *b);
+
+/* Wait for the batch's stream; report the first device-side error of any slot. */
+PPCA_API ppca_status ppca_batch_sync(ppca_batch *b);
+
+PPCA_API ppca_status ppca_batch_destroy(ppca_batch *b);
+
+/* ---------------------------------------------------------------------------
  * Individual steps of the hot path.
  * ------------------------------------------------------------------------- */
 

@@ -24,7 +24,8 @@ __all__ = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "EXPORTED_SYMBOLS",
+    "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
+    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,6 +45,7 @@ EXPORTED_SYMBOLS = [
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_eigh_noalloc", "ppca_set_schedule",
+    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy",
 ]
 
 
@@ -86,6 +88,25 @@ class ppca_schedule(ctypes.Structure):
     ]
 
 
+class ppca_instance_desc(ctypes.Structure):
+    _fields_ = [
+        ("X", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("d", ctypes.c_int64),
+        ("ld", ctypes.c_int64),
+        ("dtype", ctypes.c_int32),
+        ("k", ctypes.c_int32),
+        ("m", ctypes.c_int32),
+        ("T", ctypes.c_int32),
+        ("row_scales", ctypes.c_void_p),
+        ("V0", ctypes.c_void_p),
+        ("seed", ctypes.c_uint64),
+        ("E", ctypes.c_void_p),
+        ("lambda_", ctypes.c_void_p),
+        ("V_out", ctypes.c_void_p),
+    ]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -116,6 +137,10 @@ _SIGS = {
     "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
     "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "ppca_set_schedule": (_c_status, [_vp, ctypes.POINTER(ppca_schedule)]),
+    "ppca_batch_create": (_c_status, [ctypes.POINTER(_vp), ctypes.POINTER(ppca_instance_desc), _i32, _i32, _vp]),
+    "ppca_batch_run": (_c_status, [_vp]),
+    "ppca_batch_sync": (_c_status, [_vp]),
+    "ppca_batch_destroy": (_c_status, [_vp]),
 }
 
 
@@ -291,6 +316,61 @@ def ppca_orthonormalize(h: Handle, V, Q, m: int):
 
 def ppca_eigh(h: Handle, G, m: int, w, U):
     _check(load_library().ppca_eigh(h.ptr, _ptr(G), m, _ptr(w), _ptr(U)), "ppca_eigh")
+
+
+class Batch:
+    """Owns a ppca_batch* and keeps the instances' tensors alive."""
+
+    def __init__(self, ptr: int, keep: list):
+        self.ptr = ptr
+        self._keep = keep
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                load_library().ppca_batch_destroy(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def ppca_batch_create(instances, slots: int = 0, stream=None) -> Batch:
+    """instances: list of dicts with X (CUDA tensor), k, m, T, E ((k, d) tensor), lam ((k,) float64 tensor),
+    optional V0 ((m, d) tensor), seed, row_scales."""
+    arr = (ppca_instance_desc * len(instances))()
+    keep = []
+    for i, ins in enumerate(instances):
+        X = ins["X"]
+        arr[i].X = _ptr(X)
+        arr[i].n, arr[i].d = X.shape
+        arr[i].ld = X.stride(0)
+        arr[i].dtype = _dtype_code(X)
+        arr[i].k, arr[i].m, arr[i].T = ins["k"], ins["m"], ins["T"]
+        arr[i].row_scales = _ptr(ins.get("row_scales"))
+        arr[i].V0 = _ptr(ins.get("V0"))
+        arr[i].seed = ins.get("seed", 0)
+        arr[i].E = _ptr(ins["E"])
+        arr[i].lambda_ = _ptr(ins["lam"])
+        arr[i].V_out = _ptr(ins.get("V_out"))
+        keep.append(ins)
+    out = ctypes.c_void_p()
+    _check(load_library().ppca_batch_create(ctypes.byref(out), arr, len(instances), slots, _stream_ptr(stream)),
+           "ppca_batch_create")
+    return Batch(out.value, keep)
+
+
+def ppca_batch_run(b: Batch):
+    _check(load_library().ppca_batch_run(b.ptr), "ppca_batch_run")
+
+
+def ppca_batch_sync(b: Batch):
+    _check(load_library().ppca_batch_sync(b.ptr), "ppca_batch_sync")
+
+
+def ppca_batch_destroy(b: Batch):
+    if b.ptr:
+        _check(load_library().ppca_batch_destroy(b.ptr), "ppca_batch_destroy")
+        b.ptr = None
 
 
 def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0):

@@ -108,9 +108,10 @@ struct ppca_handle {
 
 namespace {
 
-ppca_status ensure_workspace(ppca_handle* h, int m) {
+// Workspace for problems up to n x d with up to m directions (a batch slot
+// sizes it for the largest instance it runs).
+ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     if (h->ws && h->ws_m >= m) return PPCA_OK;
-    const int64_t d = h->x.d, n = h->x.n;
     const size_t dm = al256((size_t)d * m * sizeof(float));
     const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
     size_t need = 5 * dm + al256((size_t)m * m * 8) + al256((size_t)m * m * 4) + al256((size_t)m * 8) +
@@ -151,9 +152,13 @@ ppca_status ensure_workspace(ppca_handle* h, int m) {
     h->simt.nsplit = nsplit;
     h->simt.Y = reinterpret_cast<float*>(take(simt_pass_scratch_floats(n, d, m, nsplit) * 4));
     h->simt.Zpart = h->simt.Y + (size_t)n * m;
+    h->simt.zpart_floats = (int64_t)nsplit * d * m * 2;
+    h->simt.num_sms = h->num_sms;
     h->tc = tc_pass_scratch_carve(take(tc_pass_scratch_bytes(n, d, m, h->num_sms)), n, d, m, h->num_sms);
     return PPCA_OK;
 }
+
+ppca_status ensure_workspace(ppca_handle* h, int m) { return ensure_workspace_dims(h, h->x.n, h->x.d, m); }
 
 ppca_status validate_x(const void* X, int64_t n, int64_t d, int64_t ld, ppca_dtype dt, const float* scales) {
     if (!X) return fail(PPCA_ERR_INVALID, "X is NULL");
@@ -189,7 +194,11 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
         ++h->timed_passes[(int)prec];
         h->timed_rows[(int)prec] += r1 - r0;
     }
-    if (tc_pass_supported(x, m)) {
+    // FP32 data: 3xTF32 tensor cores for the priming passes; the split-precision
+    // pass (pPCA step) runs on CUDA cores in exact FP32 with double-float folding,
+    // because long tensor-core accumulations lose accuracy beyond 1e-5.
+    const bool tc = tc_pass_supported(x, m) && !(x.dtype == PPCA_F32 && prec == PPCA_PREC_ACCURATE);
+    if (tc) {
         CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->sched, h->status, h->num_sms, h->stream));
     } else {
         CUDA_TRY(xpass_simt(x, V, m, r0, r1, Z, h->simt, h->stream));
@@ -621,6 +630,198 @@ ppca_status ppca_quantize_fp8(const float* X, int64_t n, int64_t d, int64_t ld_i
     if (!X || !out || !scales) return fail(PPCA_ERR_INVALID, "NULL argument");
     if (n < 0 || d < 0 || ld_in < d || ld_out < d) return fail(PPCA_ERR_INVALID, "bad shape");
     CUDA_TRY(quantize_fp8(X, n, d, ld_in, out, ld_out, scales, static_cast<cudaStream_t>(stream)));
+    return PPCA_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches
+
+struct ppca_batch {
+    std::vector<ppca_instance_desc> descs;
+    cudaStream_t user_stream = nullptr;   // the caller's stream (may be the legacy default stream)
+    cudaStream_t stream = nullptr;        // the batch's own stream: captured, and where the graph runs
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::vector<ppca_handle*> slots;
+    std::vector<cudaStream_t> slot_streams;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_slot(ppca_handle* h) {
+    if (!h) return;
+    if (h->ws) cudaFree(h->ws);
+    if (h->status) cudaFree(h->status);
+    delete h;
+}
+
+void free_batch(ppca_batch* b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (auto* h : b->slots) free_slot(h);
+    for (auto s : b->slot_streams) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+XView view_of(const ppca_instance_desc& ds) {
+    XView x;
+    x.ptr = ds.X;
+    x.n = ds.n;
+    x.d = ds.d;
+    x.ld = ds.ld;
+    x.dtype = (ppca_dtype)ds.dtype;
+    x.scales = ds.row_scales;
+    return x;
+}
+
+}  // namespace
+
+extern "C" {
+
+ppca_status ppca_batch_create(ppca_batch** out, const ppca_instance_desc* descs, int32_t count, int32_t slots,
+                              void* stream) {
+    if (!out) return fail(PPCA_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!descs || count < 1) return fail(PPCA_ERR_INVALID, "need at least one instance");
+    if (slots < 0) return fail(PPCA_ERR_INVALID, "slots < 0");
+    const int nslots = std::min<int>(slots == 0 ? 8 : slots, count);
+    for (int i = 0; i < count; ++i) {
+        const ppca_instance_desc& ds = descs[i];
+        ppca_status s = validate_x(ds.X, ds.n, ds.d, ds.ld, (ppca_dtype)ds.dtype, ds.row_scales);
+        if (s != PPCA_OK) return fail(s, "instance %d: %s", i, g_last_error.c_str());
+        const int64_t cap = std::min<int64_t>(std::min<int64_t>(ds.d, ds.n - 1), kMaxM);
+        if (ds.m < 1 || ds.m > cap) return fail(PPCA_ERR_INVALID, "instance %d: m = %d out of range", i, ds.m);
+        if (ds.k < 1 || ds.k > ds.m) return fail(PPCA_ERR_INVALID, "instance %d: k = %d out of range", i, ds.k);
+        if (ds.T < 0) return fail(PPCA_ERR_INVALID, "instance %d: T < 0", i);
+        if (!ds.E || !ds.lambda) return fail(PPCA_ERR_INVALID, "instance %d: NULL output", i);
+    }
+    ppca_batch* b = new (std::nothrow) ppca_batch();
+    if (!b) return fail(PPCA_ERR_OOM, "host allocation failed");
+    b->descs.assign(descs, descs + count);
+    b->user_stream = static_cast<cudaStream_t>(stream);
+    int device = 0, num_sms = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    for (int s = 0; s < nslots && e == cudaSuccess; ++s) {
+        ppca_handle* h = new (std::nothrow) ppca_handle();
+        if (!h) {
+            free_batch(b);
+            return fail(PPCA_ERR_OOM, "host allocation failed");
+        }
+        b->slots.push_back(h);
+        h->device = device;
+        h->num_sms = num_sms;
+        h->sched.fused = 0;          // slots run concurrently: no cooperative launches
+        cudaStream_t st = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) break;
+        b->slot_streams.push_back(st);
+        h->stream = st;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) break;
+        b->join.push_back(ev);
+        e = cudaMalloc(reinterpret_cast<void**>(&h->status), 256);
+        if (e == cudaSuccess) e = cudaMemset(h->status, 0, 256);
+        // workspace for the largest instance of this slot
+        int64_t nmax = 2, dmax = 1;
+        int mmax = 1;
+        for (int i = s; i < count; i += nslots) {
+            nmax = std::max<int64_t>(nmax, descs[i].n);
+            dmax = std::max<int64_t>(dmax, descs[i].d);
+            mmax = std::max(mmax, (int)descs[i].m);
+        }
+        h->x = view_of(descs[s]);
+        if (e == cudaSuccess) {
+            ppca_status ps = ensure_workspace_dims(h, nmax, dmax, mmax);
+            if (ps != PPCA_OK) {
+                const std::string msg = g_last_error;
+                free_batch(b);
+                return fail(ps, "batch slot %d: %s", s, msg.c_str());
+            }
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_batch(b);
+        return fail(PPCA_ERR_CUDA, "batch setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_run(ppca_batch* b) {
+    if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
+    if (!b->exec) {
+        const int nslots = (int)b->slots.size();
+        CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        ppca_status st = PPCA_OK;
+        cudaError_t e = cudaEventRecord(b->fork, b->stream);
+        for (int s = 0; s < nslots && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->slot_streams[s], b->fork, 0);
+        for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK; ++i) {
+            const ppca_instance_desc& ds = b->descs[i];
+            ppca_handle* h = b->slots[i % nslots];
+            h->x = view_of(ds);
+            ppca_prime_params prm;
+            ppca_prime_params_default(&prm, PPCA_POWER);
+            prm.V0 = ds.V0;
+            prm.seed = ds.seed;
+            prm.precision = PPCA_PREC_FAST;
+            st = ppca_prime(h, PPCA_POWER, ds.m, ds.T, &prm);
+            if (st == PPCA_OK) st = ppca_finalize(h, ds.k, ds.E, ds.lambda, PPCA_PREC_ACCURATE);
+            if (st == PPCA_OK && ds.V_out) st = ppca_get_basis(h, ds.V_out);
+        }
+        for (int s = 0; s < nslots && e == cudaSuccess; ++s) {
+            e = cudaEventRecord(b->join[s], b->slot_streams[s]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->join[s], 0);
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+        if (st != PPCA_OK || e != cudaSuccess || ee != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            if (st != PPCA_OK) return st;
+            return fail(PPCA_ERR_CUDA, "batch capture failed: %s",
+                        cudaGetErrorString(e != cudaSuccess ? e : ee));
+        }
+        b->graph = g;
+        CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    }
+    CUDA_TRY(cudaEventRecord(b->ev_in, b->user_stream));
+    CUDA_TRY(cudaStreamWaitEvent(b->stream, b->ev_in, 0));
+    CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
+    CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
+    CUDA_TRY(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_sync(ppca_batch* b) {
+    if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (auto* h : b->slots) {
+        ppca_status s = ppca_sync(h);
+        if (s != PPCA_OK) return s;
+    }
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_destroy(ppca_batch* b) {
+    free_batch(b);
     return PPCA_OK;
 }
 

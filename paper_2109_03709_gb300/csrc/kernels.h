@@ -15,7 +15,9 @@ namespace ppca {
 struct SimtPassScratch {
     float* Y = nullptr;
     float* Zpart = nullptr;
-    int nsplit = 1;
+    int nsplit = 1;             // split count the partial buffer was sized for
+    int64_t zpart_floats = 0;   // capacity of Zpart
+    int num_sms = 1;
 };
 size_t simt_pass_scratch_floats(int64_t rows, int64_t d, int m, int nsplit);
 int simt_pass_nsplit(int64_t rows, int64_t d, int m, int num_sms);
@@ -30,11 +32,9 @@ size_t gram_part_floats(int64_t d, int m);
 cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part,
                     cudaStream_t st);
 
-// Cholesky G = R^T R (FP64, one CTA); R upper, written as FP32 (Rf) and FP64 (Rd).
 // Cholesky G = R^T R (one CTA), in double-float arithmetic or plain FP32;
 // writes X = R^-1 (upper, row-major FP32) to Rinv.
 cudaError_t cholesky(const double* G, int m, float* Rinv, bool double_float, int* status, cudaStream_t st);
-// Q = V R^-1 by row-wise forward substitution (FP32); Q may alias V.
 // Q = V R^-1 as a product with the triangular inverse; Q must not alias V.
 cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st);
 

@@ -178,7 +178,11 @@ cudaError_t xpass_simt(const XView& x, const float* V, int m, int64_t r0, int64_
         xv_kernel<<<dim3(ceil_div_i(chunk, BM), ceil_div_i(m, BN)), 256, 0, st>>>(x, V, m, r0 + rb, chunk,
                                                                                    s.Y + rb * m);
     }
-    const int64_t split_rows = ((rows + s.nsplit - 1) / s.nsplit + BK - 1) / BK * BK;
+    // The split depends only on this problem's shape (not on how large the
+    // workspace is), so a problem gives the same bits alone or in a batch.
+    int want = simt_pass_nsplit(x.n, x.d, m, s.num_sms);
+    while (want > 1 && (int64_t)want * x.d * m * 2 > s.zpart_floats) --want;
+    const int64_t split_rows = ((rows + want - 1) / want + BK - 1) / BK * BK;
     const int nsplit = (int)((rows + split_rows - 1) / split_rows);
     note_launch();
     xty_kernel<<<dim3(ceil_div_i(x.d, BM), ceil_div_i(m, BN), nsplit), 256, 0, st>>>(x, s.Y, m, r0, rows, split_rows,

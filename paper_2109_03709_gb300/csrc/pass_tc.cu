@@ -23,6 +23,7 @@
 // kDevWaitTimeout, drains its copies, frees TMEM and returns.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "pass_tc.h"
@@ -626,6 +627,374 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     }
 }
 
+// ---------------------------------------------------------------- FP32 data: 3xTF32
+//
+// FP32 X on kind::tf32 tensor cores with FP32-class accuracy: every operand is
+// split into a TF32 head (cvt.rna) and the FP32 residual, and the products
+// hi*hi + hi*lo + lo*hi are accumulated in FP32 (the lo*lo term is below
+// 2^-22 of the result).  Transform warps (6-9) make the X operands in shared
+// memory: for Y = X V they round the TMA-loaded tile in place and write the
+// residual in the same swizzled layout; for Z = X^T Y they read an unswizzled
+// tile and write the transposed head and residual directly in the K-major
+// 128-byte-swizzled layout, so no MN-major TF32 operand is needed.
+constexpr int kF32Threads = 320;
+constexpr int kBK32 = 32;               // K extent of one stage (32 FP32 = 128 B)
+
+struct F32Header {
+    uint64_t full[kMaxStages], xform[kMaxStages], empty[kMaxStages];
+    uint64_t tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int abort;
+};
+
+__device__ inline void f32_prologue(F32Header* hd, int stages, uint32_t tmem_cols, const CUtensorMap* m0,
+                                    const CUtensorMap* m1) {
+    const int warp = threadIdx.x / 32;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) {
+            tc::mbar_init(&hd->full[i], 1);
+            tc::mbar_init(&hd->xform[i], 128);
+            tc::mbar_init(&hd->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&hd->tfull[i], 1);
+            tc::mbar_init(&hd->tempty[i], 128);
+        }
+        hd->abort = 0;
+        tc::mbar_init_fence();
+        tc::tma_prefetch(m0);
+        tc::tma_prefetch(m1);
+    }
+    if (warp == 1) tc::tmem_alloc(&hd->tmem_base, tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ inline void f32_teardown(F32Header* hd, uint32_t tmem_cols) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x / 32 == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(hd->tmem_base, tmem_cols);
+    }
+}
+
+// One 3xTF32 K-stage (32 wide): D += Ahi*Bhi + Ahi*Blo + Alo*Bhi.
+__device__ __forceinline__ void mma_3xtf32_stage(uint32_t d_tmem, uint32_t a_hi, uint32_t a_lo, uint32_t b_hi,
+                                                 uint32_t b_lo, uint32_t idesc, bool first) {
+#pragma unroll
+    for (int kk = 0; kk < kBK32 / 8; ++kk) {
+        const uint64_t ah = tc::smem_desc_sw128(a_hi + kk * 32, 16, 1024);
+        const uint64_t al = tc::smem_desc_sw128(a_lo + kk * 32, 16, 1024);
+        const uint64_t bh = tc::smem_desc_sw128(b_hi + kk * 32, 16, 1024);
+        const uint64_t bl = tc::smem_desc_sw128(b_lo + kk * 32, 16, 1024);
+        tc::mma_tf32(d_tmem, ah, bh, idesc, !(first && kk == 0));
+        tc::mma_tf32(d_tmem, ah, bl, idesc, 1);
+        tc::mma_tf32(d_tmem, al, bh, idesc, 1);
+    }
+}
+
+// Y = X V for FP32 X.  Stage: [A head 16 KB][A residual 16 KB][V head][V residual].
+__global__ void __launch_bounds__(kF32Threads, 1)
+    xv_f32_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles, int nk,
+                  int m_pad, int stages, float* __restrict__ Yt, int64_t ldy, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 128u * 128u;
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = 2u * a_bytes + 2u * b_piece;
+    F32Header* hd = reinterpret_cast<F32Header*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(m_pad);
+    f32_prologue(hd, stages, tmem_cols, &tmX, &tmV);
+    const uint32_t tmem = hd->tmem_base;
+    volatile int* abort_flag = &hd->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[s], a_bytes + 2u * b_piece);
+                    uint8_t* st = tiles + (size_t)s * stage_bytes;
+                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK32, t * 128);
+                    tc::tma_load_2d(st + 2 * a_bytes, &tmV, &hd->full[s], k * kBK32, 0);
+                    tc::tma_load_2d(st + 2 * a_bytes + b_piece, &tmV, &hd->full[s], k * kBK32, m_pad);
+                }
+            }
+            const uint32_t first = it > (uint32_t)stages ? it - (uint32_t)stages : 0u;
+            if (*abort_flag)
+                for (uint32_t j = first; j < it; ++j)
+                    tc::mbar_wait(&hd->full[j % stages], (j / stages) & 1u, status, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(128, m_pad);
+            uint32_t it = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->xform[s], ph, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+                    mma_3xtf32_stage(tmem + b * (uint32_t)m_pad, a, a + a_bytes, a + 2 * a_bytes,
+                                     a + 2 * a_bytes + b_piece, idesc, k == 0);
+                    tc::mma_commit(&hd->empty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->tfull[b]);
+            }
+        }
+    } else if (warp < 6) {
+        const int q = warp & 3;
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+            if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+            for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float y = __uint_as_float(r[j]);
+                    const float hi = tc::tf32_rna(y);
+                    Yt[(int64_t)(c0 + j) * ldy + row] = hi;
+                    Yt[(int64_t)(m_pad + c0 + j) * ldy + row] = y - hi;
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&hd->tempty[b]);
+        }
+    } else {
+        // transform: round the X tile to TF32 in place, residual into the next 16 KB
+        const int tid = threadIdx.x - 192;
+        uint32_t it = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            bool ok = true;
+            for (int k = 0; k < nk; ++k, ++it) {
+                const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                if (!tc::mbar_wait(&hd->full[s], ph, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                float4* hi = reinterpret_cast<float4*>(tiles + (size_t)s * stage_bytes);
+                float4* lo = reinterpret_cast<float4*>(tiles + (size_t)s * stage_bytes + a_bytes);
+#pragma unroll
+                for (int v = 0; v < 8; ++v) {
+                    const int idx = v * 128 + tid;
+                    float4 x = hi[idx];
+                    float4 h = make_float4(tc::tf32_rna(x.x), tc::tf32_rna(x.y), tc::tf32_rna(x.z), tc::tf32_rna(x.w));
+                    hi[idx] = h;
+                    lo[idx] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+                }
+                tc::fence_proxy_async_shared();
+                tc::mbar_arrive(&hd->xform[s]);
+            }
+            if (!ok) break;
+        }
+    }
+    f32_teardown(hd, tmem_cols);
+}
+
+// Z = X^T Y for FP32 X.  Stage: [raw X 4 x (32 x 32) 16 KB][A head 16 KB][A residual 16 KB][Y head][Y residual].
+__global__ void __launch_bounds__(kF32Threads, 1)
+    xty_f32_kernel(const __grid_constant__ CUtensorMap tmXr, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
+                   int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 128u * 128u;
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = 3u * a_bytes + 2u * b_piece;
+    F32Header* hd = reinterpret_cast<F32Header*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(m_pad);
+    f32_prologue(hd, stages, tmem_cols, &tmXr, &tmY);
+    const uint32_t tmem = hd->tmem_base;
+    const int ntask = Dt * Sg;
+    volatile int* abort_flag = &hd->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int s = task % Dt, g = task / Dt;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int k = k0; k < k1; ++k, ++it) {
+                    const uint32_t si = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[si], ph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[si], a_bytes + 2u * b_piece);
+                    uint8_t* st = tiles + (size_t)si * stage_bytes;
+#pragma unroll
+                    for (int bx = 0; bx < 4; ++bx)
+                        tc::tma_load_2d(st + bx * 4096, &tmXr, &hd->full[si], s * 128 + bx * 32, k * kBK32);
+                    tc::tma_load_2d(st + 3 * a_bytes, &tmY, &hd->full[si], k * kBK32, 0);
+                    tc::tma_load_2d(st + 3 * a_bytes + b_piece, &tmY, &hd->full[si], k * kBK32, m_pad);
+                }
+            }
+            const uint32_t first = it > (uint32_t)stages ? it - (uint32_t)stages : 0u;
+            if (*abort_flag)
+                for (uint32_t j = first; j < it; ++j)
+                    tc::mbar_wait(&hd->full[j % stages], (j / stages) & 1u, status, 100000000ull);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_tf32(128, m_pad);
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int g = task / Dt;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int kb = k0; kb < k1 && ok; kb += flush, ++fb) {
+                    const int ke = kb + flush < k1 ? kb + flush : k1;
+                    const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                    if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    for (int k = kb; k < ke; ++k, ++it) {
+                        const uint32_t si = it % stages, ph = (it / stages) & 1u;
+                        if (!tc::mbar_wait(&hd->xform[si], ph, status) || *abort_flag) {
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a = tc::smem_u32(tiles + (size_t)si * stage_bytes);
+                        mma_3xtf32_stage(tmem + b * (uint32_t)m_pad, a + a_bytes, a + 2 * a_bytes, a + 3 * a_bytes,
+                                         a + 3 * a_bytes + b_piece, idesc, k == kb);
+                        tc::mma_commit(&hd->empty[si]);
+                    }
+                    if (ok) tc::mma_commit(&hd->tfull[b]);
+                }
+            }
+        }
+    } else if (warp < 6) {
+        const int q = warp & 3;
+        uint32_t fb = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            const int s = task % Dt, g = task / Dt;
+            const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+            const int64_t j = (int64_t)s * 128 + q * 32 + lane;
+            float* z = Zacc + (((int64_t)g * Dt * 128 + j) * m_pad) * 2;
+            for (int kb = k0; kb < k1; kb += flush, ++fb) {
+                const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+                    float2* zz = reinterpret_cast<float2*>(z) + c0;
+                    if (kb == k0) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) zz[jj] = make_float2(__uint_as_float(r[jj]), 0.f);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            float2 v = zz[jj];
+                            df_add(v.x, v.y, __uint_as_float(r[jj]));
+                            zz[jj] = v;
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    } else {
+        // transform: column i of the 128-column slice -> row i of the K-major
+        // operands (head and residual), 128-byte swizzle: 16-byte chunk c of row
+        // i is stored at chunk position c ^ (i % 8) of its 1024-byte atom.
+        const int i = threadIdx.x - 192;
+        const float* raw_col = nullptr;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            const int g = task / Dt;
+            const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+            for (int k = k0; k < k1; ++k, ++it) {
+                const uint32_t si = it % stages, ph = (it / stages) & 1u;
+                if (!tc::mbar_wait(&hd->full[si], ph, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = tiles + (size_t)si * stage_bytes;
+                raw_col = reinterpret_cast<const float*>(st + (i / 32) * 4096) + (i % 32);
+                uint8_t* hi_row = st + a_bytes + (i / 8) * 1024 + (i % 8) * 128;
+                uint8_t* lo_row = st + 2 * a_bytes + (i / 8) * 1024 + (i % 8) * 128;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    float x[4], h[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        x[e] = raw_col[(c * 4 + e) * 32];
+                        h[e] = tc::tf32_rna(x[e]);
+                    }
+                    const int pos = (c ^ (i % 8)) * 16;
+                    *reinterpret_cast<float4*>(hi_row + pos) = make_float4(h[0], h[1], h[2], h[3]);
+                    *reinterpret_cast<float4*>(lo_row + pos) =
+                        make_float4(x[0] - h[0], x[1] - h[1], x[2] - h[2], x[3] - h[3]);
+                }
+                tc::fence_proxy_async_shared();
+                tc::mbar_arrive(&hd->xform[si]);
+            }
+        }
+    }
+    f32_teardown(hd, tmem_cols);
+}
+
+// V (d x m column-major FP32) -> TF32 head and FP32 residual, [2][m_pad][ldv4], zero padded.
+__global__ void split_v_f32_kernel(const float* __restrict__ V, int64_t d, int m, int m_pad, int64_t ldv4,
+                                   float* __restrict__ Vp) {
+    const int64_t total = (int64_t)m_pad * ldv4;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / ldv4);
+        const int64_t j = e % ldv4;
+        const float v = (c < m && j < d) ? V[(int64_t)c * d + j] : 0.f;
+        const float h = tc::tf32_rna(v);
+        Vp[e] = h;
+        Vp[e + total] = v - h;
+    }
+}
+
 // V (d x m column-major FP32) -> S BF16 pieces, [S][m_pad][ldv], zero padded.
 template <int S>
 __global__ void split_v_kernel(const float* __restrict__ V, int64_t d, int m, int m_pad, int64_t ldv,
@@ -671,17 +1040,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
-                    uint32_t box_inner, uint32_t box_outer) {
+bool encode_2d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t inner, uint64_t outer,
+               uint64_t pitch_bytes, uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle swz) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {inner, outer};
     cuuint64_t strides[1] = {pitch_bytes};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t pitch_bytes,
+                    uint32_t box_inner, uint32_t box_outer) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, inner, outer, pitch_bytes, box_inner, box_outer,
+                     CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
 int stages_for(uint32_t stage_bytes) {
@@ -706,8 +1080,9 @@ Layout layout_of(int64_t n, int64_t d, int m, int num_sms) {
     L.ldv = round_up(d, 8);
     L.rows_pad_max = round_up(n, 128);
     L.Dt = (int)((d + 127) / 128);
-    L.vp_bytes = (size_t)3 * L.m_pad * L.ldv * 2;
-    L.yt_bytes = (size_t)3 * L.m_pad * L.rows_pad_max * 2;
+    // sized for the larger of three BF16 pieces and two FP32 pieces
+    L.vp_bytes = std::max((size_t)3 * L.m_pad * L.ldv * 2, (size_t)2 * L.m_pad * round_up(d, 4) * 4);
+    L.yt_bytes = std::max((size_t)3 * L.m_pad * L.rows_pad_max * 2, (size_t)2 * L.m_pad * L.rows_pad_max * 4);
     L.z_bytes = (size_t)(2 * num_sms + L.Dt + 2) * 128 * L.m_pad * 8;
     L.flag_bytes = (size_t)2 * (L.rows_pad_max / 128 + 1) * sizeof(int);
     (void)m;
@@ -848,6 +1223,65 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     return launch_zreduce(static_cast<float*>(sc.zacc), Sg, 2 * Dt2, ps.d, m, ps.m_pad, Z, st);
 }
 
+// FP32 data: 3xTF32 passes (two kernels; X read twice).
+cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
+                         const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+    const int64_t d = x.d, rows = r1 - r0;
+    const int m_pad = m_pad_of(m);
+    const int64_t ldv4 = round_up(d, 4);
+    const int64_t ldy = round_up(rows, 128);
+    const int Dt = (int)((d + 127) / 128);
+    const int ntiles = (int)(ldy / 128), nk = (int)((d + kBK32 - 1) / kBK32);
+    float* Vp = static_cast<float*>(sc.vp);
+    float* Yt = static_cast<float*>(sc.yt);
+    float* Zacc = static_cast<float*>(sc.zacc);
+    {
+        const int64_t total = (int64_t)m_pad * ldv4;
+        int blocks = (int)((total + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        note_launch();
+        split_v_f32_kernel<<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv4, Vp);
+    }
+    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * 4;
+    CUtensorMap tmX, tmXr, tmV, tmY;
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    if (!encode_2d(&tmX, f32, xbase, d, rows, x.ld * 4, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tmXr, f32, xbase, d, rows, x.ld * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !encode_2d(&tmV, f32, Vp, d, 2 * (uint64_t)m_pad, ldv4 * 4, 32, m_pad, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tmY, f32, Yt, ldy, 2 * (uint64_t)m_pad, ldy * 4, 32, m_pad, CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    {
+        const uint32_t stage_bytes = 2u * 16384u + 2u * (uint32_t)m_pad * 128u;
+        int stages = (int)((kSmemBudget - 2048) / stage_bytes);
+        if (stages > kMaxStages) stages = kMaxStages;
+        const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(F32Header);
+        e = cudaFuncSetAttribute(xv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = ntiles < num_sms ? ntiles : num_sms;
+        note_launch();
+        xv_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages, Yt, ldy, status);
+    }
+    int Sg;
+    {
+        const uint32_t stage_bytes = 3u * 16384u + 2u * (uint32_t)m_pad * 128u;
+        int stages = (int)((kSmemBudget - 2048) / stage_bytes);
+        if (stages > kMaxStages) stages = kMaxStages;
+        const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(F32Header);
+        e = cudaFuncSetAttribute(xty_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int kst = (int)(ldy / kBK32);
+        Sg = Dt >= num_sms ? 1 : num_sms / Dt;
+        if (Sg > kst) Sg = kst;
+        if (Sg < 1) Sg = 1;
+        const int ntask = Dt * Sg;
+        const int grid = ntask < num_sms ? ntask : num_sms;
+        note_launch();
+        xty_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmXr, tmY, Dt, Sg, kst, flush, m_pad, stages, Zacc, status);
+    }
+    return launch_zreduce(Zacc, Sg, Dt, d, m, m_pad, Z, st);
+}
+
 }  // namespace
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms) {
@@ -871,12 +1305,13 @@ TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int
 }
 
 bool tc_pass_supported(const XView& x, int m) {
-    return x.dtype == PPCA_BF16 && m >= 1 && m <= kMaxM && encode_fn() != nullptr;
+    return (x.dtype == PPCA_BF16 || x.dtype == PPCA_F32) && m >= 1 && m <= kMaxM && encode_fn() != nullptr;
 }
 
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
                      const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
     if (r1 <= r0) return cudaErrorInvalidValue;
+    if (x.dtype == PPCA_F32) return run_pass_f32(x, V, m, r0, r1, Z, 64, s, status, num_sms, st);   // FAST only
     if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
     // The fused pass needs every 128-column slice of d owned by a resident CTA.
     const int Dt = (int)((x.d + 127) / 128);

@@ -127,6 +127,40 @@ def gaussian_data_torch(n: int, d: int, lam, seed: int, device, out_dtype, chunk
     return X, Q
 
 
+def batch_instances(count: int, seed: int):
+    """Shapes of a ragged batch: n ~ U[2000, 200000], d in {64, ..., 2048}, k ~ U[4, 32],
+    l = k, lambda_i = rho^i with rho ~ U[0.8, 0.98] per instance (m = 2k <= min(d, 128))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        d = int(rng.choice([64, 128, 256, 512, 1024, 2048]))
+        k = int(rng.integers(4, 33))
+        k = min(k, d // 2)
+        out.append({"n": int(rng.integers(2000, 200001)), "d": d, "k": k, "m": 2 * k,
+                    "rho": float(rng.uniform(0.8, 0.98)), "seed": int(seed * 100003 + i)})
+    return out
+
+
+def haar_orthogonal_torch(d: int, gen, device):
+    """Haar orthogonal d x d on a torch device: QR of a Gaussian, R's diagonal made positive."""
+    import torch
+    G = torch.randn((d, d), generator=gen, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    return Q * torch.sign(torch.diagonal(R))[None, :]
+
+
+def instance_data_torch(n: int, d: int, lam, seed: int, device, out_dtype):
+    """X = G diag(sqrt(lam)) Q^T, columns centred, drawn entirely on the device (for batches)."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    Q = haar_orthogonal_torch(d, gen, device)
+    B = (torch.sqrt(torch.as_tensor(np.asarray(lam), dtype=torch.float64, device=device))[:, None] * Q.T).float()
+    X = torch.randn((n, d), generator=gen, device=device, dtype=torch.float32) @ B
+    X -= X.double().mean(0).float()[None, :]
+    return X.to(out_dtype) if out_dtype != torch.float32 else X
+
+
 def counterexample_points():
     """The 6-point, 3-dimensional data set of the counterexample (Section 4.1)."""
     return np.array([[3, 0, 0], [-3, 0, 0], [0, 2, 0], [0, -2, 0], [0, 0, 1], [0, 0, -1]], dtype=np.float64)

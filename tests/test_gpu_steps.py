@@ -58,6 +58,25 @@ def test_xpass_fp32(P, n, d, m, r0, r1, ld):
     assert normwise(host_basis(Zd), Zref) <= 2e-5
 
 
+@pytest.mark.parametrize("n,d,m,r0,r1,ld", XPASS_CASES)
+def test_xpass_fp32_tensor_core_3xtf32(P, n, d, m, r0, r1, ld):
+    """FAST pass for FP32 data: 3xTF32 on tensor cores.  Each operand is split
+    into a TF32 head and an FP32 residual (products exact to ~2^-21); the
+    tensor-core FP32 accumulation over long K adds up to ~2e-5 relative
+    (measured at K = 2048), hence 5e-5 normwise."""
+    lam = 0.95 ** np.arange(1, d + 1)
+    X, _ = synth.gaussian_data(n, d, lam, seed=n + d)
+    Xd = dev_matrix(X, "f32", ld)
+    Vd = dev_basis(synth.initial_basis(d, m, seed=m))
+    Zd = empty_basis(d, m)
+    h = P.ppca_create(Xd)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zd, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)[r0:r1]
+    Zref = Xs.T @ (Xs @ host_basis(Vd))
+    assert normwise(host_basis(Zd), Zref) <= 5e-5
+
+
 BF16_CASES = [
     # n, d, m, r0, r1
     (3001, 512, 64, 0, 3001),
