@@ -196,7 +196,9 @@ typedef struct ppca_schedule {
     int32_t producers;        /* CTAs running Y = X V in the fused pass (0: one per SM)           */
     int32_t window;           /* tiles a producer may run ahead of the slowest consumer (0: the  */
                               /* library keeps about 48 MB of X in flight)                        */
-    int32_t reserved;         /* must be 0                                                        */
+    int32_t flush;            /* split-precision passes: K-stages (64 wide) an FP32 tensor-core   */
+                              /* accumulator takes before it is folded into a double-float sum    */
+                              /* (0: library default; larger = faster, less accurate)             */
 } ppca_schedule;
 
 /* Set the X-pass schedule of a handle (takes effect at its next pass). */
@@ -278,6 +280,19 @@ PPCA_API ppca_status ppca_batch_destroy(ppca_batch *b);
 /* ---------------------------------------------------------------------------
  * Individual steps of the hot path.
  * ------------------------------------------------------------------------- */
+
+/*
+ * Projected Gram matrix of the pPCA step (Algorithm 1, steps 3-4; Section 3):
+ *   G = (X[r0:r1] Q)^T (X[r0:r1] Q)
+ * over the data the pPCA step reads (the ppca_set_refine copy if one was set,
+ * else X).
+ *   Q  device, d x m column-major FP32 input (1 <= m <= 128), normally orthonormal
+ *   G  device, m x m FP64 output, row-major, exactly symmetric
+ * ACCURATE/AUTO: split-precision products, error about 1e-6 of |X Q|^2 entrywise
+ * scale; FAST: BF16-level products.  Requires 0 <= r0 < r1 <= n.
+ */
+PPCA_API ppca_status ppca_projected_gram(ppca_handle *h, const float *Q, int32_t m, int64_t r0, int64_t r1,
+                                double *G, ppca_precision precision);
 
 /*
  * One fused X-pass (the product X^T X V of Sections 2.1-2.3, restricted to rows

@@ -23,6 +23,7 @@ __all__ = [
     "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
+    "ppca_projected_gram",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "EXPORTED_SYMBOLS",
@@ -44,7 +45,7 @@ EXPORTED_SYMBOLS = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_eigh_noalloc", "ppca_set_schedule",
+    "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy",
 ]
 
@@ -84,7 +85,7 @@ class ppca_schedule(ctypes.Structure):
         ("fused", ctypes.c_int32),
         ("producers", ctypes.c_int32),
         ("window", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("flush", ctypes.c_int32),
     ]
 
 
@@ -130,6 +131,7 @@ _SIGS = {
     "ppca_destroy": (_c_status, [_vp]),
     "ppca_xpass": (_c_status, [_vp, _vp, _i32, _i64, _i64, _vp, ctypes.c_int]),
     "ppca_orthonormalize": (_c_status, [_vp, _vp, _vp, _i32]),
+    "ppca_projected_gram": (_c_status, [_vp, _vp, _i32, _i64, _i64, _vp, ctypes.c_int]),
     "ppca_eigh": (_c_status, [_vp, _vp, _i32, _vp, _vp]),
     "ppca_quantize_bf16": (_c_status, [_vp, _i64, _i64, _i64, _vp, _i64, _vp]),
     "ppca_quantize_fp8": (_c_status, [_vp, _i64, _i64, _i64, _vp, _i64, _vp, _vp]),
@@ -310,6 +312,12 @@ def ppca_xpass(h: Handle, V, m: int, r0: int, r1: int, Z, precision: int = PPCA_
     _check(load_library().ppca_xpass(h.ptr, _ptr(V), m, r0, r1, _ptr(Z), precision), "ppca_xpass")
 
 
+def ppca_projected_gram(h: Handle, Q, m: int, r0: int, r1: int, G, precision: int = PPCA_PREC_AUTO):
+    """G (m x m FP64, device) = (X[r0:r1] Q)^T (X[r0:r1] Q) over the data the pPCA step reads."""
+    _check(load_library().ppca_projected_gram(h.ptr, _ptr(Q), m, r0, r1, _ptr(G), precision),
+           "ppca_projected_gram")
+
+
 def ppca_orthonormalize(h: Handle, V, Q, m: int):
     _check(load_library().ppca_orthonormalize(h.ptr, _ptr(V), _ptr(Q), m), "ppca_orthonormalize")
 
@@ -373,8 +381,8 @@ def ppca_batch_destroy(b: Batch):
         b.ptr = None
 
 
-def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0):
-    s = ppca_schedule(fused, producers, window, 0)
+def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0, flush: int = 0):
+    s = ppca_schedule(fused, producers, window, flush)
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
 
 

@@ -175,10 +175,10 @@ ppca_status validate_x(const void* X, int64_t n, int64_t d, int64_t ld, ppca_dty
     return PPCA_OK;
 }
 
-// One X-pass over rows [r0, r1) of view x: Z = X^T X V.
-ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
-                      ppca_precision prec) {
-    cudaEvent_t ev_end = nullptr;
+// Timing of one pass over rows [r0, r1): records the start event and returns
+// the end event to record after the pass (nullptr when timing is off).
+ppca_status pass_timer(ppca_handle* h, ppca_precision prec, int64_t rows, cudaEvent_t* ev_end) {
+    *ev_end = nullptr;
     if (h->timing) {
         if (h->events_used == h->events.size()) {
             cudaEvent_t a, b;
@@ -190,18 +190,45 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
         h->event_prec[h->events_used] = (int)prec;
         auto& pr = h->events[h->events_used++];
         CUDA_TRY(cudaEventRecord(pr.first, h->stream));
-        ev_end = pr.second;
+        *ev_end = pr.second;
         ++h->timed_passes[(int)prec];
-        h->timed_rows[(int)prec] += r1 - r0;
+        h->timed_rows[(int)prec] += rows;
     }
-    // FP32 data: 3xTF32 tensor cores for the priming passes; the split-precision
-    // pass (pPCA step) runs on CUDA cores in exact FP32 with double-float folding,
-    // because long tensor-core accumulations lose accuracy beyond 1e-5.
+    return PPCA_OK;
+}
+
+// One X-pass over rows [r0, r1) of view x: Z = X^T X V.
+ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
+                      ppca_precision prec) {
+    cudaEvent_t ev_end = nullptr;
+    PPCA_TRY(pass_timer(h, prec, r1 - r0, &ev_end));
+    // FP32 data: 3xTF32 tensor cores for FAST passes; an ACCURATE X-pass (used
+    // when priming is asked to run at full precision) runs on CUDA cores in
+    // exact FP32 with double-float folding.  The pPCA step itself uses the
+    // projected Gram (run_gram), which is accurate on tensor cores.
     const bool tc = tc_pass_supported(x, m) && !(x.dtype == PPCA_F32 && prec == PPCA_PREC_ACCURATE);
     if (tc) {
         CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->sched, h->status, h->num_sms, h->stream));
     } else {
         CUDA_TRY(xpass_simt(x, V, m, r0, r1, Z, h->simt, h->stream));
+    }
+    if (ev_end) CUDA_TRY(cudaEventRecord(ev_end, h->stream));
+    return PPCA_OK;
+}
+
+// Projected Gram over rows [r0, r1) of view x: G = (X Q)^T (X Q), FP64.
+// Tensor cores for BF16 and FP32 data (one contraction, split precision);
+// FP8 data: the CUDA-core pass Z = X^T X Q, then G = Q^T Z in double-float.
+ppca_status run_gram(ppca_handle* h, const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
+                     ppca_precision prec) {
+    cudaEvent_t ev_end = nullptr;
+    PPCA_TRY(pass_timer(h, prec, r1 - r0, &ev_end));
+    if (tc_pass_supported(x, m)) {
+        CUDA_TRY(projected_gram_tc(x, Q, m, r0, r1, G, prec, h->sched.flush, h->tc, h->status, h->num_sms,
+                                   h->stream));
+    } else {
+        CUDA_TRY(xpass_simt(x, Q, m, r0, r1, h->T, h->simt, h->stream));
+        CUDA_TRY(gram_df(Q, h->T, x.d, m, G, h->gram_part, h->stream));
     }
     if (ev_end) CUDA_TRY(cudaEventRecord(ev_end, h->stream));
     return PPCA_OK;
@@ -436,8 +463,7 @@ ppca_status ppca_finalize(ppca_handle* h, int32_t k, float* E, double* lambda, p
     const int64_t d = h->x.d, n = h->x.n;
     PPCA_TRY(run_orth(h, h->V, h->Q, m));                                          // step 2: span
     const XView& xf = h->has_ref ? h->xref : h->x;
-    PPCA_TRY(run_xpass(h, xf, h->Q, m, 0, n, h->T, prec));                         // step 3: X^T X Q
-    CUDA_TRY(gram_df(h->Q, h->T, d, m, h->G, h->gram_part, h->stream));            // G = (XQ)^T (XQ)
+    PPCA_TRY(run_gram(h, xf, h->Q, m, 0, n, h->G, prec));                          // step 3: G = (XQ)^T XQ
     CUDA_TRY(eigh_small(h->G, m, h->w, h->U, h->jac, h->status, h->stream));       // step 4: full-PCA
     CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)n, E, lambda, h->stream));   // step 5
     return PPCA_OK;
@@ -528,11 +554,12 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
 
 ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
-    if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->reserved != 0)
+    if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0)
         return fail(PPCA_ERR_INVALID, "schedule out of range");
     h->sched.fused = s->fused;
     h->sched.producers = s->producers;
     h->sched.window = s->window;
+    h->sched.flush = s->flush;
     return PPCA_OK;
 }
 
@@ -591,6 +618,20 @@ ppca_status ppca_xpass(ppca_handle* h, const float* V, int32_t m, int64_t r0, in
     PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
     const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_FAST : precision;
     return run_xpass(h, h->x, V, m, r0, r1, Z, prec);
+}
+
+ppca_status ppca_projected_gram(ppca_handle* h, const float* Q, int32_t m, int64_t r0, int64_t r1, double* G,
+                                ppca_precision precision) {
+    if (!h || !Q || !G) return fail(PPCA_ERR_INVALID, "NULL argument");
+    PPCA_TRY(check_m(h, m));
+    if (r0 < 0 || r1 > h->x.n || r0 >= r1)
+        return fail(PPCA_ERR_INVALID, "row range [%lld, %lld) invalid for n = %lld", (long long)r0, (long long)r1,
+                    (long long)h->x.n);
+    if (precision < PPCA_PREC_AUTO || precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", (int)precision);
+    PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
+    const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_ACCURATE : precision;
+    return run_gram(h, h->has_ref ? h->xref : h->x, Q, m, r0, r1, G, prec);
 }
 
 ppca_status ppca_orthonormalize(ppca_handle* h, const float* V, float* Q, int32_t m) {

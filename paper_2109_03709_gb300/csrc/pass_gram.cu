@@ -1,0 +1,550 @@
+// pass_gram.cu -- projected Gram matrix of the pPCA step on tcgen05 + TMA.
+//
+// Algorithm 1, steps 3-4 diagonalise the m x m matrix Q^T X^T X Q of an
+// orthonormal Q (Section 3: the full PCA of the data projected on span(V)).
+// It is formed as the Gram matrix of Y = X Q, so the pass over X runs one
+// n x d x m contraction instead of the two of Z = X^T (X Q):
+//
+//   ygen   Y = X Q    persistent over 128-row tiles of X.  Q (FP32) is split
+//                     into NV BF16 pieces; FP32 X is split in shared memory
+//                     into NX BF16 pieces by four transform warps (BF16 X is
+//                     one exact piece).  Of the piece products x_a q_b those
+//                     with a + b < max(NX, NV) are kept; the dropped ones are
+//                     below 2^-24 of the result.
+//   gram   G = Y^T Y  from Y's three BF16 pieces, products y_a^T y_b with
+//                     a + b <= 2, one double-float partial per CTA.
+//   reduce G = sum of the partials in FP64, symmetrised.
+//
+// Accumulation.  An FP32 tensor-core accumulator that takes many MMAs in a row
+// drifts: on sm_103a a relative error of roughly 2e-8 per accumulating MMA was
+// measured, systematic rather than random, so it grows linearly with K.  Both
+// kernels therefore empty the accumulator every `flush` K-stages (64 wide) into
+// a double-float running sum kept in TMEM beside it (columns [2 m_pad, 4 m_pad)),
+// which caps the drift at the MMAs of one flush group.
+//
+// Warp roles: warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs (one
+// thread), warps 2-5 are the epilogue (TMEM lane quarter = warp % 4), warps
+// 6-9 (FP32 X only) make the X pieces.  Every wait is bounded (2 s); on a
+// timeout the kernel records kDevWaitTimeout, drains its copies, frees TMEM
+// and returns.
+#include <cudaTypedefs.h>
+
+#include "pass_tc.h"
+#include "tc_host.h"
+#include "tc_ptx.cuh"
+
+namespace ppca {
+
+namespace {
+
+constexpr int kGThreadsBf16 = 192;
+constexpr int kGThreadsF32 = 320;
+constexpr int kGMaxStages = 6;
+constexpr int kGBK = 64;                    // K extent of one stage (64 BF16 = 128 B)
+constexpr uint32_t kPiece = 128u * 128u;    // one 128-row x 128-byte operand tile
+constexpr int kGSmemBudget = 200 * 1024;
+
+struct GHeader {
+    uint64_t full[kGMaxStages], xform[kGMaxStages], empty[kGMaxStages];
+    uint64_t tfull[2], tempty[2];
+    uint32_t tmem_base;
+    int abort;
+    int xform_go;
+};
+
+__host__ __device__ inline uint32_t pow2_cols(uint32_t need) {
+    uint32_t c = 32;
+    while (c < need) c <<= 1;
+    return c;
+}
+
+__device__ inline uint8_t* align1024(uint8_t* p) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ inline void g_prologue(GHeader* hd, int stages, uint32_t tmem_cols, const CUtensorMap* m0,
+                                  const CUtensorMap* m1) {
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) {
+            tc::mbar_init(&hd->full[i], 1);
+            tc::mbar_init(&hd->xform[i], 128);
+            tc::mbar_init(&hd->empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&hd->tfull[i], 1);
+            tc::mbar_init(&hd->tempty[i], 128);
+        }
+        hd->abort = 0;
+        hd->xform_go = 0;
+        tc::mbar_init_fence();
+        tc::tma_prefetch(m0);
+        if (m1) tc::tma_prefetch(m1);
+    }
+    if (threadIdx.x / 32 == 1) tc::tmem_alloc(&hd->tmem_base, tmem_cols);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+__device__ inline void g_teardown(GHeader* hd, uint32_t tmem_cols) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (threadIdx.x / 32 == 1) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(hd->tmem_base, tmem_cols);
+    }
+}
+
+__device__ inline void g_drain(GHeader* hd, uint32_t issued, int stages, int* status) {
+    const uint32_t first = issued > (uint32_t)stages ? issued - (uint32_t)stages : 0u;
+    for (uint32_t it = first; it < issued; ++it)
+        tc::mbar_wait(&hd->full[it % stages], (it / stages) & 1u, status, 100000000ull);
+}
+
+// (hi, lo) -> three BF16 pieces whose sum is hi + lo to about 2^-24.
+__device__ __forceinline__ void split3_df(float hi, float lo, __nv_bfloat16* dst, int64_t piece_stride) {
+    const __nv_bfloat16 p1 = __float2bfloat16_rn(hi);
+    const float r1 = __fadd_rn(__fsub_rn(hi, __bfloat162float(p1)), lo);
+    const __nv_bfloat16 p2 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(p2));
+    dst[0] = p1;
+    dst[piece_stride] = p2;
+    dst[2 * piece_stride] = __float2bfloat16_rn(r2);
+}
+
+// One flush group's epilogue step for a 32-column chunk of this thread's TMEM
+// lane: fold the accumulator chunk `a` into the running sum (R, L) at column
+// offset `run`; returns the updated sum in (rh, rl).  g = group index.
+__device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col, uint32_t run_col, int m_pad, int g,
+                                           bool keep, uint32_t (&a)[32], uint32_t (&rh)[32], uint32_t (&rl)[32]) {
+    tc::tmem_ld32(lane_base + acc_col, a);
+    if (g == 0) {
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            rh[j] = a[j];
+            rl[j] = 0u;
+        }
+    } else {
+        tc::tmem_ld32(lane_base + run_col, rh);
+        tc::tmem_ld32(lane_base + run_col + (uint32_t)m_pad, rl);
+        tc::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            float hi = __uint_as_float(rh[j]), lo = __uint_as_float(rl[j]);
+            df_add(hi, lo, __uint_as_float(a[j]));
+            rh[j] = __float_as_uint(hi);
+            rl[j] = __float_as_uint(lo);
+        }
+    }
+    if (keep) {
+        tc::tmem_st32(lane_base + run_col, rh);
+        tc::tmem_st32(lane_base + run_col + (uint32_t)m_pad, rl);
+        tc::tmem_st_wait();
+    }
+}
+
+// ---------------------------------------------------------------- Y = X Q
+
+// Stage: [X area][Q piece 0 .. NV-1].  X area: BF16 X -> one 16 KB tile; FP32 X
+// -> two raw 32-column boxes (32 KB), overwritten in place by the NX pieces.
+template <int NX, int NV, bool F32X>
+__global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
+    ygen_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int ntiles, int nk,
+                int flush, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int* status) {
+    constexpr int ORD = (NX > NV ? NX : NV) - 1;
+    constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t q_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = x_bytes + NV * q_piece;
+    GHeader* hd = reinterpret_cast<GHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int ngroups = (nk + flush - 1) / flush;
+    const uint32_t tmem_cols = pow2_cols((ngroups > 1 ? 4u : 2u) * (uint32_t)m_pad);
+    g_prologue(hd, stages, tmem_cols, &tmX, &tmQ);
+    const uint32_t tmem = hd->tmem_base;
+    volatile int* abort_flag = &hd->abort;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[s], (F32X ? 2u * kPiece : kPiece) + NV * q_piece);
+                    uint8_t* st = tiles + (size_t)s * stage_bytes;
+                    if (F32X) {
+                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, t * 128);
+                        tc::tma_load_2d(st + kPiece, &tmX, &hd->full[s], k * kGBK + 32, t * 128);
+                    } else {
+                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, t * 128);
+                    }
+#pragma unroll
+                    for (int p = 0; p < NV; ++p)
+                        tc::tma_load_2d(st + x_bytes + p * q_piece, &tmQ, &hd->full[s], k * kGBK, p * m_pad);
+                }
+            }
+            if (!ok) g_drain(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int g = 0; g < ngroups && ok; ++g, ++fb) {
+                    const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                    if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
+                    const int k0 = g * flush, k1 = k0 + flush < nk ? k0 + flush : nk;
+                    uint32_t acc = 0;
+                    for (int k = k0; k < k1; ++k, ++it) {
+                        const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                        if (!tc::mbar_wait(F32X ? &hd->xform[s] : &hd->full[s], ph, status) || *abort_flag) {
+                            *abort_flag = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a0 = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < kGBK / 16; ++kk) {
+#pragma unroll
+                            for (int pa = 0; pa < NX; ++pa) {
+#pragma unroll
+                                for (int pb = 0; pb < NV; ++pb) {
+                                    if (pa + pb > ORD) continue;
+                                    const uint64_t ad = tc::smem_desc_sw128(a0 + pa * kPiece + kk * 32, 16, 1024);
+                                    const uint64_t bd =
+                                        tc::smem_desc_sw128(a0 + x_bytes + pb * q_piece + kk * 32, 16, 1024);
+                                    tc::mma_f16(d_tmem, ad, bd, idesc, acc);
+                                    acc = 1;
+                                }
+                            }
+                        }
+                        tc::mma_commit(&hd->empty[s]);
+                    }
+                    if (ok) tc::mma_commit(&hd->tfull[b]);
+                }
+            }
+        }
+    } else if (warp < 6) {
+        const int q = warp & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const int64_t piece_stride = (int64_t)m_pad * ldy;
+        uint32_t fb = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+            for (int g = 0; g < ngroups; ++g, ++fb) {
+                const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                const bool last = g == ngroups - 1;
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t a[32], rh[32], rl[32];
+                    fold_chunk(lane_base, b * (uint32_t)m_pad + (uint32_t)c0, 2u * (uint32_t)m_pad + (uint32_t)c0,
+                               m_pad, g, !last, a, rh, rl);
+                    if (last) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            split3_df(__uint_as_float(rh[j]), __uint_as_float(rl[j]),
+                                      Yt + (int64_t)(c0 + j) * ldy + row, piece_stride);
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    } else if (F32X) {
+        // Raw FP32 (two boxes of 128 rows x 32 columns, 128-byte swizzle) ->
+        // NX BF16 pieces (128 rows x 64 columns, 128-byte swizzle), in place.
+        // Task (r, c): row r, piece chunk c = columns 8c .. 8c+7 = raw box c / 4,
+        // raw chunks 2 (c % 4) and 2 (c % 4) + 1.
+        const int tid = threadIdx.x - 192;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int k = 0; k < nk; ++k, ++it) {
+                const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                if (tid == 0) {
+                    const bool go = tc::mbar_wait(&hd->full[s], ph, status) && !*abort_flag;
+                    if (!go) *abort_flag = 1;
+                    *(volatile int*)&hd->xform_go = go ? 1 : 0;
+                }
+                tc::named_barrier(1, 128);
+                if (!*(volatile int*)&hd->xform_go) {
+                    ok = false;
+                    break;
+                }
+                uint8_t* xs = tiles + (size_t)s * stage_bytes;
+                float v[8][8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int id = i * 128 + tid, r = id >> 3, c = id & 7;
+                    const uint8_t* rowp = xs + (c >> 2) * kPiece + r * 128;
+                    const int q0 = (c & 3) * 2;
+                    const float4 u0 = *reinterpret_cast<const float4*>(rowp + ((q0 ^ (r & 7)) << 4));
+                    const float4 u1 = *reinterpret_cast<const float4*>(rowp + (((q0 + 1) ^ (r & 7)) << 4));
+                    v[i][0] = u0.x; v[i][1] = u0.y; v[i][2] = u0.z; v[i][3] = u0.w;
+                    v[i][4] = u1.x; v[i][5] = u1.y; v[i][6] = u1.z; v[i][7] = u1.w;
+                }
+                tc::named_barrier(1, 128);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int id = i * 128 + tid, r = id >> 3, c = id & 7;
+                    uint32_t w[NX][4];
+#pragma unroll
+                    for (int e = 0; e < 8; e += 2) {
+                        float x0 = v[i][e], x1 = v[i][e + 1];
+#pragma unroll
+                        for (int p = 0; p < NX; ++p) {
+                            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+                            w[p][e / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
+                                          ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                            x0 = __fsub_rn(x0, __bfloat162float(h0));
+                            x1 = __fsub_rn(x1, __bfloat162float(h1));
+                        }
+                    }
+                    const uint32_t off = (uint32_t)r * 128u + (uint32_t)((c ^ (r & 7)) << 4);
+#pragma unroll
+                    for (int p = 0; p < NX; ++p)
+                        *reinterpret_cast<uint4*>(xs + p * kPiece + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+                }
+                tc::fence_proxy_async_shared();
+                tc::mbar_arrive(&hd->xform[s]);
+            }
+        }
+    }
+    g_teardown(hd, tmem_cols);
+}
+
+// ---------------------------------------------------------------- G = Y^T Y
+
+// Stage: three 16 KB slots (pieces y1, y2, y3 of 64 rows of Y, as m_pad rows of
+// Y^T x 128 B); slot rows m_pad .. 127 stay zero so the M = 128 MMA reads
+// zeros there.  CTA c takes K-stages [c kst / grid, (c + 1) kst / grid); the
+// launch keeps grid <= kst, so every CTA has at least one.
+__global__ void __launch_bounds__(kGThreadsBf16, 1)
+    gram_y_kernel(const __grid_constant__ CUtensorMap tmY, int kst, int flush, int m_pad, int stages,
+                  float2* __restrict__ Gpart, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t stage_bytes = 3u * kPiece;
+    GHeader* hd = reinterpret_cast<GHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int k0 = (int)((int64_t)blockIdx.x * kst / gridDim.x);
+    const int k1 = (int)((int64_t)(blockIdx.x + 1) * kst / gridDim.x);
+    const int ngroups = (k1 - k0 + flush - 1) / flush;
+    const uint32_t tmem_cols = pow2_cols(4u * (uint32_t)m_pad);
+    // zero the slot rows no TMA box covers
+    {
+        const uint32_t tail = (128u - (uint32_t)m_pad) * 128u / 16u;   // uint4 per slot
+        for (uint32_t e = threadIdx.x; e < (uint32_t)stages * 3u * tail; e += blockDim.x) {
+            const uint32_t slot = e / tail, w = e % tail;
+            *reinterpret_cast<uint4*>(tiles + slot * kPiece + (uint32_t)m_pad * 128u + w * 16u) =
+                make_uint4(0u, 0u, 0u, 0u);
+        }
+        tc::fence_proxy_async_shared();
+    }
+    g_prologue(hd, stages, tmem_cols, &tmY, nullptr);
+    const uint32_t tmem = hd->tmem_base;
+    volatile int* abort_flag = &hd->abort;
+    const uint32_t box_bytes = (uint32_t)m_pad * 128u;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int k = k0; k < k1; ++k, ++it) {
+                const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    g_drain(hd, it, stages, status);
+                    break;
+                }
+                tc::mbar_expect_tx(&hd->full[s], 3u * box_bytes);
+                uint8_t* st = tiles + (size_t)s * stage_bytes;
+#pragma unroll
+                for (int p = 0; p < 3; ++p) tc::tma_load_2d(st + p * kPiece, &tmY, &hd->full[s], k * kGBK, p * m_pad);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int g = 0; g < ngroups && ok; ++g) {
+                const uint32_t b = (uint32_t)g & 1u, tph = ((uint32_t)g >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
+                const int ka = k0 + g * flush, kb = ka + flush < k1 ? ka + flush : k1;
+                uint32_t acc = 0;
+                for (int k = ka; k < kb; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->full[s], ph, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < kGBK / 16; ++kk) {
+#pragma unroll
+                        for (int pa = 0; pa < 3; ++pa) {
+#pragma unroll
+                            for (int pb = 0; pb < 3; ++pb) {
+                                if (pa + pb > 2) continue;
+                                const uint64_t ad = tc::smem_desc_sw128(a0 + pa * kPiece + kk * 32, 16, 1024);
+                                const uint64_t bd = tc::smem_desc_sw128(a0 + pb * kPiece + kk * 32, 16, 1024);
+                                tc::mma_f16(d_tmem, ad, bd, idesc, acc);
+                                acc = 1;
+                            }
+                        }
+                    }
+                    tc::mma_commit(&hd->empty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->tfull[b]);
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const int i = q * 32 + lane;                 // row of G
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const bool live = q * 32 < m_pad;            // warp-uniform
+        for (int g = 0; g < ngroups; ++g) {
+            const uint32_t b = (uint32_t)g & 1u, tph = ((uint32_t)g >> 1) & 1u;
+            if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const bool last = g == ngroups - 1;
+            if (live) {
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t a[32], rh[32], rl[32];
+                    fold_chunk(lane_base, b * (uint32_t)m_pad + (uint32_t)c0, 2u * (uint32_t)m_pad + (uint32_t)c0,
+                               m_pad, g, !last, a, rh, rl);
+                    if (last) {
+                        float2* dst = Gpart + ((int64_t)blockIdx.x * m_pad + i) * m_pad + c0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dst[j] = make_float2(__uint_as_float(rh[j]), __uint_as_float(rl[j]));
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&hd->tempty[b]);
+        }
+    }
+    g_teardown(hd, tmem_cols);
+}
+
+// G[i][j] = (sum_p part_p[i][j] + sum_p part_p[j][i]) / 2 in FP64.
+__global__ void gram_parts_reduce_kernel(const float2* __restrict__ Gpart, int nparts, int m, int m_pad,
+                                         double* __restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= m * m) return;
+    const int i = e / m, j = e % m;
+    double s = 0.0;
+    for (int p = 0; p < nparts; ++p) {
+        const float2 a = Gpart[((int64_t)p * m_pad + i) * m_pad + j];
+        const float2 b = Gpart[((int64_t)p * m_pad + j) * m_pad + i];
+        s += ((double)a.x + (double)a.y) + ((double)b.x + (double)b.y);
+    }
+    G[e] = 0.5 * s;
+}
+
+template <int NX, int NV, bool F32X>
+cudaError_t launch_ygen(const CUtensorMap& tmX, const CUtensorMap& tmQ, int ntiles, int nk, int flush, int m_pad,
+                        __nv_bfloat16* Yt, int64_t ldy, int* status, int num_sms, cudaStream_t st) {
+    constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
+    const uint32_t stage_bytes = x_bytes + NV * (uint32_t)m_pad * 128u;
+    int stages = (int)((kGSmemBudget - 2048) / stage_bytes);
+    if (stages > kGMaxStages) stages = kGMaxStages;
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(GHeader);
+    auto kern = ygen_kernel<NX, NV, F32X>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    note_launch();
+    kern<<<grid, F32X ? kGThreadsF32 : kGThreadsBf16, smem, st>>>(tmX, tmQ, ntiles, nk, flush, m_pad, stages, Yt, ldy,
+                                                                 status);
+    return cudaGetLastError();
+}
+
+inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
+                              ppca_precision prec, int flush, const TcPassScratch& sc, int* status, int num_sms,
+                              cudaStream_t st) {
+    if (r1 <= r0 || m < 1 || m > 128) return cudaErrorInvalidValue;
+    const bool f32 = x.dtype == PPCA_F32;
+    const bool accurate = prec != PPCA_PREC_FAST;
+    const int m_pad = (int)rup(m, 32);
+    const int64_t d = x.d, rows = r1 - r0;
+    const int64_t ldv = rup(d, 8), ldy = rup(rows, 128);
+    const int ntiles = (int)(ldy / 128), nk = (int)((d + kGBK - 1) / kGBK);
+    const int NV = accurate ? 3 : (f32 ? 2 : 1);
+    if (flush <= 0) flush = accurate ? (f32 ? 1 : 2) : nk;
+    __nv_bfloat16* Qp = static_cast<__nv_bfloat16*>(sc.vp);
+    __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
+    cudaError_t e = launch_split_v(Q, d, m, m_pad, ldv, NV, Qp, st);
+    if (e != cudaSuccess) return e;
+    CUtensorMap tmX, tmQ, tmY;
+    const int esz = f32 ? 4 : 2;
+    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * esz;
+    const bool ok_x = f32 ? encode_2d(&tmX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, xbase, d, rows, x.ld * 4, 32, 128,
+                                      CU_TENSOR_MAP_SWIZZLE_128B)
+                          : encode_bf16_2d(&tmX, xbase, d, rows, x.ld * 2, 64, 128);
+    if (!ok_x || !encode_bf16_2d(&tmQ, Qp, d, (uint64_t)NV * m_pad, ldv * 2, 64, m_pad) ||
+        !encode_bf16_2d(&tmY, Yt, ldy, 3ull * m_pad, ldy * 2, 64, m_pad))
+        return cudaErrorInvalidValue;
+    if (f32) {
+        e = accurate ? launch_ygen<3, 3, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st)
+                     : launch_ygen<2, 2, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st);
+    } else {
+        e = accurate ? launch_ygen<1, 3, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st)
+                     : launch_ygen<1, 1, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st);
+    }
+    if (e != cudaSuccess) return e;
+    // G = Y^T Y
+    const int kst = (int)(ldy / kGBK);
+    const int grid = kst < num_sms ? kst : num_sms;
+    const int gstages = 4;
+    const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
+    e = cudaFuncSetAttribute(gram_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    float2* parts = static_cast<float2*>(sc.zacc);
+    note_launch();
+    gram_y_kernel<<<grid, kGThreadsBf16, smem, st>>>(tmY, kst, 1, m_pad, gstages, parts, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G);
+    return cudaGetLastError();
+}
+
+}  // namespace ppca

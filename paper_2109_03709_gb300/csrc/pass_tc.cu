@@ -27,6 +27,7 @@
 #include <mutex>
 
 #include "pass_tc.h"
+#include "tc_host.h"
 #include "tc_ptx.cuh"
 
 namespace ppca {
@@ -1026,6 +1027,8 @@ __global__ void zreduce_kernel(const float* __restrict__ Zacc, int Sg, int Dt, i
 
 // ---------------------------------------------------------------- host side
 
+}  // namespace
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -1057,6 +1060,23 @@ bool encode_bf16_2d(CUtensorMap* map, const void* base, uint64_t inner, uint64_t
     return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, base, inner, outer, pitch_bytes, box_inner, box_outer,
                      CU_TENSOR_MAP_SWIZZLE_128B);
 }
+
+cudaError_t launch_split_v(const float* V, int64_t d, int m, int m_pad, int64_t ldv, int S, __nv_bfloat16* Vp,
+                           cudaStream_t st) {
+    const int64_t total = (int64_t)m_pad * ldv;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4096) blocks = 4096;
+    note_launch();
+    if (S == 1)
+        split_v_kernel<1><<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv, Vp);
+    else if (S == 2)
+        split_v_kernel<2><<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv, Vp);
+    else
+        split_v_kernel<3><<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv, Vp);
+    return cudaGetLastError();
+}
+
+namespace {
 
 int stages_for(uint32_t stage_bytes) {
     int s = (int)((kSmemBudget - 2048) / stage_bytes);

@@ -17,11 +17,19 @@ struct TcSchedule {
     int fused = -1;         // 1: fused single-read kernel, 0: two GEMM kernels, -1: choose
     int producers = 0;      // CTAs running the Y = X V pipeline in the fused kernel
     int window = 0;         // tiles a producer may run ahead of the slowest consumer
+    int flush = 0;          // split-precision passes: K-stages per accumulator flush (0: default)
 };
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms);
 TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int num_sms);
 bool tc_pass_supported(const XView& x, int m);
+// G = (X[r0:r1] Q)^T (X[r0:r1] Q), m x m FP64 row-major (symmetric), for BF16 or
+// FP32 X.  ACCURATE/AUTO: split-precision products (about 2^-24); FAST: one BF16
+// piece of Q (BF16 X) or two pieces of each operand (FP32 X).  flush <= 0: the
+// library's choice of K-stages per accumulator flush.
+cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
+                              ppca_precision prec, int flush, const TcPassScratch& s, int* status, int num_sms,
+                              cudaStream_t st);
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
                      const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st);
 
