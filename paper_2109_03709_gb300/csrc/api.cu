@@ -73,7 +73,8 @@ struct ppca_handle {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int ws_m = 0;
-    int* status = nullptr;    // device status word (own allocation)
+    int* status = nullptr;    // device status word (own 256-byte allocation; status[1] is the
+                              // CholeskyQR fallback flag)
 
     float* V = nullptr;       // primed basis d x m
     float* Z = nullptr;       // pass output d x m
@@ -82,6 +83,7 @@ struct ppca_handle {
     float* buf = nullptr;     // EigenGame momentum d x m
     double* G = nullptr;      // m x m
     float* Rf = nullptr;      // m x m
+    float* Gf = nullptr;      // m x m, FP32 copy of G (CholeskyQR's FP32 attempt)
     double* w = nullptr;      // m
     double* U = nullptr;      // m x m
     float* gram_part = nullptr;
@@ -114,7 +116,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     if (h->ws && h->ws_m >= m) return PPCA_OK;
     const size_t dm = al256((size_t)d * m * sizeof(float));
     const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
-    size_t need = 5 * dm + al256((size_t)m * m * 8) + al256((size_t)m * m * 4) + al256((size_t)m * 8) +
+    size_t need = 5 * dm + al256((size_t)m * m * 8) + 2 * al256((size_t)m * m * 4) + al256((size_t)m * 8) +
                   al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
                   al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
                   al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
@@ -144,6 +146,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     h->buf = reinterpret_cast<float*>(take((size_t)d * m * 4));
     h->G = reinterpret_cast<double*>(take((size_t)m * m * 8));
     h->Rf = reinterpret_cast<float*>(take((size_t)m * m * 4));
+    h->Gf = reinterpret_cast<float*>(take((size_t)m * m * 4));
     h->w = reinterpret_cast<double*>(take((size_t)m * 8));
     h->U = reinterpret_cast<double*>(take((size_t)m * m * 8));
     h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
@@ -235,17 +238,18 @@ ppca_status run_gram(ppca_handle* h, const XView& x, const float* Q, int m, int6
 }
 
 // CholeskyQR2: Q = orth(V) with positive diagonal, Q may alias V (the first
-// pass writes the workspace buffer T, the second writes Q).  The first
-// Cholesky runs in double-float arithmetic (V may be ill-conditioned); the
-// second factors a Gram matrix within rounding of the identity, so FP32
-// suffices there.
+// pass writes the workspace buffer T, the second writes Q).  Both Gram
+// matrices are accumulated in double-float.  The first Cholesky runs in FP32
+// on the diagonally scaled Gram matrix and falls back to double-float on the
+// device when its conditioning bound says V is too ill-conditioned for that;
+// the second factors a matrix within rounding of the identity, in FP32.
 ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     const int64_t d = h->x.d;
     const float* src = V;
     for (int rep = 0; rep < 2; ++rep) {
         float* dst = rep == 0 ? h->T : Q;
-        CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream));
-        CUDA_TRY(cholesky(h->G, m, h->Rf, rep == 0, h->status, h->stream));
+        CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream, h->Gf));
+        CUDA_TRY(cholesky_adaptive(h->G, h->Gf, m, h->Rf, rep == 0, h->status + 1, h->status, h->stream));
         CUDA_TRY(apply_rinv(src, h->Rf, d, m, dst, h->stream));
         src = dst;
     }

@@ -2,8 +2,10 @@
 //
 //   gram_df          G = A^T B with double-float accumulation (CholeskyQR2's Gram,
 //                    the projected Gram of the pPCA step, Oja's Y^T Y, EigenGame's C)
-//   cholesky         G = R^T R in FP64 (one CTA)                 -- CholeskyQR2
-//   apply_rinv       Q = V R^-1 by forward substitution          -- CholeskyQR2
+//   cholesky_adaptive G = R^T R and R^-1: blocked FP32 on the diagonally scaled
+//                    G, double-float fallback when the conditioning bound fails
+//                    -- CholeskyQR2
+//   apply_rinv       Q = V R^-1                                   -- CholeskyQR2
 //   eigh_small       parallel-order Jacobi (FP32 sweeps) + FP64 Rayleigh quotients
 //                    -- the full-PCA of Algorithm 1, step 4
 //   rotate_and_sign  E = Q U[:, :k], sign convention, lambda = w / n -- step 5
@@ -24,7 +26,7 @@ namespace ppca {
 namespace {
 
 constexpr int kGramTile = 32;        // output tile of gram_df
-constexpr int kGramRows = 256;       // rows of A/B per slice
+constexpr int kGramRows = 128;       // rows of A/B per slice
 
 inline int gram_nslices(int64_t d) {
     int p = (int)((d + kGramRows - 1) / kGramRows);
@@ -57,19 +59,33 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
             Bs[rr][cc] = (r < rend && jb < m) ? B[(int64_t)jb * d + r] : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
+        // Dot2 over the 32 rows of the tile (Ogita, Rump and Oishi, "Accurate
+        // sum and dot product", 2005): the running sum sacc carries one
+        // rounding per step, whose exact error (TwoSum) and the product's
+        // (TwoProduct) go to cacc; the tile's sacc + cacc is as accurate as a
+        // dot product in twice the precision, and is folded into (hi, lo).
+        float sacc[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, cacc[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
         for (int rr = 0; rr < 32; ++rr) {
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    float pp, pe;
+                    float pp, pe, sn, se;
                     two_prod(As[rr][ty * 2 + a], Bs[rr][tx * 2 + b], pp, pe);
-                    df_add(hi[a][b], lo[a][b], pp);
-                    lo[a][b] = __fadd_rn(lo[a][b], pe);
+                    two_sum(sacc[a][b], pp, sn, se);
+                    sacc[a][b] = sn;
+                    cacc[a][b] = __fadd_rn(cacc[a][b], __fadd_rn(se, pe));
                 }
             }
         }
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                df_add(hi[a][b], lo[a][b], sacc[a][b]);
+                lo[a][b] = __fadd_rn(lo[a][b], cacc[a][b]);
+            }
         __syncthreads();
     }
 #pragma unroll
@@ -85,17 +101,22 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
         }
 }
 
-__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, bool sym, double* __restrict__ G) {
+__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, bool sym, double* __restrict__ G,
+                                   float* __restrict__ Gf) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
     const int i = idx / m, j = idx % m;
     const int src = (sym && i / kGramTile > j / kGramTile) ? j * m + i : idx;
-    double s = 0.0;
+    float hi = 0.f, lo = 0.f;
     for (int p = 0; p < P; ++p) {
-        const float* o = part + ((int64_t)p * m * m + src) * 2;
-        s += (double)o[0] + (double)o[1];
+        const float2 o = reinterpret_cast<const float2*>(part)[(int64_t)p * m * m + src];
+        df_add(hi, lo, o.x);
+        lo = __fadd_rn(lo, o.y);
     }
-    G[idx] = s;
+    float s, e;
+    two_sum(hi, lo, s, e);
+    G[idx] = (double)s + (double)e;
+    if (Gf) Gf[idx] = s;
 }
 
 // ------------------------------------------------------------------ Cholesky
@@ -114,7 +135,9 @@ constexpr int kCholThreads = 512;
 
 template <bool DF>
 __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ G, int m,
-                                                               float* __restrict__ Rinv, int* status) {
+                                                               float* __restrict__ Rinv, const int* run_if,
+                                                               int* status) {
+    if (run_if && *run_if == 0) return;      // the FP32 attempt was accepted
     extern __shared__ float csm[];
     float* ah = csm;                       // m x m, hi parts (the FP32 value when !DF)
     float* al = ah + m * m;                // m x m, lo parts (DF only)
@@ -205,34 +228,437 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
     if (threadIdx.x == 0 && broke) set_status(status, kDevCholeskyBreakdown);
 }
 
-// Q = V X with X = R^-1 upper triangular (row-major): thread = one row of V,
-// block column = 32 output columns; Q must not alias V.
-constexpr int kApplyRows = 128;
+// Blocked Cholesky in FP32 of the diagonally scaled Gram matrix G' = D G D
+// (D = diag(G)^-1/2, so G' has a unit diagonal), with the triangular inverse
+// W = R'^-1 built block by block; writes Rinv = D W, so V Rinv = V R^-1 for
+// G = R^T R.  Panels of 32 columns:
+//   (a) warp 0 factors the 32 x 32 diagonal block (lane j holds column j,
+//       pivots and rows broadcast by shuffles) and inverts it;
+//   (b) the block row of R: R_pj = W_pp^T A_pj;
+//   (c) the trailing update A_ij -= R_pi^T R_pj.
+// Then the off-diagonal blocks of W, one block diagonal at a time:
+// W_pq = -W_pp sum_{p<l<=q} R_pl W_lq.  Ten to twenty barriers in all.
+// With `fallback` set (first CholeskyQR pass, V possibly ill-conditioned) the
+// kernel bounds kappa(G') <= (max row sum |G'|) ||W||_F^2 (Gershgorin for
+// lambda_max; trace(G'^-1) = ||W||_F^2 >= 1/lambda_min).  A non-positive
+// pivot or a bound above 2^16 sets *fallback = 1 and the double-float kernel
+// redoes the factorisation.  2^16 is below 1 / (m u) for every m <= 128: an
+// exactly rank-deficient G' rounded to FP32 has lambda_min ~ m u lambda_max,
+// so it cannot pass and its breakdown is reported by the double-float kernel;
+// an accepted G' has kappa(V D) <= 256, well inside the range where an FP32
+// first pass lets the second CholeskyQR pass restore orthogonality.
+// Without `fallback` (second pass, G' within rounding of I) a non-positive
+// pivot is recorded as kDevCholeskyBreakdown.
+constexpr int kCBThreads = 512;
+constexpr int kCB = 32;
+constexpr float kCholKappaMax = 65536.f;     // 2^16
 
-__global__ void __launch_bounds__(kApplyRows) apply_rinv_kernel(const float* __restrict__ V,
-                                                                 const float* __restrict__ Rinv, int64_t d, int m,
-                                                                 float* __restrict__ Q) {
-    extern __shared__ float xs[];   // (j0 + 32) x 32 slice of X
-    const int j0 = blockIdx.y * 32;
-    const int lmax = min(m, j0 + 32);
-    for (int e = threadIdx.x; e < lmax * 32; e += blockDim.x) {
-        const int l = e / 32, jj = e % 32;
-        xs[e] = (j0 + jj < m) ? Rinv[l * m + j0 + jj] : 0.f;
+// C (m x m, upper part, row stride lda) = op(X) Y for upper-triangular X and Y
+// on 4 x 4 register tiles: TRANS_X: C = X^T Y (both read by rows); else C = X Y.
+// Block-wide; the caller synchronises before and after.
+template <bool TRANS_X>
+__device__ void upper_matmul(const float* X, const float* Y, float* C, int m, int lda) {
+    const int nq = (m + 3) / 4;
+    for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
+        const int bi = e / nq, bj = e % nq;
+        if (bi > bj) continue;
+        const int i0 = bi * 4, j0 = bj * 4;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        const int l0 = TRANS_X ? 0 : i0, l1 = TRANS_X ? min(m, i0 + 4) : min(m, j0 + 4);
+        for (int l = l0; l < l1; ++l) {
+            float xv[4];
+            if (TRANS_X) {
+                const float4 x4 = *reinterpret_cast<const float4*>(X + l * lda + i0);
+                xv[0] = x4.x; xv[1] = x4.y; xv[2] = x4.z; xv[3] = x4.w;
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = (i0 + u < m) ? X[(i0 + u) * lda + l] : 0.f;
+            }
+            const float4 y4 = *reinterpret_cast<const float4*>(Y + l * lda + j0);
+            const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = __fmaf_rn(xv[u], yv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (i0 + u < m)
+                *reinterpret_cast<float4*>(C + (i0 + u) * lda + j0) =
+                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+    }
+}
+
+// Second CholeskyQR pass: G' = I + E with small E (the first pass already
+// orthonormalised V up to rounding amplified by its conditioning).  Then
+// R' = I + N to third order in E, with N = U1 + U2: U1 = the upper triangle of
+// E with its diagonal halved, U2 the same of -U1^T U1 (from (I + N)^T (I + N)
+// = I + E); and R'^-1 = I - N + N^2 - N^3.  Neglected terms are O(|E|^3) =
+// below 1e-8 for |E|_max <= 2e-3, the acceptance bound.  Every step is a
+// parallel matrix product instead of m sequential pivots.  Returns false
+// (leaving A untouched) when |E|_max is above the bound.
+constexpr float kSeriesMax = 2e-3f;
+
+__device__ bool chol_series(float* A, float* W, const float* dsc, int m, int lda, float* __restrict__ Rinv) {
+    __shared__ float emax_w[kCBThreads / 32];
+    __shared__ int accept;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float mx = 0.f;
+    for (int e = tid; e < m * lda; e += blockDim.x) {
+        const int i = e / lda, j = e % lda;
+        if (j < m) mx = fmaxf(mx, fabsf(A[e] - (i == j ? 1.f : 0.f)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) emax_w[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        float r = 0.f;
+        for (int w = 0; w < (int)(blockDim.x / 32); ++w) r = fmaxf(r, emax_w[w]);
+        accept = (r <= kSeriesMax) ? 1 : 0;      // false for NaN
     }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * kApplyRows + threadIdx.x;
-    if (r >= d) return;
-    float acc[32];
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) acc[jj] = 0.f;
-    for (int l = 0; l < lmax; ++l) {
-        const float v = V[(int64_t)l * d + r];
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = __fmaf_rn(v, xs[l * 32 + jj], acc[jj]);
+    if (!accept) return false;
+    // W = U1
+    for (int e = tid; e < m * lda; e += blockDim.x) {
+        const int i = e / lda, j = e % lda;
+        W[e] = (j < m && i < j) ? A[e] : (i == j ? 0.5f * (A[e] - 1.f) : 0.f);
     }
+    __syncthreads();
+    upper_matmul<true>(W, W, A, m, lda);         // A = U1^T U1 (upper part)
+    __syncthreads();
+    for (int e = tid; e < m * lda; e += blockDim.x) {   // W = N = U1 + U2
+        const int i = e / lda, j = e % lda;
+        if (j < m && i < j) W[e] -= A[e];
+        else if (i == j) W[e] -= 0.5f * A[e];
+    }
+    __syncthreads();
+    upper_matmul<false>(W, W, A, m, lda);        // A = N^2
+    __syncthreads();
+    // Rinv = D (I - N + N^2 - N^3), N^3 = N N^2 on the fly
+    const int nq = (m + 3) / 4;
+    for (int e = tid; e < nq * nq; e += blockDim.x) {
+        const int bi = e / nq, bj = e % nq;
+        const int i0 = bi * 4, j0 = bj * 4;
+        float acc[4][4];
 #pragma unroll
-    for (int jj = 0; jj < 32; ++jj)
-        if (j0 + jj < m) Q[(int64_t)(j0 + jj) * d + r] = acc[jj];
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        if (bi <= bj) {
+            for (int l = i0; l < min(m, j0 + 4); ++l) {
+                float xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = (i0 + u < m) ? W[(i0 + u) * lda + l] : 0.f;
+                const float4 y4 = *reinterpret_cast<const float4*>(A + l * lda + j0);
+                const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = __fmaf_rn(xv[u], yv[v], acc[u][v]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u;
+            if (i >= m) continue;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int j = j0 + v;
+                if (j >= m) continue;
+                float r = 0.f;
+                if (i <= j) r = (i == j ? 1.f : 0.f) - W[i * lda + j] + A[i * lda + j] - acc[u][v];
+                Rinv[i * m + j] = dsc[i] * r;
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float* __restrict__ Gf, int m,
+                                                                   float* __restrict__ Rinv, int* fallback,
+                                                                   int* status, int near_identity) {
+    extern __shared__ __align__(16) float cbs[];
+    const int lda = (m + 3) & ~3;           // shared-memory row stride: rows start 16-byte aligned
+    float* A = cbs;                         // m x lda; upper triangle, rows of R' overwrite it panel by panel
+    float* W = A + m * lda;                 // m x lda, R'^-1 (upper, zero below)
+    float* T = W + m * lda;                 // (kCB x kCB) per block pair of one block diagonal
+    float* dsc = T + 3 * kCB * kCB;         // m: G_ii^-1/2
+    __shared__ int bad;
+    __shared__ float red[kCBThreads / 32];
+    __shared__ float rowsum_max;
+    const unsigned full = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = kCBThreads / 32;
+    const int nb = (m + kCB - 1) / kCB;
+    if (tid == 0) bad = 0;
+    for (int i = tid; i < m; i += kCBThreads) {
+        const float g = Gf[i * m + i];
+        dsc[i] = g > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(g)) : 0.f;
+    }
+    __syncthreads();
+    {
+        float mx = 0.f;
+        for (int i = warp; i < m; i += nw) {
+            const float di = dsc[i];
+            float sum = 0.f;
+            for (int j = lane; j < lda; j += 32) {
+                const float v = j < m ? Gf[i * m + j] * di * dsc[j] : 0.f;
+                A[i * lda + j] = v;
+                W[i * lda + j] = 0.f;
+                sum += fabsf(v);
+            }
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+            mx = fmaxf(mx, sum);
+        }
+        if (lane == 0) red[warp] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            float r = 0.f;
+            for (int w = 0; w < nw; ++w) r = fmaxf(r, red[w]);
+            rowsum_max = r;
+        }
+    }
+    if (near_identity && chol_series(A, W, dsc, m, lda, Rinv)) {
+        if (tid == 0 && fallback) *fallback = 0;
+        return;
+    }
+    for (int p = 0; p < nb; ++p) {
+        const int p0 = p * kCB, bw = min(kCB, m - p0), p1 = p0 + bw;
+        float* Ap = A + p0 * lda + p0;      // diagonal block, row stride lda
+        float* Wp = W + p0 * lda + p0;
+        // (a) warp 0: the diagonal block as R_pp = S U (U unit upper, S = diag(s))
+        // by an LDL^T elimination, then W_pp = U^-1 S^-1.  Lane j holds column j
+        // in registers, shifted each step so that the active row sits at a[0]
+        // (no dynamic register indexing); rows of U are broadcast by shuffles.
+        if (warp == 0) {
+            const bool own = lane < bw;
+            float a[kCB];
+#pragma unroll
+            for (int i = 0; i < kCB; ++i) a[i] = (own && i <= lane) ? Ap[i * lda + lane] : 0.f;
+            bool brk = false;
+            float dme = 1.f;                         // D_lane
+            for (int c = 0; c < bw; ++c) {
+                float piv = __shfl_sync(full, a[0], c);       // D_c = A_cc after the earlier columns
+                if (!(piv > 0.f)) {
+                    brk = true;
+                    piv = 1e-30f;
+                }
+                const float inv = __frcp_rn(piv);
+                const float acj = a[0];                        // A_cj (unscaled), lanes j >= c
+                const float ucj = acj * inv;                   // U_cj
+                if (own && lane > c) Ap[c * lda + lane] = ucj;
+                if (lane == c) dme = piv;
+#pragma unroll
+                for (int k = 1; k < kCB; ++k) {               // rows i = c + k: A_ij -= U_ci A_cj
+                    const float uci = __shfl_sync(full, ucj, (c + k) & (kCB - 1));
+                    if (c + k < bw && lane >= c + k) a[k] = __fmaf_rn(-uci, acj, a[k]);
+                }
+#pragma unroll
+                for (int k = 0; k < kCB - 1; ++k) a[k] = a[k + 1];
+                a[kCB - 1] = 0.f;
+            }
+            const float sme = __fsqrt_rn(dme);                 // s_lane
+            const float isme = __frcp_rn(sme);
+            __syncwarp();
+            // column `lane` of U^-1 (U x = e_lane, column-oriented back substitution), times 1/s_lane;
+            // y_i is kept at register position i + (kCB - 1 - l) while step l runs
+            float y[kCB];
+#pragma unroll
+            for (int k = 0; k < kCB; ++k) y[k] = (k - (kCB - bw) == lane) ? 1.f : 0.f;
+            for (int l = bw - 1; l >= 0; --l) {
+                const float xl = y[kCB - 1];
+                if (own) Wp[l * lda + lane] = (l <= lane) ? xl * isme : 0.f;
+#pragma unroll
+                for (int k = 0; k < kCB - 1; ++k) {           // row i = k + l - (kCB - 1) < l
+                    const int i = k + l - (kCB - 1);
+                    if (i >= 0) y[k] = __fmaf_rn(-Ap[i * lda + l], xl, y[k]);
+                }
+#pragma unroll
+                for (int k = kCB - 1; k > 0; --k) y[k] = y[k - 1];
+                y[0] = 0.f;
+            }
+            __syncwarp();
+            // R_pp = S U: row c scaled by s_c, diagonal s_c
+            for (int c = 0; c < bw; ++c) {
+                const float sc = __shfl_sync(full, sme, c);
+                if (own && lane > c) Ap[c * lda + lane] *= sc;
+                else if (lane == c) Ap[c * lda + c] = sc;
+            }
+            if (lane == 0 && brk) bad = 1;
+        }
+        __syncthreads();
+        const int nj = m - p1;
+        if (nj <= 0) continue;
+        const int nq = (nj + 3) / 4;            // column quads of the trailing part
+        // (b) block row of R: R_pj = W_pp^T A_pj; thread = (row i, column quad)
+        {
+            constexpr int kPer = (kCB * 32 + kCBThreads - 1) / kCBThreads;
+            float4 vals[kPer];
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int e = tid + q * kCBThreads;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < bw * nq) {
+                    const int i = e / nq, j0 = p1 + (e % nq) * 4;
+                    for (int l = 0; l <= i; ++l) {
+                        const float w = W[(p0 + l) * lda + p0 + i];
+                        const float4 a4 = *reinterpret_cast<const float4*>(A + (p0 + l) * lda + j0);
+                        v.x = __fmaf_rn(w, a4.x, v.x);
+                        v.y = __fmaf_rn(w, a4.y, v.y);
+                        v.z = __fmaf_rn(w, a4.z, v.z);
+                        v.w = __fmaf_rn(w, a4.w, v.w);
+                    }
+                }
+                vals[q] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < kPer; ++q) {
+                const int e = tid + q * kCBThreads;
+                if (e < bw * nq) {
+                    const int i = e / nq, j0 = p1 + (e % nq) * 4;
+                    *reinterpret_cast<float4*>(A + (p0 + i) * lda + j0) = vals[q];
+                }
+            }
+            __syncthreads();
+        }
+        // (c) trailing update A_ij -= sum_c R_ci R_cj on 4 x 4 blocks of the upper triangle
+        {
+            for (int e = tid; e < nq * nq; e += kCBThreads) {
+                const int bi = e / nq, bj = e % nq;
+                if (bi > bj) continue;
+                const int i0 = p1 + bi * 4, j0 = p1 + bj * 4;
+                float acc[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+                for (int c = 0; c < bw; ++c) {
+                    const float* r = A + (p0 + c) * lda;
+                    const float4 ri = *reinterpret_cast<const float4*>(r + i0);
+                    const float4 rj = *reinterpret_cast<const float4*>(r + j0);
+                    const float riv[4] = {ri.x, ri.y, ri.z, ri.w}, rjv[4] = {rj.x, rj.y, rj.z, rj.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = __fmaf_rn(riv[u], rjv[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (i0 + u >= m) continue;
+                    float4* dst = reinterpret_cast<float4*>(A + (i0 + u) * lda + j0);
+                    float4 d4 = *dst;
+                    d4.x -= acc[u][0];
+                    d4.y -= acc[u][1];
+                    d4.z -= acc[u][2];
+                    d4.w -= acc[u][3];
+                    *dst = d4;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // off-diagonal blocks of W, one block diagonal sd = q - p at a time; thread = (pair, row i, column quad)
+    for (int sd = 1; sd < nb; ++sd) {
+        const int npairs = nb - sd;
+        for (int e = tid; e < npairs * kCB * (kCB / 4); e += kCBThreads) {
+            const int p = e / (kCB * kCB / 4), r = e % (kCB * kCB / 4), i = r / (kCB / 4), j = (r % (kCB / 4)) * 4;
+            const int p0 = p * kCB, q0 = (p + sd) * kCB;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (p0 + i < m && q0 + j < m) {
+                const int cend = min(m, q0 + j + 4);
+                for (int c = p0 + kCB; c < cend; ++c) {
+                    const float rv = A[(p0 + i) * lda + c];
+                    const float4 w4 = *reinterpret_cast<const float4*>(W + c * lda + q0 + j);
+                    acc.x = __fmaf_rn(rv, w4.x, acc.x);
+                    acc.y = __fmaf_rn(rv, w4.y, acc.y);
+                    acc.z = __fmaf_rn(rv, w4.z, acc.z);
+                    acc.w = __fmaf_rn(rv, w4.w, acc.w);
+                }
+            }
+            *reinterpret_cast<float4*>(T + p * kCB * kCB + i * kCB + j) = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < npairs * kCB * (kCB / 4); e += kCBThreads) {
+            const int p = e / (kCB * kCB / 4), r = e % (kCB * kCB / 4), i = r / (kCB / 4), j = (r % (kCB / 4)) * 4;
+            const int p0 = p * kCB, q0 = (p + sd) * kCB;
+            if (p0 + i >= m || q0 + j >= m) continue;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int c = i; c < kCB; ++c) {
+                const float wv = W[(p0 + i) * lda + p0 + c];
+                const float4 t4 = *reinterpret_cast<const float4*>(T + p * kCB * kCB + c * kCB + j);
+                acc.x = __fmaf_rn(-wv, t4.x, acc.x);
+                acc.y = __fmaf_rn(-wv, t4.y, acc.y);
+                acc.z = __fmaf_rn(-wv, t4.z, acc.z);
+                acc.w = __fmaf_rn(-wv, t4.w, acc.w);
+            }
+            *reinterpret_cast<float4*>(W + (p0 + i) * lda + q0 + j) = acc;
+        }
+        __syncthreads();
+    }
+    // kappa bound, then Rinv = D W
+    {
+        float wf = 0.f;
+        for (int e = tid; e < m * lda; e += kCBThreads) wf = __fmaf_rn(W[e], W[e], wf);
+        for (int o = 16; o > 0; o >>= 1) wf += __shfl_xor_sync(full, wf, o);
+        if (lane == 0) red[warp] = wf;
+        __syncthreads();
+        if (tid == 0) {
+            float t = 0.f;
+            for (int w = 0; w < nw; ++w) t += red[w];
+            const bool reject = bad || !(rowsum_max * t <= kCholKappaMax);
+            if (fallback) *fallback = reject ? 1 : 0;
+            else if (bad) set_status(status, kDevCholeskyBreakdown);
+        }
+    }
+    for (int i = warp; i < m; i += nw) {
+        const float di = dsc[i];
+        for (int j = lane; j < m; j += 32) Rinv[i * m + j] = di * W[i * lda + j];
+    }
+}
+
+// Q = V X with X = R^-1 upper triangular (row-major).  A block takes 16 rows
+// of V (staged in shared memory, read as broadcasts) and thread c computes
+// output column c for them: Q[r, c] = sum_{l <= c} V[r, l] X[l, c], X read
+// from global memory (the same m x m matrix for every block, cached).
+// Q must not alias V.
+constexpr int kApplyRows = 16;
+
+__global__ void __launch_bounds__(128) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
+                                                         int64_t d, int m, float* __restrict__ Q) {
+    __shared__ __align__(16) float vs[128][kApplyRows];
+    const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
+    for (int e = threadIdx.x; e < m * kApplyRows; e += blockDim.x) {
+        const int l = e / kApplyRows, r = e % kApplyRows;
+        vs[l][r] = (r0 + r < d) ? V[(int64_t)l * d + r0 + r] : 0.f;
+    }
+    __syncthreads();
+    const int c = threadIdx.x;
+    if (c >= m) return;
+    float acc[kApplyRows];
+#pragma unroll
+    for (int r = 0; r < kApplyRows; ++r) acc[r] = 0.f;
+#pragma unroll 2
+    for (int l = 0; l <= c; ++l) {
+        const float x = __ldg(Rinv + l * m + c);
+        const float4* v4 = reinterpret_cast<const float4*>(vs[l]);
+#pragma unroll
+        for (int q = 0; q < kApplyRows / 4; ++q) {
+            const float4 v = v4[q];
+            acc[4 * q + 0] = __fmaf_rn(v.x, x, acc[4 * q + 0]);
+            acc[4 * q + 1] = __fmaf_rn(v.y, x, acc[4 * q + 1]);
+            acc[4 * q + 2] = __fmaf_rn(v.z, x, acc[4 * q + 2]);
+            acc[4 * q + 3] = __fmaf_rn(v.w, x, acc[4 * q + 3]);
+        }
+    }
+    float* out = Q + (int64_t)c * d + r0;
+#pragma unroll
+    for (int r = 0; r < kApplyRows; ++r)
+        if (r0 + r < d) out[r] = acc[r];
 }
 
 // ------------------------------------------------------------------ Jacobi
@@ -663,41 +1089,42 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 size_t gram_part_floats(int64_t d, int m) { return (size_t)gram_nslices(d) * m * m * 2; }
 
-cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st) {
+cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st,
+                    float* Gf) {
     const int P = gram_nslices(d);
     const int64_t slice = (d + P - 1) / P;
     const int T = (m + kGramTile - 1) / kGramTile;
     note_launch();
     gram_df_kernel<<<dim3(T, T, P), 256, 0, st>>>(A, B, d, m, part, slice);
     note_launch();
-    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G);
+    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G, Gf);
     return cudaGetLastError();
 }
 
-cudaError_t cholesky(const double* G, int m, float* Rinv, bool double_float, int* status, cudaStream_t st) {
-    cudaError_t e;
-    if (double_float) {
-        const size_t smem = (size_t)3 * m * m * sizeof(float);
-        e = allow_smem(cholesky_kernel<true>, smem);
-        if (e != cudaSuccess) return e;
-        note_launch();
-        cholesky_kernel<true><<<1, kCholThreads, smem, st>>>(G, m, Rinv, status);
-    } else {
-        const size_t smem = (size_t)2 * m * m * sizeof(float);
-        e = allow_smem(cholesky_kernel<false>, smem);
-        if (e != cudaSuccess) return e;
-        note_launch();
-        cholesky_kernel<false><<<1, kCholThreads, smem, st>>>(G, m, Rinv, status);
-    }
+cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
+                              int* status, cudaStream_t st) {
+    const size_t lda = (size_t)((m + 3) & ~3);
+    const size_t smem = ((size_t)2 * m * lda + 3 * kCB * kCB + m) * sizeof(float);
+    cudaError_t e = allow_smem(chol_blocked_kernel, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    chol_blocked_kernel<<<1, kCBThreads, smem, st>>>(Gf, m, Rinv, may_fall_back ? flag : nullptr, status,
+                                                      may_fall_back ? 0 : 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !may_fall_back) return e;
+    const size_t smem_df = (size_t)3 * m * m * sizeof(float);
+    e = allow_smem(cholesky_kernel<true>, smem_df);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    cholesky_kernel<true><<<1, kCholThreads, smem_df, st>>>(G, m, Rinv, flag, status);
     return cudaGetLastError();
 }
 
 cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st) {
-    if (V == Q) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)m * 32 * sizeof(float);
+    if (V == Q || m > 128) return cudaErrorInvalidValue;
+    const int threads = (m + 31) / 32 * 32;
     note_launch();
-    apply_rinv_kernel<<<dim3(ceil_div_i(d, kApplyRows), ceil_div_i(m, 32)), kApplyRows, smem, st>>>(V, Rinv, d, m,
-                                                                                                     Q);
+    apply_rinv_kernel<<<ceil_div_i(d, kApplyRows), threads, 0, st>>>(V, Rinv, d, m, Q);
     return cudaGetLastError();
 }
 

@@ -144,7 +144,7 @@ def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window):
     assert normwise(Zg, host_basis(Zu)) <= 1e-5
 
 
-@pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (4096, 128)])
+@pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (300, 33), (2000, 100), (4096, 128)])
 def test_cholesky_qr2_matches_thin_qr(P, d, m):
     V = synth.initial_basis(d, m, seed=d)
     Vd = dev_basis(V)
@@ -176,10 +176,41 @@ def test_cholesky_qr2_ill_conditioned(P):
     assert oracle.principal_angles(Q, host_basis(Vd)).max() < 1e-2
 
 
+@pytest.mark.parametrize("kappa", [1.0, 30.0, 300.0, 3e3, 3e4, 1e6])
+def test_cholesky_qr2_conditioning_sweep(P, kappa):
+    """Across the switch between the FP32 first pass (accepted while the bound
+    on kappa(V D)^2 stays below 2^16) and its double-float fallback: Q is
+    orthonormal to 1e-5 and spans span(V) to kappa * 1e-7; for kappa <= 3e4 it equals the
+    unique thin-QR factor of the oracle to kappa * 1e-7 (FP32 input V carries
+    relative rounding 6e-8, amplified by kappa in R)."""
+    d, m = 2048, 128
+    rng = np.random.default_rng(int(kappa))
+    U, _ = np.linalg.qr(rng.standard_normal((d, m)))
+    W, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    s = np.logspace(0, -np.log10(kappa), m)
+    V = (U * s[None, :]) @ W.T
+    V = V * rng.uniform(0.1, 10.0, m)[None, :]               # column scales the diagonal scaling removes
+    Vd = dev_basis(V)
+    Qd = empty_basis(d, m)
+    h = P.ppca_create(dev_matrix(np.zeros((2, d)), "f32"))
+    P.ppca_orthonormalize(h, Vd, Qd, m)
+    P.ppca_sync(h)
+    Q = host_basis(Qd)
+    assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-5
+    # span(V) itself is only defined to ~kappa u by the FP32 input and arithmetic
+    assert oracle.principal_angles(Q, host_basis(Vd)).max() < 1e-5 + kappa * 1e-7
+    if kappa <= 3e4:
+        assert np.abs(Q - oracle.orth(host_basis(Vd))).max() <= max(1e-5, kappa * 1e-7)
+
+
 def test_cholesky_breakdown_is_reported(P):
+    """A zero column makes a pivot exactly zero in every precision.  (An exactly
+    repeated column leaves a pivot at the rounding level of the double-float
+    factorisation, ~1e-14 of the diagonal, which may land on either side of the
+    1e-15 * trace(G) floor, so it is not a deterministic case.)"""
     d, m = 128, 8
     V = synth.initial_basis(d, m, seed=2)
-    V[:, 5] = V[:, 2]                                       # rank-deficient
+    V[:, 5] = 0.0                                           # rank-deficient
     h = P.ppca_create(dev_matrix(np.zeros((2, d)), "f32"))
     Qd = empty_basis(d, m)
     P.ppca_orthonormalize(h, dev_basis(V), Qd, m)
