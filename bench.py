@@ -398,6 +398,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     P.ppca_batch_sync(b)
+    kernels = P.ppca_batch_kernel_count(b)
     ms = e0.elapsed_time(e1)
     peaks, peak_kind = measured_peaks()
     value = total_bytes * args.steps / (ms / 1e3) / 1e9
@@ -407,11 +408,13 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": 8,
                        "bytes_per_step": total_bytes, "form": "one CUDA-graph launch per step",
-                       "l2": "inputs (142 GB) larger than L2, no flush"},
+                       "l2": f"inputs ({sum(i['X'].numel() * 4 for i in inst) / 1e9:.0f} GB) larger than L2, "
+                             "no flush"},
             "roofline": {"bound": "hbm", "achieved": round(value, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(value / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": peak_kind,
-                         "kernel": "whole batch step (FP32 CUDA-core X-passes dominate)"},
-            "clocks": clk, "gpu_launches": None}
+                         "kernel": "whole batch step: 3xTF32 priming passes, projected-Gram pPCA step, "
+                                   "CholeskyQR2 and Jacobi per instance"},
+            "clocks": clk, "gpu_launches": kernels * args.steps}
     if rank == 0:
         print(json.dumps(line))
 

@@ -272,6 +272,10 @@ PPCA_API ppca_status ppca_batch_create(ppca_batch **out, const ppca_instance_des
  */
 PPCA_API ppca_status ppca_batch_run(ppca_batch *b);
 
+/* Kernel launches one ppca_batch_run performs (the kernels captured in its graph;
+ * 0 before the first run). */
+PPCA_API ppca_status ppca_batch_kernel_count(const ppca_batch *b, int64_t *count);
+
 /* Wait for the batch's stream; report the first device-side error of any slot. */
 PPCA_API ppca_status ppca_batch_sync(ppca_batch *b);
 

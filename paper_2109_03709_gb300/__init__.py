@@ -26,7 +26,8 @@ __all__ = [
     "ppca_projected_gram",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
-    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "EXPORTED_SYMBOLS",
+    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
+    "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,7 +47,7 @@ EXPORTED_SYMBOLS = [
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram",
-    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy",
+    "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
 ]
 
 
@@ -143,6 +144,7 @@ _SIGS = {
     "ppca_batch_run": (_c_status, [_vp]),
     "ppca_batch_sync": (_c_status, [_vp]),
     "ppca_batch_destroy": (_c_status, [_vp]),
+    "ppca_batch_kernel_count": (_c_status, [_vp, ctypes.POINTER(_i64)]),
 }
 
 
@@ -369,6 +371,13 @@ def ppca_batch_create(instances, slots: int = 0, stream=None) -> Batch:
 
 def ppca_batch_run(b: Batch):
     _check(load_library().ppca_batch_run(b.ptr), "ppca_batch_run")
+
+
+def ppca_batch_kernel_count(b: Batch) -> int:
+    """Kernel launches one ppca_batch_run performs (0 before the first run)."""
+    c = _i64(0)
+    _check(load_library().ppca_batch_kernel_count(b.ptr, ctypes.byref(c)), "ppca_batch_kernel_count")
+    return int(c.value)
 
 
 def ppca_batch_sync(b: Batch):

@@ -693,6 +693,7 @@ struct ppca_batch {
     cudaEvent_t fork = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;                  // kernel launches captured in the graph
 };
 
 namespace {
@@ -815,6 +816,7 @@ ppca_status ppca_batch_run(ppca_batch* b) {
     if (!b->exec) {
         const int nslots = (int)b->slots.size();
         CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const int64_t launches0 = launches_so_far();
         ppca_status st = PPCA_OK;
         cudaError_t e = cudaEventRecord(b->fork, b->stream);
         for (int s = 0; s < nslots && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->slot_streams[s], b->fork, 0);
@@ -845,6 +847,7 @@ ppca_status ppca_batch_run(ppca_batch* b) {
                         cudaGetErrorString(e != cudaSuccess ? e : ee));
         }
         b->graph = g;
+        b->kernels = launches_so_far() - launches0;
         CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
     }
     CUDA_TRY(cudaEventRecord(b->ev_in, b->user_stream));
@@ -852,6 +855,12 @@ ppca_status ppca_batch_run(ppca_batch* b) {
     CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
     CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
     CUDA_TRY(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_kernel_count(const ppca_batch* b, int64_t* count) {
+    if (!b || !count) return fail(PPCA_ERR_INVALID, "NULL argument");
+    *count = b->kernels;
     return PPCA_OK;
 }
 

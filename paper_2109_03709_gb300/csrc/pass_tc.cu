@@ -115,10 +115,15 @@ __device__ inline void drain_copies(SmemHeader* hd, uint32_t issued, int stages,
 
 // ---------------------------------------------------------------- Y = X V
 
+// Split K: with ksplit > 1 a task is (tile t, K-range ks) and writes its FP32
+// partial Y rows to Ypart[ks][row][m_pad]; ypart_reduce_kernel sums them and
+// splits the sum into the BF16 pieces (for few row tiles and large d, e.g. a
+// minibatch of a wide matrix).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     xv_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
-                 int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int* status) {
+                 int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int ksplit,
+                 float* __restrict__ Ypart, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t a_bytes = 128u * 128u;
@@ -134,8 +139,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int k = 0; k < nk; ++k, ++it) {
+            for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x) {
+                const int t = task / ksplit, ks = task % ksplit;
+                const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
+                for (int k = k0; k < k1; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
                         hd->abort = 1;
@@ -157,7 +164,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
             uint32_t it = 0, tl = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+            for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x, ++tl) {
+                const int ks = task % ksplit;
+                const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
                 const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
                     hd->abort = 1;
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc::fence_after_sync();
                 const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
-                for (int k = 0; k < nk; ++k, ++it) {
+                for (int k = k0; k < k1; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
                         hd->abort = 1;
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int p = 0; p < S; ++p) {
                             const uint64_t bdesc =
                                 tc::smem_desc_sw128(a_addr + a_bytes + p * b_piece + kk * 32, 16, 1024);
-                            tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k | kk | p) != 0);
+                            tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k != k0 || kk != 0 || p != 0) ? 1u : 0u);
                         }
                     }
                     tc::mma_commit(&hd->empty[s]);
@@ -192,7 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         const int q = warp & 3;
         uint32_t tl = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+        for (int task = blockIdx.x; task < ntiles * ksplit; task += gridDim.x, ++tl) {
+            const int t = task / ksplit, ks = task % ksplit;
             const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
             if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
                 hd->abort = 1;
@@ -204,9 +214,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
+                if (ksplit == 1) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    split_store<S>(__uint_as_float(r[j]), Yt + (int64_t)(c0 + j) * ldy + row, (int64_t)m_pad * ldy);
+                    for (int j = 0; j < 32; ++j)
+                        split_store<S>(__uint_as_float(r[j]), Yt + (int64_t)(c0 + j) * ldy + row,
+                                       (int64_t)m_pad * ldy);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(Ypart + ((int64_t)ks * ldy + row) * m_pad + c0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                }
             }
             tc::fence_before_sync();
             tc::mbar_arrive(&hd->tempty[b]);
@@ -1009,6 +1028,20 @@ __global__ void split_v_kernel(const float* __restrict__ V, int64_t d, int m, in
     }
 }
 
+// Y = sum over the K-ranges of the split-K partials, then the S BF16 pieces of Y^T.
+template <int S>
+__global__ void ypart_reduce_kernel(const float* __restrict__ Ypart, int ksplit, int64_t ldy, int m_pad,
+                                    __nv_bfloat16* __restrict__ Yt) {
+    const int64_t total = ldy * m_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / m_pad;
+        const int c = (int)(e % m_pad);
+        float acc = 0.f;
+        for (int ks = 0; ks < ksplit; ++ks) acc += Ypart[(int64_t)ks * total + e];
+        split_store<S>(acc, Yt + (int64_t)c * ldy + row, (int64_t)m_pad * ldy);
+    }
+}
+
 __global__ void zreduce_kernel(const float* __restrict__ Zacc, int Sg, int Dt, int64_t d, int m, int m_pad,
                                float* __restrict__ Z) {
     const int64_t total = d * m;
@@ -1169,10 +1202,28 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const size_t smem = smem_bytes(stages, stage_bytes);
         e = cudaFuncSetAttribute(xv_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int grid = ps.ntiles < num_sms ? ps.ntiles : num_sms;
+        // few row tiles (a minibatch) and a long K: split K so that every SM has work
+        int ksplit = 1;
+        if (ps.ntiles * 2 <= num_sms && ps.nk >= 8) {
+            ksplit = (2 * num_sms + ps.ntiles - 1) / ps.ntiles;
+            ksplit = std::min(ksplit, ps.nk / 4);
+            const int64_t cap = (int64_t)(sc.z_bytes / ((size_t)ps.ldy * ps.m_pad * sizeof(float)));
+            ksplit = (int)std::min<int64_t>(ksplit, cap);
+            if (ksplit < 2) ksplit = 1;
+        }
+        const int ntask = ps.ntiles * ksplit;
+        const int grid = ntask < num_sms ? ntask : num_sms;
+        float* Ypart = static_cast<float*>(sc.zacc);
         note_launch();
         xv_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXa, tmV, ps.ntiles, ps.nk, ps.m_pad, stages, Yt, ps.ldy,
-                                                       status);
+                                                       ksplit, Ypart, status);
+        if (ksplit > 1) {
+            const int64_t total = ps.ldy * ps.m_pad;
+            int blocks = (int)((total + 255) / 256);
+            if (blocks > 4096) blocks = 4096;
+            note_launch();
+            ypart_reduce_kernel<S><<<blocks, 256, 0, st>>>(Ypart, ksplit, ps.ldy, ps.m_pad, Yt);
+        }
     }
     int Sg;
     {
@@ -1319,6 +1370,7 @@ TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int
     s.yt = p;
     p += al(L.yt_bytes);
     s.zacc = p;
+    s.z_bytes = L.z_bytes;
     p += al(L.z_bytes);
     s.flags = reinterpret_cast<int*>(p);
     return s;

@@ -9,6 +9,8 @@ struct TcPassScratch {
     void* vp = nullptr;     // V pieces, [3][128][round_up(d, 8)] BF16
     void* yt = nullptr;     // Y^T pieces, [3][128][round_up(n, 128)] BF16
     void* zacc = nullptr;   // double-float Z partials, [row group][d slice * 128][128] x 2 FP32
+                            // (also split-K partials of Y and the projected Gram's partials)
+    size_t z_bytes = 0;     // capacity of zacc
     int* flags = nullptr;   // fused pass: ready[tiles], consumed[tiles]
 };
 

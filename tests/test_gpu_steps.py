@@ -85,14 +85,17 @@ BF16_CASES = [
     (5000, 1024, 128, 0, 5000),
     (600000, 64, 16, 0, 600000),     # many tiles per CTA, several flush blocks per row group
     (4096, 4096, 128, 0, 4096),
+    (1000, 8192, 64, 0, 512),        # few row tiles, long K: split-K Y = X V
+    (700, 20000, 32, 3, 300),        # split-K with ragged rows and a ragged last K-stage
 ]
 
 
 @pytest.mark.parametrize("n,d,m,r0,r1", BF16_CASES)
 @pytest.mark.parametrize("prec,tol", [("FAST", 1e-2), ("ACCURATE", 2e-5)])
 def test_xpass_bf16(P, n, d, m, r0, r1, prec, tol):
-    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=9) if n * d <= 5e7 else \
-        (np.random.default_rng(9).standard_normal((n, d)), None)
+    # a Haar rotation costs O(d^3) on the host: wide or very tall cases use axis-aligned data
+    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=9) if n * d <= 5e7 and d <= 4096 else \
+        (np.random.default_rng(9).standard_normal((n, d)) * (0.97 ** np.arange(1, d + 1))[None, :] ** 0.5, None)
     Xd = dev_matrix(X, "bf16")
     V = synth.initial_basis(d, m, seed=3)
     Vd = dev_basis(V)
@@ -140,8 +143,10 @@ def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window):
     assert normwise(Zg, Zref) <= 1e-2
     for c in range(m):
         assert normwise(Zg[:, c], Zref[:, c]) <= 4e-2
-    # same Y rounding as the two-kernel pass: only the FP32 summation order differs
-    assert normwise(Zg, host_basis(Zu)) <= 1e-5
+    # the two-kernel pass rounds the same Y to BF16, except where it splits K over
+    # CTAs (few row tiles): there a summation-order difference can move a Y element
+    # to the neighbouring BF16 value (2^-8 relative); a few such elements move Z by ~1e-5
+    assert normwise(Zg, host_basis(Zu)) <= 1e-4
 
 
 @pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (300, 33), (2000, 100), (4096, 128)])
