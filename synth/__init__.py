@@ -13,6 +13,9 @@ Generators:
   orthogonal to the all-ones vector, so X is centred and X^T X = Q diag(sigma^2)
   Q^T holds up to rounding: eigenpairs known in closed form.
 * ``initial_basis``: Gaussian d x m starting basis for the primers.
+* ``hadamard_rotated_data_torch``: the known-lambda recipe for very wide X
+  (d = 2^18), with a structured orthogonal Q = H D1 P H D2 applied by fast
+  Walsh-Hadamard transforms instead of a stored Haar matrix.
 
 Small problems are drawn with numpy on the host (float64, then rounded to the
 storage type).  Large problems (``*_torch``) are drawn on a torch device in
@@ -159,6 +162,72 @@ def instance_data_torch(n: int, d: int, lam, seed: int, device, out_dtype):
     X = torch.randn((n, d), generator=gen, device=device, dtype=torch.float32) @ B
     X -= X.double().mean(0).float()[None, :]
     return X.to(out_dtype) if out_dtype != torch.float32 else X
+
+
+def _fwht_rows_(Y):
+    """In-place normalised Walsh-Hadamard transform of each row of Y (last dim a power of two)."""
+    import torch
+    n, d = Y.shape
+    h = 1
+    while h < d:
+        v = Y.view(n, d // (2 * h), 2, h)
+        a = v[:, :, 0, :].clone()
+        v[:, :, 0, :] += v[:, :, 1, :]
+        v[:, :, 1, :] *= -1.0
+        v[:, :, 1, :] += a
+        h *= 2
+    Y *= 1.0 / math.sqrt(d)
+    return Y
+
+
+def hadamard_rotated_data_torch(n: int, d: int, lam, seed: int, device, out_dtype, chunk_rows: int = 1024):
+    """X = G diag(sqrt(lam)) Q^T for d a power of two, Q = H D1 P H D2 (H the normalised
+    Walsh-Hadamard matrix, D1, D2 random sign diagonals, P a random permutation), columns
+    centred, stored as ``out_dtype``.  Q is orthogonal and never formed: each row is
+    rotated with two fast transforms, so d = 2^18 fits.  Drawn on ``device`` in row chunks
+    from per-chunk torch generators (two passes: column means, then the centred rows).
+    Returns (X, (D1, perm, D2)) with the signs and permutation as host arrays.
+    """
+    import torch
+
+    assert d & (d - 1) == 0, "d must be a power of two"
+    lam = np.asarray(lam, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    D1 = rng.choice([-1.0, 1.0], size=d)
+    D2 = rng.choice([-1.0, 1.0], size=d)
+    perm = rng.permutation(d)
+    sq = torch.from_numpy(np.sqrt(lam)).to(device=device, dtype=torch.float32)
+    d1 = torch.from_numpy(D1).to(device=device, dtype=torch.float32)
+    d2 = torch.from_numpy(D2).to(device=device, dtype=torch.float32)
+    pinv = torch.from_numpy(np.argsort(perm)).to(device=device)
+
+    def rows(c):
+        r0 = c * chunk_rows
+        r1 = min(n, r0 + chunk_rows)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed) * 1000003 + c)
+        Y = torch.randn((r1 - r0, d), generator=gen, device=device, dtype=torch.float32)
+        Y *= sq[None, :]                  # G diag(sqrt(lam))
+        Y *= d2[None, :]                  # ... Q^T = D2 H P^T D1 H, applied on the right
+        _fwht_rows_(Y)
+        Y = Y[:, pinv]
+        Y *= d1[None, :]
+        _fwht_rows_(Y)
+        return r0, r1, Y
+
+    nchunks = (n + chunk_rows - 1) // chunk_rows
+    mean = torch.zeros(d, dtype=torch.float64, device=device)
+    for c in range(nchunks):
+        _, _, Y = rows(c)
+        mean += Y.double().sum(0)
+    mean /= n
+    meanf = mean.float()
+    X = torch.empty((n, d), dtype=out_dtype, device=device)
+    for c in range(nchunks):
+        r0, r1, Y = rows(c)
+        Y -= meanf[None, :]
+        X[r0:r1] = Y.to(out_dtype)
+    return X, (D1, perm, D2)
 
 
 def counterexample_points():
