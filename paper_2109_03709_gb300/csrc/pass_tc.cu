@@ -440,6 +440,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     if (warp == 0) {
         // ---------------- producer TMA
         if (lane == 0 && producer) {
+            // X tiles stay in L2 until their consumers have re-read them (evict_last
+            // here, evict_first on the consumers' reads)
+            const uint64_t keep = tc::policy_evict_last();
             uint32_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += NP) {
@@ -456,7 +459,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     }
                     tc::mbar_expect_tx(&hd->pfull[s], p_stage);
                     uint8_t* st = ptiles + (size_t)s * p_stage;
-                    tc::tma_load_2d(st, &tmXa, &hd->pfull[s], k * kBK, t * 128);
+                    tc::tma_load_2d_hint(st, &tmXa, &hd->pfull[s], k * kBK, t * 128, keep);
                     tc::tma_load_2d(st + p_a, &tmV, &hd->pfull[s], k * kBK, 0);
                 }
             }
@@ -532,6 +535,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     } else if (warp == 6) {
         // ---------------- consumer TMA
         if (lane == 0 && consumer) {
+            const uint64_t drop = tc::policy_evict_first();
             uint32_t it = 0;
             bool ok = true;
             for (int t = cg; t < ntiles && ok; t += Sg) {
@@ -552,7 +556,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     const int y = t * 128 + kk2 * 64;
 #pragma unroll
                     for (int bx = 0; bx < 4; ++bx)
-                        tc::tma_load_2d(st + bx * 8192, &tmXb, &hd->cfull[s], sp * 256 + bx * 64, y);
+                        tc::tma_load_2d_hint(st + bx * 8192, &tmXb, &hd->cfull[s], sp * 256 + bx * 64, y, drop);
                     tc::tma_load_2d(st + c_a, &tmY, &hd->cfull[s], y, 0);
                 }
             }
