@@ -555,6 +555,9 @@ def run_batch(args):
         total_bytes += (T + 1) * n * d * 4
     stream = torch.cuda.current_stream()
     b = P.ppca_batch_create(inst, slots=8, stream=stream)
+    t_tune = time.perf_counter()
+    groups = P.ppca_batch_autotune(b, 2)
+    t_tune = time.perf_counter() - t_tune
     for _ in range(max(args.warmup, 1)):
         P.ppca_batch_run(b)
     P.ppca_batch_sync(b)
@@ -579,6 +582,7 @@ def run_batch(args):
             "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": 8,
+                       "autotune": {"groups": groups, "seconds": round(t_tune, 1)},
                        "bytes_per_step": total_bytes, "form": "one CUDA-graph launch per step",
                        "l2": f"inputs ({sum(i['X'].numel() * 4 for i in inst) / 1e9:.0f} GB) larger than L2, "
                              "no flush"},

@@ -199,10 +199,23 @@ typedef struct ppca_schedule {
     int32_t flush;            /* split-precision passes: K-stages (64 wide) an FP32 tensor-core   */
                               /* accumulator takes before it is folded into a double-float sum    */
                               /* (0: library default; larger = faster, less accurate)             */
+    int32_t engine;           /* X-pass engine: 0 library choice, 1 tensor cores (BF16 / FP32     */
+                              /* data), 2 CUDA cores (any data type)                              */
 } ppca_schedule;
 
 /* Set the X-pass schedule of a handle (takes effect at its next pass). */
 PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
+
+/*
+ * Autotuner: time one fast X-pass over rows [0, rows) of the handle's data
+ * (rows = 0: all n) with m directions for every candidate schedule -- engine
+ * (tensor cores / CUDA cores) and, for BF16 data, the fused single-read pass
+ * or two kernels -- taking the fastest of `reps` timed runs after a warm-up
+ * each, then set the winner on the handle and copy it to *best (may be NULL).
+ * Uses the handle's scratch buffers (not the primed basis); blocks the host
+ * until the handle's stream is idle.
+ */
+PPCA_API ppca_status ppca_autotune(ppca_handle *h, int32_t m, int64_t rows, int32_t reps, ppca_schedule *best);
 
 /* Device-time accounting of the X-passes (the hot step), for measurement. */
 typedef struct ppca_timing {
@@ -271,6 +284,16 @@ PPCA_API ppca_status ppca_batch_create(ppca_batch **out, const ppca_instance_des
  * the batch's stream (asynchronous).
  */
 PPCA_API ppca_status ppca_batch_run(ppca_batch *b);
+
+/*
+ * Tune the batch before its first run: instances are grouped by (data type,
+ * d, m, n rounded up to a power of two); for each group the autotuner
+ * (ppca_autotune, cooperative fused pass excluded because slots run
+ * concurrently) times the candidates on the group's first instance, and every
+ * instance of the group then runs with the winner.  Returns the number of
+ * groups in *groups (may be NULL).  PPCA_ERR_STATE after the first run.
+ */
+PPCA_API ppca_status ppca_batch_autotune(ppca_batch *b, int32_t reps, int32_t *groups);
 
 /* Kernel launches one ppca_batch_run performs (the kernels captured in its graph;
  * 0 before the first run). */

@@ -23,7 +23,7 @@ __all__ = [
     "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
-    "ppca_projected_gram",
+    "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
@@ -46,7 +46,7 @@ EXPORTED_SYMBOLS = [
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
     "ppca_sync", "ppca_get_state", "ppca_set_state", "ppca_destroy", "ppca_xpass", "ppca_orthonormalize",
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
-    "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram",
+    "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
 ]
 
@@ -87,6 +87,7 @@ class ppca_schedule(ctypes.Structure):
         ("producers", ctypes.c_int32),
         ("window", ctypes.c_int32),
         ("flush", ctypes.c_int32),
+        ("engine", ctypes.c_int32),
     ]
 
 
@@ -140,6 +141,8 @@ _SIGS = {
     "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
     "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "ppca_set_schedule": (_c_status, [_vp, ctypes.POINTER(ppca_schedule)]),
+    "ppca_autotune": (_c_status, [_vp, _i32, _i64, _i32, ctypes.POINTER(ppca_schedule)]),
+    "ppca_batch_autotune": (_c_status, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ppca_batch_create": (_c_status, [ctypes.POINTER(_vp), ctypes.POINTER(ppca_instance_desc), _i32, _i32, _vp]),
     "ppca_batch_run": (_c_status, [_vp]),
     "ppca_batch_sync": (_c_status, [_vp]),
@@ -373,6 +376,13 @@ def ppca_batch_run(b: Batch):
     _check(load_library().ppca_batch_run(b.ptr), "ppca_batch_run")
 
 
+def ppca_batch_autotune(b: Batch, reps: int = 2) -> int:
+    """Tune every (dtype, d, m, n bucket) group of the batch before its first run; returns the group count."""
+    g = _i32(0)
+    _check(load_library().ppca_batch_autotune(b.ptr, reps, ctypes.byref(g)), "ppca_batch_autotune")
+    return int(g.value)
+
+
 def ppca_batch_kernel_count(b: Batch) -> int:
     """Kernel launches one ppca_batch_run performs (0 before the first run)."""
     c = _i64(0)
@@ -390,9 +400,17 @@ def ppca_batch_destroy(b: Batch):
         b.ptr = None
 
 
-def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0, flush: int = 0):
-    s = ppca_schedule(fused, producers, window, flush)
+def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0, flush: int = 0,
+                      engine: int = 0):
+    s = ppca_schedule(fused, producers, window, flush, engine)
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
+
+
+def ppca_autotune(h: Handle, m: int, rows: int = 0, reps: int = 3) -> ppca_schedule:
+    """Time the candidate fast-pass schedules on the handle's data; the fastest is set and returned."""
+    best = ppca_schedule()
+    _check(load_library().ppca_autotune(h.ptr, m, rows, reps, ctypes.byref(best)), "ppca_autotune")
+    return best
 
 
 def ppca_eigh_noalloc(G, m: int, w, U, status=None, stream=None):

@@ -209,7 +209,9 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
     // when priming is asked to run at full precision) runs on CUDA cores in
     // exact FP32 with double-float folding.  The pPCA step itself uses the
     // projected Gram (run_gram), which is accurate on tensor cores.
-    const bool tc = tc_pass_supported(x, m) && !(x.dtype == PPCA_F32 && prec == PPCA_PREC_ACCURATE);
+    const bool tc = h->sched.engine == 2 ? false
+                    : h->sched.engine == 1 ? tc_pass_supported(x, m)
+                                           : tc_pass_supported(x, m) && !(x.dtype == PPCA_F32 && prec == PPCA_PREC_ACCURATE);
     if (tc) {
         CUDA_TRY(xpass_tc(x, V, m, r0, r1, Z, prec, h->tc, h->sched, h->status, h->num_sms, h->stream));
     } else {
@@ -558,12 +560,99 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
 
 ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
-    if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0)
+    if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0 || s->engine < 0 ||
+        s->engine > 2)
         return fail(PPCA_ERR_INVALID, "schedule out of range");
     h->sched.fused = s->fused;
     h->sched.producers = s->producers;
     h->sched.window = s->window;
     h->sched.flush = s->flush;
+    h->sched.engine = s->engine;
+    return PPCA_OK;
+}
+
+namespace {
+
+ppca_schedule to_abi(const TcSchedule& t) {
+    ppca_schedule s{};
+    s.fused = t.fused;
+    s.producers = t.producers;
+    s.window = t.window;
+    s.flush = t.flush;
+    s.engine = t.engine;
+    return s;
+}
+
+// Time the fast pass under each candidate schedule; keep the fastest on the handle.
+ppca_status autotune_handle(ppca_handle* h, int m, int64_t rows, int reps, bool allow_fused, TcSchedule* out) {
+    PPCA_TRY(ensure_workspace(h, std::max(m, h->ws_m)));
+    const XView& x = h->x;
+    if (rows <= 0 || rows > x.n) rows = x.n;
+    std::vector<TcSchedule> cands;
+    TcSchedule base = h->sched;
+    if (tc_pass_supported(x, m)) {
+        TcSchedule c = base;
+        c.engine = 1;
+        c.fused = 0;
+        cands.push_back(c);
+        if (allow_fused && x.dtype == PPCA_BF16) {
+            c.fused = 1;
+            cands.push_back(c);
+        }
+    }
+    {
+        TcSchedule c = base;
+        c.engine = 2;
+        c.fused = 0;
+        cands.push_back(c);
+    }
+    CUDA_TRY(init_gaussian(h->Q, x.d, m, 0x5eedull, h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = -1.f;
+    TcSchedule best = cands.front();
+    ppca_status st = PPCA_OK;
+    for (const TcSchedule& c : cands) {
+        h->sched = c;
+        st = run_xpass(h, x, h->Q, m, 0, rows, h->T, PPCA_PREC_FAST);     // warm-up
+        if (st != PPCA_OK) break;
+        float ms_min = -1.f;
+        for (int r = 0; r < std::max(reps, 1) && st == PPCA_OK; ++r) {
+            cudaEventRecord(e0, h->stream);
+            st = run_xpass(h, x, h->Q, m, 0, rows, h->T, PPCA_PREC_FAST);
+            cudaEventRecord(e1, h->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                st = fail(PPCA_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms_min < 0.f || ms < ms_min) ms_min = ms;
+        }
+        if (st != PPCA_OK) break;
+        if (best_ms < 0.f || ms_min < best_ms) {
+            best_ms = ms_min;
+            best = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->sched = st == PPCA_OK ? best : base;
+    if (st != PPCA_OK) return st;
+    if (out) *out = best;
+    return PPCA_OK;
+}
+
+}  // namespace
+
+ppca_status ppca_autotune(ppca_handle* h, int32_t m, int64_t rows, int32_t reps, ppca_schedule* best) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    PPCA_TRY(check_m(h, m));
+    if (rows < 0) return fail(PPCA_ERR_INVALID, "rows < 0");
+    TcSchedule t;
+    PPCA_TRY(autotune_handle(h, m, rows, reps, true, &t));
+    if (best) *best = to_abi(t);
     return PPCA_OK;
 }
 
@@ -694,6 +783,7 @@ struct ppca_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;                  // kernel launches captured in the graph
+    std::vector<TcSchedule> inst_sched;   // per instance, after ppca_batch_autotune
 };
 
 namespace {
@@ -829,6 +919,7 @@ ppca_status ppca_batch_run(ppca_batch* b) {
             prm.V0 = ds.V0;
             prm.seed = ds.seed;
             prm.precision = PPCA_PREC_FAST;
+            if (!b->inst_sched.empty()) h->sched = b->inst_sched[i];
             st = ppca_prime(h, PPCA_POWER, ds.m, ds.T, &prm);
             if (st == PPCA_OK) st = ppca_finalize(h, ds.k, ds.E, ds.lambda, PPCA_PREC_ACCURATE);
             if (st == PPCA_OK && ds.V_out) st = ppca_get_basis(h, ds.V_out);
@@ -855,6 +946,41 @@ ppca_status ppca_batch_run(ppca_batch* b) {
     CUDA_TRY(cudaGraphLaunch(b->exec, b->stream));
     CUDA_TRY(cudaEventRecord(b->ev_out, b->stream));
     CUDA_TRY(cudaStreamWaitEvent(b->user_stream, b->ev_out, 0));
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_autotune(ppca_batch* b, int32_t reps, int32_t* groups) {
+    if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
+    if (b->exec) return fail(PPCA_ERR_STATE, "the batch has already been captured");
+    const int nslots = (int)b->slots.size();
+    const int count = (int)b->descs.size();
+    // group key: dtype, d, m, n rounded up to a power of two
+    std::vector<std::pair<std::vector<int64_t>, int>> keys;     // key -> representative instance
+    std::vector<int> group_of(count, -1);
+    for (int i = 0; i < count; ++i) {
+        const ppca_instance_desc& ds = b->descs[i];
+        int64_t nb = 1;
+        while (nb < ds.n) nb <<= 1;
+        const std::vector<int64_t> key{ds.dtype, ds.d, ds.m, nb};
+        int g = -1;
+        for (size_t j = 0; j < keys.size(); ++j)
+            if (keys[j].first == key) g = (int)j;
+        if (g < 0) {
+            g = (int)keys.size();
+            keys.emplace_back(key, i);
+        }
+        group_of[i] = g;
+    }
+    std::vector<TcSchedule> best(keys.size());
+    for (size_t g = 0; g < keys.size(); ++g) {
+        const int i = keys[g].second;
+        ppca_handle* h = b->slots[i % nslots];
+        h->x = view_of(b->descs[i]);
+        PPCA_TRY(autotune_handle(h, b->descs[i].m, 0, reps, false, &best[g]));
+    }
+    b->inst_sched.resize(count);
+    for (int i = 0; i < count; ++i) b->inst_sched[i] = best[group_of[i]];
+    if (groups) *groups = (int32_t)keys.size();
     return PPCA_OK;
 }
 

@@ -98,3 +98,26 @@ def test_batch_rejects_bad_descriptors(cuda_device):
     with pytest.raises(P.PPCAError) as ei:
         P.ppca_batch_create(bad)
     assert ei.value.status_name == "PPCA_ERR_INVALID"
+
+
+def test_batch_autotuned_matches_oracle(cuda_device):
+    """After ppca_batch_autotune (each (dtype, d, m, n-bucket) group runs the fastest
+    measured engine), the pPCA step still equals the oracle's on the primed basis."""
+    import paper_2109_03709_gb300 as P
+    inst = make_batch(8, seed=23, T=8, nmax=12000)
+    b = P.ppca_batch_create(inst, slots=3)
+    groups = P.ppca_batch_autotune(b)
+    assert 1 <= groups <= len(inst)
+    P.ppca_batch_run(b)
+    P.ppca_batch_sync(b)
+    for i, ins in enumerate(inst):
+        Xs = ins["X"].double().cpu().numpy()
+        Vg = host_basis(ins["V_out"])
+        Eo, lo = oracle.ppca_finalize(Xs, Vg, ins["k"])
+        np.testing.assert_allclose(ins["lam"].cpu().numpy(), lo, rtol=1e-5, err_msg=f"instance {i}")
+        assert oracle.angles(host_basis(ins["E"]), Eo).max() <= 1e-4, i
+        Vo = oracle.power_prime(Xs, host_basis(ins["V0"]), ins["T"])
+        assert oracle.principal_angles(Vg, Vo).max() <= 1e-2, i
+    with pytest.raises(P.PPCAError) as ei:
+        P.ppca_batch_autotune(b)                      # already captured
+    assert ei.value.status_name == "PPCA_ERR_STATE"

@@ -77,6 +77,41 @@ def test_xpass_fp32_tensor_core_3xtf32(P, n, d, m, r0, r1, ld):
     assert normwise(host_basis(Zd), Zref) <= 5e-5
 
 
+def test_cuda_core_engine_on_bf16_data(P):
+    """engine = 2 runs the exact-FP32 CUDA-core pass even for BF16 data: FP32
+    products of the stored values, so the FP32 tolerance (2e-5) holds at FAST."""
+    n, d, m = 3000, 384, 40
+    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=12)
+    Xd = dev_matrix(X, "bf16")
+    Vd = dev_basis(synth.initial_basis(d, m, seed=5))
+    Zd = empty_basis(d, m)
+    h = P.ppca_create(Xd)
+    P.ppca_set_schedule(h, engine=2)
+    P.ppca_xpass(h, Vd, m, 0, n, Zd, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)
+    assert normwise(host_basis(Zd), Xs.T @ (Xs @ host_basis(Vd))) <= 2e-5
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f32"])
+def test_autotune_picks_a_valid_schedule(P, dtype):
+    n, d, m = 20000, 1024, 64
+    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=13)
+    Xd = dev_matrix(X, dtype)
+    h = P.ppca_create(Xd)
+    best = P.ppca_autotune(h, m, reps=2)
+    assert best.engine in (1, 2)
+    assert best.fused in (-1, 0, 1)
+    if dtype == "f32":
+        assert best.fused != 1
+    Vd = dev_basis(synth.initial_basis(d, m, seed=6))
+    Zd = empty_basis(d, m)
+    P.ppca_xpass(h, Vd, m, 0, n, Zd, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    Xs = stored_f64(Xd)
+    assert normwise(host_basis(Zd), Xs.T @ (Xs @ host_basis(Vd))) <= 1e-2
+
+
 BF16_CASES = [
     # n, d, m, r0, r1
     (3001, 512, 64, 0, 3001),
