@@ -223,12 +223,13 @@ ppca_status run_xpass(ppca_handle* h, const XView& x, const float* V, int m, int
 
 // Projected Gram over rows [r0, r1) of view x: G = (X Q)^T (X Q), FP64.
 // Tensor cores for BF16 and FP32 data (one contraction, split precision);
-// FP8 data: the CUDA-core pass Z = X^T X Q, then G = Q^T Z in double-float.
+// FP8 data (normally refined through a BF16/FP32 copy) and the CUDA-core
+// engine: the exact-FP32 pass Z = X^T X Q, then G = Q^T Z in double-float.
 ppca_status run_gram(ppca_handle* h, const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
                      ppca_precision prec) {
     cudaEvent_t ev_end = nullptr;
     PPCA_TRY(pass_timer(h, prec, r1 - r0, &ev_end));
-    if (tc_pass_supported(x, m)) {
+    if (tc_pass_supported(x, m) && x.dtype != PPCA_FP8_E4M3 && h->sched.engine != 2) {
         CUDA_TRY(projected_gram_tc(x, Q, m, r0, r1, G, prec, h->sched.flush, h->tc, h->status, h->num_sms,
                                    h->stream));
     } else {

@@ -41,6 +41,7 @@ constexpr int kBK = 64;                 // K extent of one stage (64 BF16 = 128 
 
 struct SmemHeader {
     uint64_t full[kMaxStages];
+    uint64_t xform[kMaxStages];     // FP8 data: the stage's BF16 operand is ready
     uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
@@ -80,6 +81,7 @@ __device__ inline void tc_prologue(SmemHeader* hd, int stages, uint32_t tmem_col
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
             tc::mbar_init(&hd->full[i], 1);
+            tc::mbar_init(&hd->xform[i], 128);
             tc::mbar_init(&hd->empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -113,22 +115,55 @@ __device__ inline void drain_copies(SmemHeader* hd, uint32_t issued, int stages,
         tc::mbar_wait(&hd->full[it % stages], (it / stages) & 1u, status, 100000000ull);
 }
 
+// ---------------------------------------------------------------- FP8 data
+//
+// E4M3 X is widened to BF16 in shared memory by four transform warps (6-9):
+// every E4M3 value is exact in BF16, so the MMAs see the stored values.  The
+// row scale s_r of X = diag(s) X8 is applied in the Y epilogue as s_r^2:
+// Z = X^T X V = X8^T diag(s^2) (X8 V), so the Z = X^T Y kernel runs on X8 and
+// Y' = diag(s^2) X8 V unchanged.
+
+// E4M3 byte -> BF16 bits: place the 7 exponent/mantissa bits at float bits
+// 26..20 and rescale by 2^(127 - 7); normal and subnormal codes alike land on
+// the exact value, whose 3 mantissa bits survive truncation to BF16.
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint32_t b0, uint32_t b1) {
+    const float f0 = __uint_as_float(((b0 & 0x80u) << 24) | ((b0 & 0x7Fu) << 20)) * 0x1p120f;
+    const float f1 = __uint_as_float(((b1 & 0x80u) << 24) | ((b1 & 0x7Fu) << 20)) * 0x1p120f;
+    return (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
+}
+
+// 16 E4M3 bytes -> 16 BF16 values (two 16-byte chunks).
+__device__ __forceinline__ void widen16(const uint4 raw, uint4& lo, uint4& hi) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+    uint32_t o[8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        o[2 * i] = e4m3x2_to_bf16x2(w[i] & 0xFFu, (w[i] >> 8) & 0xFFu);
+        o[2 * i + 1] = e4m3x2_to_bf16x2((w[i] >> 16) & 0xFFu, w[i] >> 24);
+    }
+    lo = make_uint4(o[0], o[1], o[2], o[3]);
+    hi = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
 // ---------------------------------------------------------------- Y = X V
 
 // Split K: with ksplit > 1 a task is (tile t, K-range ks) and writes its FP32
 // partial Y rows to Ypart[ks][row][m_pad]; ypart_reduce_kernel sums them and
 // splits the sum into the BF16 pieces (for few row tiles and large d, e.g. a
 // minibatch of a wide matrix).
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1)
+// FP8X: X is E4M3 (stage = [raw 128 x 64 bytes][BF16 A][V pieces]), row scales
+// `scales` (rows r0.., `rows` valid) applied as s_r^2 to Y.
+template <int S, bool FP8X>
+__global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
     xv_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
                  int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int ksplit,
-                 float* __restrict__ Ypart, int* status) {
+                 float* __restrict__ Ypart, const float* __restrict__ scales, int64_t rows, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
+    constexpr uint32_t raw_bytes = FP8X ? 128u * 64u : 0u;
     const uint32_t a_bytes = 128u * 128u;
     const uint32_t b_piece = (uint32_t)m_pad * 128u;
-    const uint32_t stage_bytes = a_bytes + S * b_piece;
+    const uint32_t stage_bytes = raw_bytes + a_bytes + S * b_piece;
     SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t tmem_cols = tmem_cols_for(m_pad);
@@ -149,12 +184,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    tc::mbar_expect_tx(&hd->full[s], stage_bytes);
+                    tc::mbar_expect_tx(&hd->full[s], FP8X ? raw_bytes + S * b_piece : stage_bytes);
                     uint8_t* st = tiles + (size_t)s * stage_bytes;
                     tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK, t * 128);
 #pragma unroll
                     for (int p = 0; p < S; ++p)
-                        tc::tma_load_2d(st + a_bytes + p * b_piece, &tmV, &hd->full[s], k * kBK, p * m_pad);
+                        tc::tma_load_2d(st + raw_bytes + a_bytes + p * b_piece, &tmV, &hd->full[s], k * kBK,
+                                        p * m_pad);
                 }
             }
             if (!ok) drain_copies(hd, it, stages, status);
@@ -176,13 +212,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
                 for (int k = k0; k < k1; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
-                    if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
+                    if (!tc::mbar_wait(FP8X ? &hd->xform[s] : &hd->full[s], ph, status) ||
+                        *(volatile int*)&hd->abort) {
                         hd->abort = 1;
                         ok = false;
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t a_addr = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+                    const uint32_t a_addr = tc::smem_u32(tiles + (size_t)s * stage_bytes + raw_bytes);
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 32, 16, 1024);
@@ -198,7 +235,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (ok) tc::mma_commit(&hd->tfull[b]);
             }
         }
-    } else {
+    } else if (warp < 6) {
         const int q = warp & 3;
         uint32_t tl = 0;
         for (int task = blockIdx.x; task < ntiles * ksplit; task += gridDim.x, ++tl) {
@@ -210,10 +247,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc::fence_after_sync();
             const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+            float rs = 1.f;
+            if (FP8X) {
+                const float sr = row < rows ? scales[row] : 0.f;
+                rs = sr * sr;
+            }
             for (int c0 = 0; c0 < m_pad; c0 += 32) {
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
+                if (FP8X) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(__uint_as_float(r[j]) * rs);
+                }
                 if (ksplit == 1) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
@@ -230,21 +276,54 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc::fence_before_sync();
             tc::mbar_arrive(&hd->tempty[b]);
         }
+    } else if (FP8X) {
+        // transform: raw row r (64 bytes, unswizzled) -> BF16 row r of A (128 bytes, 128-byte swizzle);
+        // task (r, q): raw bytes 16q..16q+15 -> A chunks 2q, 2q + 1
+        const int tid = threadIdx.x - 192;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x) {
+            const int ks = task % ksplit;
+            const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
+            for (int k = k0; k < k1; ++k, ++it) {
+                const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = tiles + (size_t)s * stage_bytes;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int id = i * 128 + tid, r = id >> 2, q = id & 3;
+                    const uint4 raw = *reinterpret_cast<const uint4*>(st + r * 64 + q * 16);
+                    uint4 lo, hi;
+                    widen16(raw, lo, hi);
+                    uint8_t* arow = st + raw_bytes + r * 128;
+                    *reinterpret_cast<uint4*>(arow + (((2 * q) ^ (r & 7)) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(arow + (((2 * q + 1) ^ (r & 7)) << 4)) = hi;
+                }
+                tc::fence_proxy_async_shared();
+                tc::mbar_arrive(&hd->xform[s]);
+            }
+        }
     }
     tc_epilogue_teardown(hd, tmem_cols);
 }
 
 // ---------------------------------------------------------------- Z = X^T Y
 
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1)
+// FP8X: X is E4M3 (stage = [raw 64 rows x 128 bytes][BF16 A][Y pieces]).
+template <int S, bool FP8X>
+__global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
     xty_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
                   int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
+    constexpr uint32_t raw_bytes = FP8X ? 64u * 128u : 0u;
     const uint32_t a_bytes = 2u * 64u * 128u;     // two 64-row x 64-col boxes
     const uint32_t b_piece = (uint32_t)m_pad * 128u;
-    const uint32_t stage_bytes = a_bytes + S * b_piece;
+    const uint32_t stage_bytes = raw_bytes + a_bytes + S * b_piece;
     SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t tmem_cols = tmem_cols_for(m_pad);
@@ -266,13 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    tc::mbar_expect_tx(&hd->full[st_i], stage_bytes);
+                    tc::mbar_expect_tx(&hd->full[st_i], FP8X ? raw_bytes + S * b_piece : stage_bytes);
                     uint8_t* st = tiles + (size_t)st_i * stage_bytes;
                     tc::tma_load_2d(st, &tmX, &hd->full[st_i], s * 128, k * kBK);
-                    tc::tma_load_2d(st + 8192, &tmX, &hd->full[st_i], s * 128 + 64, k * kBK);
+                    if (!FP8X) tc::tma_load_2d(st + 8192, &tmX, &hd->full[st_i], s * 128 + 64, k * kBK);
 #pragma unroll
                     for (int p = 0; p < S; ++p)
-                        tc::tma_load_2d(st + a_bytes + p * b_piece, &tmY, &hd->full[st_i], k * kBK, p * m_pad);
+                        tc::tma_load_2d(st + raw_bytes + a_bytes + p * b_piece, &tmY, &hd->full[st_i], k * kBK,
+                                        p * m_pad);
                 }
             }
             if (!ok) drain_copies(hd, it, stages, status);
@@ -297,13 +377,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
                     for (int k = kb; k < ke; ++k, ++it) {
                         const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
-                        if (!tc::mbar_wait(&hd->full[st_i], ph, status) || *(volatile int*)&hd->abort) {
+                        if (!tc::mbar_wait(FP8X ? &hd->xform[st_i] : &hd->full[st_i], ph, status) ||
+                            *(volatile int*)&hd->abort) {
                             hd->abort = 1;
                             ok = false;
                             break;
                         }
                         tc::fence_after_sync();
-                        const uint32_t a_addr = tc::smem_u32(tiles + (size_t)st_i * stage_bytes);
+                        const uint32_t a_addr = tc::smem_u32(tiles + (size_t)st_i * stage_bytes + raw_bytes);
 #pragma unroll
                         for (int kk = 0; kk < kBK / 16; ++kk) {
                             const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 2048, 8192, 1024);
@@ -320,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
         }
-    } else {
+    } else if (warp < 6) {
         const int q = warp & 3;
         uint32_t fb = 0;
         bool ok = true;
@@ -356,6 +437,39 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    } else if (FP8X) {
+        // transform: raw [64 rows][128 bytes] (columns of the 128-column slice) -> two BF16
+        // boxes [64 rows][64 columns] (128-byte swizzle), the MN-major operand X^T;
+        // task (r, q): raw bytes 16q..16q+15 -> box q / 4, chunks 2 (q % 4), 2 (q % 4) + 1 of row r
+        const int tid = threadIdx.x - 192;
+        uint32_t it = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            const int g = task / Dt;
+            const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+            for (int k = k0; k < k1; ++k, ++it) {
+                const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                if (!tc::mbar_wait(&hd->full[st_i], ph, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    ok = false;
+                    break;
+                }
+                uint8_t* st = tiles + (size_t)st_i * stage_bytes;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int id = i * 128 + tid, r = id >> 3, q = id & 7;
+                    const uint4 raw = *reinterpret_cast<const uint4*>(st + r * 128 + q * 16);
+                    uint4 lo, hi;
+                    widen16(raw, lo, hi);
+                    uint8_t* arow = st + raw_bytes + (q >> 2) * 8192 + r * 128;
+                    const int c = 2 * (q & 3);
+                    *reinterpret_cast<uint4*>(arow + ((c ^ (r & 7)) << 4)) = lo;
+                    *reinterpret_cast<uint4*>(arow + (((c + 1) ^ (r & 7)) << 4)) = hi;
+                }
+                tc::fence_proxy_async_shared();
+                tc::mbar_arrive(&hd->xform[st_i]);
             }
         }
     }
@@ -1151,7 +1265,7 @@ struct PassShape {
     int m_pad, Dt, ntiles, nk;
 };
 
-template <int S>
+template <int S, bool FP8X = false>
 cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, const TcPassScratch& sc,
                          PassShape& ps, CUtensorMap& tmXa, CUtensorMap& tmXb, CUtensorMap& tmV, CUtensorMap& tmY,
                          cudaStream_t st) {
@@ -1172,9 +1286,15 @@ cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int6
         note_launch();
         split_v_kernel<S><<<blocks, 256, 0, st>>>(V, ps.d, m, ps.m_pad, ps.ldv, Vp);
     }
-    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * 2;
-    if (!encode_bf16_2d(&tmXa, xbase, ps.d, ps.rows, x.ld * 2, 64, 128) ||
-        !encode_bf16_2d(&tmXb, xbase, ps.d, ps.rows, x.ld * 2, 64, 64) ||
+    const int esz = FP8X ? 1 : 2;
+    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * esz;
+    const bool xmaps = FP8X ? encode_2d(&tmXa, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, ps.rows, x.ld, 64, 128,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE) &&
+                                  encode_2d(&tmXb, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, ps.rows, x.ld, 128, 64,
+                                            CU_TENSOR_MAP_SWIZZLE_NONE)
+                            : encode_bf16_2d(&tmXa, xbase, ps.d, ps.rows, x.ld * 2, 64, 128) &&
+                                  encode_bf16_2d(&tmXb, xbase, ps.d, ps.rows, x.ld * 2, 64, 64);
+    if (!xmaps ||
         !encode_bf16_2d(&tmV, Vp, ps.d, (uint64_t)S * ps.m_pad, ps.ldv * 2, 64, ps.m_pad) ||
         !encode_bf16_2d(&tmY, Yt, ps.ldy, (uint64_t)S * ps.m_pad, ps.ldy * 2, 64, ps.m_pad))
         return cudaErrorInvalidValue;
@@ -1191,20 +1311,22 @@ cudaError_t launch_zreduce(const float* Zacc, int Sg, int Dt, int64_t d, int m, 
 }
 
 // Two GEMM kernels: Y = X V, then Z = X^T Y (X is read twice).
-template <int S>
+template <int S, bool FP8X = false>
 cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
                      const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
     PassShape ps;
     CUtensorMap tmXa, tmXb, tmV, tmY;
-    cudaError_t e = prepare_pass<S>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
+    cudaError_t e = prepare_pass<S, FP8X>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
+    constexpr int threads = FP8X ? 320 : kThreads;
+    constexpr uint32_t raw_xv = FP8X ? 128u * 64u : 0u, raw_xty = FP8X ? 64u * 128u : 0u;
     if (e != cudaSuccess) return e;
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
     float* Zacc = static_cast<float*>(sc.zacc);
     {
-        const uint32_t stage_bytes = 128u * 128u + S * (uint32_t)ps.m_pad * 128u;
+        const uint32_t stage_bytes = raw_xv + 128u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        e = cudaFuncSetAttribute(xv_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(xv_tc_kernel<S, FP8X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         // few row tiles (a minibatch) and a long K: split K so that every SM has work
         int ksplit = 1;
@@ -1219,8 +1341,9 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const int grid = ntask < num_sms ? ntask : num_sms;
         float* Ypart = static_cast<float*>(sc.zacc);
         note_launch();
-        xv_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXa, tmV, ps.ntiles, ps.nk, ps.m_pad, stages, Yt, ps.ldy,
-                                                       ksplit, Ypart, status);
+        const float* scales = FP8X ? x.scales + r0 : nullptr;
+        xv_tc_kernel<S, FP8X><<<grid, threads, smem, st>>>(tmXa, tmV, ps.ntiles, ps.nk, ps.m_pad, stages, Yt,
+                                                            ps.ldy, ksplit, Ypart, scales, ps.rows, status);
         if (ksplit > 1) {
             const int64_t total = ps.ldy * ps.m_pad;
             int blocks = (int)((total + 255) / 256);
@@ -1231,10 +1354,10 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
     }
     int Sg;
     {
-        const uint32_t stage_bytes = 2u * 64u * 128u + S * (uint32_t)ps.m_pad * 128u;
+        const uint32_t stage_bytes = raw_xty + 2u * 64u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        e = cudaFuncSetAttribute(xty_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(xty_tc_kernel<S, FP8X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int kst = (int)(ps.ldy / kBK);
         Sg = ps.Dt >= num_sms ? 1 : num_sms / ps.Dt;
@@ -1243,8 +1366,8 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const int ntask = ps.Dt * Sg;
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
-        xty_tc_kernel<S><<<grid, kThreads, smem, st>>>(tmXb, tmY, ps.Dt, Sg, kst, flush, ps.m_pad, stages, Zacc,
-                                                        status);
+        xty_tc_kernel<S, FP8X><<<grid, threads, smem, st>>>(tmXb, tmY, ps.Dt, Sg, kst, flush, ps.m_pad, stages,
+                                                              Zacc, status);
     }
     return launch_zreduce(Zacc, Sg, ps.Dt, ps.d, m, ps.m_pad, Z, st);
 }
@@ -1381,13 +1504,17 @@ TcPassScratch tc_pass_scratch_carve(void* base, int64_t n, int64_t d, int m, int
 }
 
 bool tc_pass_supported(const XView& x, int m) {
-    return (x.dtype == PPCA_BF16 || x.dtype == PPCA_F32) && m >= 1 && m <= kMaxM && encode_fn() != nullptr;
+    return (x.dtype == PPCA_BF16 || x.dtype == PPCA_F32 || x.dtype == PPCA_FP8_E4M3) && m >= 1 && m <= kMaxM &&
+           encode_fn() != nullptr;
 }
 
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
                      const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
     if (r1 <= r0) return cudaErrorInvalidValue;
     if (x.dtype == PPCA_F32) return run_pass_f32(x, V, m, r0, r1, Z, 64, s, status, num_sms, st);   // FAST only
+    if (x.dtype == PPCA_FP8_E4M3)
+        return prec == PPCA_PREC_ACCURATE ? run_pass<3, true>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st)
+                                          : run_pass<1, true>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
     if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
     // The fused pass needs every 128-column slice of d owned by a resident CTA.
     const int Dt = (int)((x.d + 127) / 128);

@@ -299,6 +299,41 @@ def test_quantize_bf16_bit_exact(P):
     np.testing.assert_array_equal(out.cpu().numpy(), lib)
 
 
+FP8_CASES = [
+    # n, d, m, r0, r1
+    (3001, 512, 64, 0, 3001),
+    (1000, 200, 33, 17, 931),        # ragged d and rows
+    (257, 64, 1, 0, 257),
+    (5000, 1024, 128, 0, 5000),
+    (1000, 8192, 64, 0, 512),        # split-K Y = X V
+]
+
+
+@pytest.mark.parametrize("n,d,m,r0,r1", FP8_CASES)
+@pytest.mark.parametrize("prec,tol", [("FAST", 1e-2), ("ACCURATE", 2e-5)])
+def test_xpass_fp8_tensor_cores(P, n, d, m, r0, r1, prec, tol):
+    """FP8 E4M3 data with per-row scales on tensor cores: the E4M3 tiles are widened
+    to BF16 in shared memory (exact) and s_r^2 scales Y.  The reference is
+    X^T X V of the dequantised stored values in FP64; FAST rounds Y to BF16
+    (1e-2), ACCURATE splits V and Y into three BF16 pieces (2e-5)."""
+    import torch
+    X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=31) if d <= 4096 else \
+        (np.random.default_rng(31).standard_normal((n, d)) * (0.9995 ** np.arange(1, d + 1))[None, :], None)
+    codes, scales = oracle.fp8_row_quantize(X)
+    ldp = (d + 15) // 16 * 16                          # 16-byte row pitch
+    Xd = torch.zeros((n, ldp), dtype=torch.uint8, device="cuda")[:, :d]
+    Xd.copy_(torch.from_numpy(codes))
+    sd = torch.from_numpy(scales).cuda()
+    Vd = dev_basis(synth.initial_basis(d, m, seed=8))
+    Zd = empty_basis(d, m)
+    h = P.ppca_create(Xd, row_scales=sd)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zd, getattr(P, "PPCA_PREC_" + prec))
+    P.ppca_sync(h)
+    Xs = (oracle.e4m3_decode(codes) * scales.astype(np.float64)[:, None])[r0:r1]
+    Zref = Xs.T @ (Xs @ host_basis(Vd))
+    assert normwise(host_basis(Zd), Zref) <= tol
+
+
 def test_quantize_fp8_bit_exact(P):
     import torch
     rng = np.random.default_rng(1)
