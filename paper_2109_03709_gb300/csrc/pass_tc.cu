@@ -35,6 +35,8 @@ namespace ppca {
 namespace {
 
 constexpr int kThreads = 192;
+constexpr int kThreadsFp8 = 448;          // + eight transform warps (6-13) for E4M3 data
+constexpr int kFp8XformThreads = kThreadsFp8 - 192;
 constexpr int kMaxStages = 8;
 constexpr int kSmemBudget = 200 * 1024;
 constexpr int kBK = 64;                 // K extent of one stage (64 BF16 = 128 B)
@@ -81,7 +83,7 @@ __device__ inline void tc_prologue(SmemHeader* hd, int stages, uint32_t tmem_col
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
             tc::mbar_init(&hd->full[i], 1);
-            tc::mbar_init(&hd->xform[i], 128);
+            tc::mbar_init(&hd->xform[i], kFp8XformThreads);
             tc::mbar_init(&hd->empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -117,19 +119,24 @@ __device__ inline void drain_copies(SmemHeader* hd, uint32_t issued, int stages,
 
 // ---------------------------------------------------------------- FP8 data
 //
-// E4M3 X is widened to BF16 in shared memory by four transform warps (6-9):
+// E4M3 X is widened to BF16 in shared memory by eight transform warps (6-13):
 // every E4M3 value is exact in BF16, so the MMAs see the stored values.  The
 // row scale s_r of X = diag(s) X8 is applied in the Y epilogue as s_r^2:
 // Z = X^T X V = X8^T diag(s^2) (X8 V), so the Z = X^T Y kernel runs on X8 and
 // Y' = diag(s^2) X8 V unchanged.
 
-// E4M3 byte -> BF16 bits: place the 7 exponent/mantissa bits at float bits
-// 26..20 and rescale by 2^(127 - 7); normal and subnormal codes alike land on
-// the exact value, whose 3 mantissa bits survive truncation to BF16.
-__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2(uint32_t b0, uint32_t b1) {
-    const float f0 = __uint_as_float(((b0 & 0x80u) << 24) | ((b0 & 0x7Fu) << 20)) * 0x1p120f;
-    const float f1 = __uint_as_float(((b1 & 0x80u) << 24) | ((b1 & 0x7Fu) << 20)) * 0x1p120f;
-    return (__float_as_uint(f0) >> 16) | (__float_as_uint(f1) & 0xFFFF0000u);
+// Two E4M3 codes (low byte first) -> BF16x2 with the hardware conversions:
+// E4M3 -> FP16 (exact), FP16 -> FP32 (exact), FP32 -> BF16 (exact: at most
+// four significant bits).
+__device__ __forceinline__ uint32_t e4m3x2_to_bf16x2_cvt(uint32_t two) {
+    uint32_t h2, out;
+    float lo, hi;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((unsigned short)two));
+    asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(h2));
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(out) : "f"(hi), "f"(lo));
+    return out;
 }
 
 // 16 E4M3 bytes -> 16 BF16 values (two 16-byte chunks).
@@ -138,8 +145,8 @@ __device__ __forceinline__ void widen16(const uint4 raw, uint4& lo, uint4& hi) {
     uint32_t o[8];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        o[2 * i] = e4m3x2_to_bf16x2(w[i] & 0xFFu, (w[i] >> 8) & 0xFFu);
-        o[2 * i + 1] = e4m3x2_to_bf16x2((w[i] >> 16) & 0xFFu, w[i] >> 24);
+        o[2 * i] = e4m3x2_to_bf16x2_cvt(w[i] & 0xFFFFu);
+        o[2 * i + 1] = e4m3x2_to_bf16x2_cvt(w[i] >> 16);
     }
     lo = make_uint4(o[0], o[1], o[2], o[3]);
     hi = make_uint4(o[4], o[5], o[6], o[7]);
@@ -154,7 +161,7 @@ __device__ __forceinline__ void widen16(const uint4 raw, uint4& lo, uint4& hi) {
 // FP8X: X is E4M3 (stage = [raw 128 x 64 bytes][BF16 A][V pieces]), row scales
 // `scales` (rows r0.., `rows` valid) applied as s_r^2 to Y.
 template <int S, bool FP8X>
-__global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
+__global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
     xv_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
                  int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int ksplit,
                  float* __restrict__ Ypart, const float* __restrict__ scales, int64_t rows, int* status) {
@@ -294,8 +301,8 @@ __global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
                 }
                 uint8_t* st = tiles + (size_t)s * stage_bytes;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int id = i * 128 + tid, r = id >> 2, q = id & 3;
+                for (int i = 0; i < 512 / kFp8XformThreads; ++i) {
+                    const int id = i * kFp8XformThreads + tid, r = id >> 2, q = id & 3;
                     const uint4 raw = *reinterpret_cast<const uint4*>(st + r * 64 + q * 16);
                     uint4 lo, hi;
                     widen16(raw, lo, hi);
@@ -315,7 +322,7 @@ __global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
 
 // FP8X: X is E4M3 (stage = [raw 64 rows x 128 bytes][BF16 A][Y pieces]).
 template <int S, bool FP8X>
-__global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
+__global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
     xty_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
                   int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
     extern __shared__ uint8_t smem_raw[];
@@ -458,8 +465,8 @@ __global__ void __launch_bounds__(FP8X ? 320 : kThreads, 1)
                 }
                 uint8_t* st = tiles + (size_t)st_i * stage_bytes;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int id = i * 128 + tid, r = id >> 3, q = id & 7;
+                for (int i = 0; i < 512 / kFp8XformThreads; ++i) {
+                    const int id = i * kFp8XformThreads + tid, r = id >> 3, q = id & 7;
                     const uint4 raw = *reinterpret_cast<const uint4*>(st + r * 128 + q * 16);
                     uint4 lo, hi;
                     widen16(raw, lo, hi);
@@ -791,7 +798,7 @@ __device__ inline void f32_prologue(F32Header* hd, int stages, uint32_t tmem_col
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
             tc::mbar_init(&hd->full[i], 1);
-            tc::mbar_init(&hd->xform[i], 128);
+            tc::mbar_init(&hd->xform[i], kFp8XformThreads);
             tc::mbar_init(&hd->empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -1317,7 +1324,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
     PassShape ps;
     CUtensorMap tmXa, tmXb, tmV, tmY;
     cudaError_t e = prepare_pass<S, FP8X>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
-    constexpr int threads = FP8X ? 320 : kThreads;
+    constexpr int threads = FP8X ? kThreadsFp8 : kThreads;
     constexpr uint32_t raw_xv = FP8X ? 128u * 64u : 0u, raw_xty = FP8X ? 64u * 128u : 0u;
     if (e != cudaSuccess) return e;
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
