@@ -187,7 +187,8 @@ PPCA_API ppca_status ppca_sync(ppca_handle *h);
  * Schedule of the fast X-pass over BF16 data (the knobs an autotuner sets).
  * The product X^T X V needs every element of X once; the fused form reads each
  * 128-row tile of X from HBM once: a producer pipeline computes Y = X V for the
- * tile while consumer pipelines, each owning a 128-column slice of Z for the
+ * tile (or for one half of its columns, kparts = 2, the two halves summed in
+ * FP32) while consumer pipelines, each owning a 256-column slice of Z for the
  * whole pass, re-read the tile from L2 for Z += X^T Y.  The unfused form runs
  * the two products as separate kernels (X read twice).
  */
@@ -195,12 +196,14 @@ typedef struct ppca_schedule {
     int32_t fused;            /* 1: fused single-read pass; 0: two kernels; -1: library default */
     int32_t producers;        /* CTAs running Y = X V in the fused pass (0: one per SM)           */
     int32_t window;           /* tiles a producer may run ahead of the slowest consumer (0: the  */
-                              /* library keeps about 48 MB of X in flight)                        */
+                              /* tiles being produced plus four per consumer row group)           */
     int32_t flush;            /* split-precision passes: K-stages (64 wide) an FP32 tensor-core   */
                               /* accumulator takes before it is folded into a double-float sum    */
                               /* (0: library default; larger = faster, less accurate)             */
     int32_t engine;           /* X-pass engine: 0 library choice, 1 tensor cores (BF16 / FP32     */
                               /* data), 2 CUDA cores (any data type)                              */
+    int32_t kparts;           /* fused pass: K parts per 128-row tile of Y = X V (1 or 2, 2 only  */
+                              /* when d spans two 64-column stages; 0: library default, 1)        */
 } ppca_schedule;
 
 /* Set the X-pass schedule of a handle (takes effect at its next pass). */

@@ -562,13 +562,14 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
 ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
     if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0 || s->engine < 0 ||
-        s->engine > 2)
+        s->engine > 2 || s->kparts < 0 || s->kparts > 2)
         return fail(PPCA_ERR_INVALID, "schedule out of range");
     h->sched.fused = s->fused;
     h->sched.producers = s->producers;
     h->sched.window = s->window;
     h->sched.flush = s->flush;
     h->sched.engine = s->engine;
+    h->sched.kparts = s->kparts;
     return PPCA_OK;
 }
 
@@ -581,6 +582,7 @@ ppca_schedule to_abi(const TcSchedule& t) {
     s.window = t.window;
     s.flush = t.flush;
     s.engine = t.engine;
+    s.kparts = t.kparts;
     return s;
 }
 
@@ -598,7 +600,10 @@ ppca_status autotune_handle(ppca_handle* h, int m, int64_t rows, int reps, bool 
         cands.push_back(c);
         if (allow_fused && x.dtype == PPCA_BF16) {
             c.fused = 1;
-            cands.push_back(c);
+            for (int kp = 2; kp >= 1; --kp) {           // half-K or whole-K producer tiles
+                c.kparts = kp;
+                cands.push_back(c);
+            }
         }
     }
     {

@@ -487,9 +487,18 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
 //
 // One persistent, cooperatively launched kernel; every CTA runs two
 // warp-specialised pipelines that share the tensor core and TMEM:
-//   producer (warps 0-5)   Y_t = X_t V for 128-row tiles t = p, p + NP, ...
-//                          (X streamed from HBM), Y_t written as BF16, then
-//                          ready[t] released (one add per epilogue warp);
+//   producer (warps 0-5)   Y_t = X_t V for 128-row tiles (X streamed from
+//                          HBM), Y_t written as BF16, then ready[t] released
+//                          (one add per epilogue warp).  With kparts = 2 a
+//                          tile is two work items, the two halves of the K
+//                          range (d), taken by neighbouring CTAs: the first
+//                          epilogue warp of a row quarter to finish stores
+//                          its FP32 partial and releases pready, the second
+//                          adds it to its own accumulator and publishes
+//                          Y_t.  Half-tiles halve the X bytes in flight
+//                          (152 x 0.5 MB instead of 152 x 1 MB), so more
+//                          of the consumers' re-reads still find X_t in
+//                          L2, at the same V traffic per byte of X;
 //   consumer (warps 6-11)  CTA (sp, g) owns the 256-column slice pair sp of Z
 //                          for the whole pass (two M = 128 accumulators in
 //                          TMEM) and consumes the tiles t = g, g + Sg, ...: it
@@ -513,10 +522,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                        const __grid_constant__ CUtensorMap tmXb, const __grid_constant__ CUtensorMap tmY, int ntiles,
                        int nk, int Dt2, int Sg, int NP, int window, int flush_tiles, int m_pad, int p_stages,
                        int c_stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, float* __restrict__ Zacc,
-                       int* __restrict__ ready, int* __restrict__ consumed, int* status) {
+                       int* __restrict__ ready, int* __restrict__ consumed, int kparts, float* __restrict__ Ypart,
+                       int* __restrict__ arrive, int* __restrict__ pready, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t p_a = 128u * 128u;            // 128 rows x 64 columns
+    const int nitems = ntiles * kparts;          // producer work items (tile, K part)
+    const int kh = (nk + 1) / 2;                 // K-stages of the first half when kparts = 2
     const uint32_t c_a = 4u * 64u * 128u;        // 64 rows x 256 columns, four 64-column boxes
     const uint32_t b_piece = (uint32_t)m_pad * 128u;
     const uint32_t p_stage = p_a + b_piece, c_stage = c_a + b_piece;
@@ -566,12 +578,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const uint64_t keep = tc::policy_evict_last();
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += NP) {
+            for (int i = blockIdx.x; i < nitems && ok; i += NP) {
+                const int t = i / kparts, part = i - t * kparts;
+                const int kb0 = part ? kh : 0, kb1 = (kparts == 1 || part) ? nk : kh;
                 if (t >= window && !tc::wait_flag_geq(consumed + (t - window), Dt2, status)) {
                     *abort_flag = 1;
                     break;
                 }
-                for (int k = 0; k < nk; ++k, ++it) {
+                for (int k = kb0; k < kb1; ++k, ++it) {
                     const uint32_t s = it % p_stages, ph = (it / p_stages) & 1u;
                     if (!tc::mbar_wait(&hd->pempty[s], ph ^ 1u, status) || *abort_flag) {
                         *abort_flag = 1;
@@ -595,7 +609,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
             uint32_t it = 0, tl = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += NP, ++tl) {
+            for (int i = blockIdx.x; i < nitems && ok; i += NP, ++tl) {
+                const int part = i % kparts;
+                const int kb0 = part ? kh : 0, kb1 = (kparts == 1 || part) ? nk : kh;
                 const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->ptempty[b], tph ^ 1u, status) || *abort_flag) {
                     *abort_flag = 1;
@@ -603,7 +619,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 }
                 tc::fence_after_sync();
                 const uint32_t d_tmem = ptmem + b * (uint32_t)m_pad;
-                for (int k = 0; k < nk; ++k, ++it) {
+                for (int k = kb0; k < kb1; ++k, ++it) {
                     const uint32_t s = it % p_stages, ph = (it / p_stages) & 1u;
                     if (!tc::mbar_wait(&hd->pfull[s], ph, status) || *abort_flag) {
                         *abort_flag = 1;
@@ -616,7 +632,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 32, 16, 1024);
                         const uint64_t bdesc = tc::smem_desc_sw128(a_addr + p_a + kk * 32, 16, 1024);
-                        tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k | kk) != 0);
+                        tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k - kb0 | kk) != 0);
                     }
                     tc::mma_commit(&hd->pempty[s]);
                 }
@@ -628,7 +644,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         if (producer) {
             const int q = warp & 3;
             uint32_t tl = 0;
-            for (int t = blockIdx.x; t < ntiles; t += NP, ++tl) {
+            for (int i = blockIdx.x; i < nitems; i += NP, ++tl) {
+                const int t = i / kparts;
                 const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->ptfull[b], tph, status) || *abort_flag) {
                     *abort_flag = 1;
@@ -636,16 +653,55 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                 }
                 tc::fence_after_sync();
                 const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+                const uint32_t acc = ptmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad;
+                // partial of this row quarter: [tile][column][128 rows] FP32, one 128-byte line per column
+                float* yp = Ypart + ((int64_t)t * m_pad) * 128 + q * 32;
+                int order = 1;                                   // kparts = 1: the only (= last) arrival
+                if (kparts == 2) {
+                    if (lane == 0) order = atomicAdd(arrive + t * 4 + q, 1);
+                    order = __shfl_sync(0xffffffffu, order, 0);
+                }
+                if (order == 0) {
+                    // first half done: store the FP32 partial, then release it
+                    for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(acc + (uint32_t)c0, r);
+                        tc::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) yp[(int64_t)(c0 + j) * 128 + lane] = __uint_as_float(r[j]);
+                    }
+                    tc::fence_before_sync();
+                    tc::mbar_arrive(&hd->ptempty[b]);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) tc::red_release_add_gpu(pready + t * 4 + q, 1);
+                    continue;
+                }
+                if (kparts == 2 && (!tc::wait_flag_geq(pready + t * 4 + q, 1, status) || *abort_flag)) {
+                    *abort_flag = 1;
+                    break;
+                }
                 for (int c0 = 0; c0 < m_pad; c0 += 32) {
                     uint32_t r[32];
-                    tc::tmem_ld32(ptmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
+                    tc::tmem_ld32(acc + (uint32_t)c0, r);
                     tc::tmem_ld_wait();
+                    if (kparts == 2) {
+                        // FP32 a + b is commutative: Y_t does not depend on which half came first
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            r[j] = __float_as_uint(__uint_as_float(r[j]) + __ldcg(yp + (int64_t)(c0 + j) * 128 + lane));
+                    }
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
                         Yt[(int64_t)(c0 + j) * ldy + row] = __float2bfloat16_rn(__uint_as_float(r[j]));
                 }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&hd->ptempty[b]);
+                if (kparts == 2) {
+                    // the partial is dead: drop its lines from L2 without writing them back
+                    __syncwarp();
+                    for (int c = lane; c < m_pad; c += 32) tc::discard_l2_line(yp + (int64_t)c * 128);
+                }
                 // publish: every lane fences its stores, the warp syncs, and one
                 // lane adds a release to ready[t]; consumers wait for all 4 warps
                 __threadfence();
@@ -798,7 +854,7 @@ __device__ inline void f32_prologue(F32Header* hd, int stages, uint32_t tmem_col
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
             tc::mbar_init(&hd->full[i], 1);
-            tc::mbar_init(&hd->xform[i], kFp8XformThreads);
+            tc::mbar_init(&hd->xform[i], 128);           // four transform warps (6-9)
             tc::mbar_init(&hd->empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
@@ -1262,7 +1318,7 @@ Layout layout_of(int64_t n, int64_t d, int m, int num_sms) {
     L.vp_bytes = std::max((size_t)3 * L.m_pad * L.ldv * 2, (size_t)2 * L.m_pad * round_up(d, 4) * 4);
     L.yt_bytes = std::max((size_t)3 * L.m_pad * L.rows_pad_max * 2, (size_t)2 * L.m_pad * L.rows_pad_max * 4);
     L.z_bytes = (size_t)(2 * num_sms + L.Dt + 2) * 128 * L.m_pad * 8;
-    L.flag_bytes = (size_t)2 * (L.rows_pad_max / 128 + 1) * sizeof(int);
+    L.flag_bytes = (size_t)10 * (L.rows_pad_max / 128 + 1) * sizeof(int);   // fused pass: 2 + 2 x 4 per tile
     (void)m;
     return L;
 }
@@ -1389,10 +1445,12 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     const int Dt2 = (ps.Dt + 1) / 2;
     int Sg = num_sms / Dt2;
     if (Sg > ps.ntiles) Sg = ps.ntiles;
+    // whole-K tiles unless asked for two K halves (which need at least two K-stages)
+    const int kparts = (sched.kparts == 2 && ps.nk >= 2) ? 2 : 1;
     int NP = sched.producers > 0 ? sched.producers : num_sms;
     if (NP > num_sms) NP = num_sms;
-    if (NP > ps.ntiles) NP = ps.ntiles;
-    int window = sched.window > 0 ? sched.window : NP + 4 * Sg;
+    if (NP > ps.ntiles * kparts) NP = ps.ntiles * kparts;
+    int window = sched.window > 0 ? sched.window : (NP + kparts - 1) / kparts + 4 * Sg;
     if (window < 1) window = 1;
     const int grid = NP > Dt2 * Sg ? NP : Dt2 * Sg;
     const uint32_t b_piece = (uint32_t)ps.m_pad * 128u;
@@ -1407,7 +1465,11 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     if (e != cudaSuccess) return e;
     int* ready = sc.flags;
     int* consumed = sc.flags + ps.ntiles + 1;
-    e = cudaMemsetAsync(sc.flags, 0, (size_t)2 * (ps.ntiles + 1) * sizeof(int), st);
+    int* arrive = sc.flags + 2 * (ps.ntiles + 1);          // [tile][row quarter]
+    int* pready = arrive + 4 * (ps.ntiles + 1);
+    e = cudaMemsetAsync(sc.flags, 0, (size_t)(kparts == 2 ? 10 : 2) * (ps.ntiles + 1) * sizeof(int), st);
+    // FP32 partials of the first K half, [tile][m_pad][128], after the BF16 Y^T in the Y scratch
+    float* Ypart = reinterpret_cast<float*>(static_cast<__nv_bfloat16*>(sc.yt) + (size_t)ps.m_pad * ps.ldy);
     if (e != cudaSuccess) return e;
     const int flush_tiles = 64;
     cudaLaunchConfig_t cfg = {};
@@ -1423,7 +1485,7 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     note_launch();
     e = cudaLaunchKernelEx(&cfg, xpass_fused_kernel, tmXa, tmV, tmXb, tmY, ps.ntiles, ps.nk, Dt2, Sg, NP, window,
                            flush_tiles, ps.m_pad, p_stages, c_stages, static_cast<__nv_bfloat16*>(sc.yt), ps.ldy,
-                           static_cast<float*>(sc.zacc), ready, consumed, status);
+                           static_cast<float*>(sc.zacc), ready, consumed, kparts, Ypart, arrive, pready, status);
     if (e != cudaSuccess) return e;
     return launch_zreduce(static_cast<float*>(sc.zacc), Sg, 2 * Dt2, ps.d, m, ps.m_pad, Z, st);
 }

@@ -122,6 +122,12 @@ __device__ __forceinline__ void red_release_add_gpu(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Invalidate one 128-byte L2 line (128-byte aligned) without writing it back:
+// for scratch that is dead once read.
+__device__ __forceinline__ void discard_l2_line(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Order this thread's later async-proxy (TMA) accesses after the generic-proxy
 // writes it has observed.
 __device__ __forceinline__ void fence_proxy_async_global() {

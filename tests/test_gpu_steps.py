@@ -158,17 +158,22 @@ FUSED_CASES = [
 ]
 
 
+@pytest.mark.parametrize("kparts", [1, 2])
 @pytest.mark.parametrize("n,d,m,r0,r1,producers,window", FUSED_CASES)
-def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window):
+def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window, kparts):
     X = np.random.default_rng(n + d).standard_normal((n, d)) * (0.97 ** np.arange(1, d + 1))[None, :] ** 0.5
     Xd = dev_matrix(X, "bf16")
     V = synth.initial_basis(d, m, seed=4)
     Vd = dev_basis(V)
     Zf, Zu = empty_basis(d, m), empty_basis(d, m)
     h = P.ppca_create(Xd)
-    P.ppca_set_schedule(h, fused=1, producers=producers, window=window)
+    P.ppca_set_schedule(h, fused=1, producers=producers, window=window, kparts=kparts)
     P.ppca_xpass(h, Vd, m, r0, r1, Zf, P.PPCA_PREC_FAST)
     P.ppca_sync(h)
+    Zf2 = empty_basis(d, m)
+    P.ppca_xpass(h, Vd, m, r0, r1, Zf2, P.PPCA_PREC_FAST)
+    P.ppca_sync(h)
+    assert np.array_equal(host_basis(Zf), host_basis(Zf2))   # run to run: bitwise
     P.ppca_set_schedule(h, fused=0)
     P.ppca_xpass(h, Vd, m, r0, r1, Zu, P.PPCA_PREC_FAST)
     P.ppca_sync(h)
@@ -179,9 +184,10 @@ def test_xpass_bf16_fused_single_read(P, n, d, m, r0, r1, producers, window):
     for c in range(m):
         assert normwise(Zg[:, c], Zref[:, c]) <= 4e-2
     # the two-kernel pass rounds the same Y to BF16, except where it splits K over
-    # CTAs (few row tiles): there a summation-order difference can move a Y element
-    # to the neighbouring BF16 value (2^-8 relative); a few such elements move Z by ~1e-5
-    assert normwise(Zg, host_basis(Zu)) <= 1e-4
+    # CTAs (few row tiles), or the fused pass sums two K halves (kparts = 2): there a
+    # summation-order difference can move a Y element to the neighbouring BF16 value
+    # (2^-8 relative); such elements move Z by ~1e-5 (split K) to ~5e-5 (two halves)
+    assert normwise(Zg, host_basis(Zu)) <= (1e-4 if kparts == 1 else 2e-4)
 
 
 @pytest.mark.parametrize("d,m", [(64, 1), (256, 16), (1000, 64), (300, 33), (2000, 100), (4096, 128)])
