@@ -197,9 +197,10 @@ typedef struct ppca_schedule {
     int32_t producers;        /* CTAs running Y = X V in the fused pass (0: one per SM)           */
     int32_t window;           /* tiles a producer may run ahead of the slowest consumer (0: the  */
                               /* tiles being produced plus four per consumer row group)           */
-    int32_t flush;            /* split-precision passes: K-stages (64 wide) an FP32 tensor-core   */
-                              /* accumulator takes before it is folded into a double-float sum    */
-                              /* (0: library default; larger = faster, less accurate)             */
+    int32_t flush;            /* split-precision passes and the fused pass's Z = X^T Y: K-stages  */
+                              /* (64 wide) an FP32 tensor-core accumulator takes before it is     */
+                              /* folded into a double-float sum (0: library default; larger =     */
+                              /* fewer folds, less accurate)                                      */
     int32_t engine;           /* X-pass engine: 0 library choice, 1 tensor cores (BF16 / FP32     */
                               /* data), 2 CUDA cores (any data type)                              */
     int32_t kparts;           /* fused pass: K parts per 128-row tile of Y = X V (1 or 2, 2 only  */
