@@ -176,6 +176,27 @@ PPCA_API ppca_status ppca_prime_continue(ppca_handle *h, int64_t T);
 PPCA_API ppca_status ppca_finalize(ppca_handle *h, int32_t k, float *E, double *lambda,
                           ppca_precision precision);
 
+/*
+ * Host-buffer entry points, for data that lives in host memory.  Both are
+ * stream-ordered on the handle's stream and asynchronous when the host buffers
+ * are page-locked (cudaHostAlloc / cudaHostRegister); with pageable memory the
+ * copies complete before the call returns.  Results are valid after ppca_sync.
+ *
+ * ppca_upload: copy all n rows of X from host memory into the device buffer the
+ * handle was created with (which it overwrites), e.g. to stream a new data set
+ * of the same shape through one handle.  X_host has the handle's dtype and
+ * leading dimension ld_host >= d (elements).  row_scales_host: n FP32 row
+ * scales for FP8 data (required then, NULL otherwise).  The FP32/BF16 copy set
+ * by ppca_set_refine is not touched.
+ *
+ * ppca_finalize_host: ppca_finalize into the handle's workspace, then E (d x k
+ * column-major FP32) and lambda (k FP64) are copied to the host buffers.
+ */
+PPCA_API ppca_status ppca_upload(ppca_handle *h, const void *X_host, int64_t ld_host,
+                                 const float *row_scales_host);
+PPCA_API ppca_status ppca_finalize_host(ppca_handle *h, int32_t k, float *E_host, double *lambda_host,
+                                        ppca_precision precision);
+
 /* Device copy of the current primed basis V (d x m column-major FP32). */
 PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
 

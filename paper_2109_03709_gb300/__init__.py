@@ -27,7 +27,7 @@ __all__ = [
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
-    "EXPORTED_SYMBOLS",
+    "ppca_upload", "ppca_finalize_host", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,6 +48,7 @@ EXPORTED_SYMBOLS = [
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
+    "ppca_upload", "ppca_finalize_host",
 ]
 
 
@@ -127,6 +128,8 @@ _SIGS = {
     "ppca_prime": (_c_status, [_vp, ctypes.c_int, _i32, _i64, ctypes.POINTER(ppca_prime_params)]),
     "ppca_prime_continue": (_c_status, [_vp, _i64]),
     "ppca_finalize": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int]),
+    "ppca_upload": (_c_status, [_vp, _vp, _i64, _vp]),
+    "ppca_finalize_host": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int]),
     "ppca_get_basis": (_c_status, [_vp, _vp]),
     "ppca_sync": (_c_status, [_vp]),
     "ppca_get_state": (_c_status, [_vp, _vp, ctypes.POINTER(_i64)]),
@@ -284,6 +287,19 @@ def ppca_prime_continue(h: Handle, T: int):
 
 def ppca_finalize(h: Handle, k: int, E, lam, precision: int = PPCA_PREC_AUTO):
     _check(load_library().ppca_finalize(h.ptr, k, _ptr(E), _ptr(lam), precision), "ppca_finalize")
+
+
+def ppca_upload(h: Handle, X_host, row_scales_host=None, ld_host: int | None = None):
+    """Copy host X (a CPU tensor or array pointer of the handle's dtype) into the handle's device X."""
+    if ld_host is None:
+        ld_host = X_host.stride(0)
+    _check(load_library().ppca_upload(h.ptr, _ptr(X_host), ld_host, _ptr(row_scales_host)), "ppca_upload")
+
+
+def ppca_finalize_host(h: Handle, k: int, E_host, lam_host, precision: int = PPCA_PREC_AUTO):
+    """pPCA step with E (k x d row-major = d x k column-major FP32) and lambda (k FP64) written to host memory."""
+    _check(load_library().ppca_finalize_host(h.ptr, k, _ptr(E_host), _ptr(lam_host), precision),
+           "ppca_finalize_host")
 
 
 def ppca_get_basis(h: Handle, V_out):

@@ -86,6 +86,8 @@ struct ppca_handle {
     float* Gf = nullptr;      // m x m, FP32 copy of G (CholeskyQR's FP32 attempt)
     double* w = nullptr;      // m
     double* U = nullptr;      // m x m
+    float* E_res = nullptr;   // d x m: ppca_finalize_host's eigenvectors before the copy out
+    double* lam_res = nullptr;  // m: ppca_finalize_host's eigenvalues
     float* gram_part = nullptr;
     void* jac = nullptr;
     double* eg = nullptr;
@@ -118,6 +120,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
     size_t need = 5 * dm + al256((size_t)m * m * 8) + 2 * al256((size_t)m * m * 4) + al256((size_t)m * 8) +
                   al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
+                  dm + al256((size_t)m * 8) +
                   al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
                   al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
     if (h->ws_limit > 0 && (int64_t)need > h->ws_limit)
@@ -149,6 +152,8 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     h->Gf = reinterpret_cast<float*>(take((size_t)m * m * 4));
     h->w = reinterpret_cast<double*>(take((size_t)m * 8));
     h->U = reinterpret_cast<double*>(take((size_t)m * m * 8));
+    h->E_res = reinterpret_cast<float*>(take((size_t)d * m * 4));
+    h->lam_res = reinterpret_cast<double*>(take((size_t)m * 8));
     h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
     h->jac = take(jacobi_scratch_bytes(m));
     h->eg = reinterpret_cast<double*>(take(eigengame_scratch_bytes(d, m)));
@@ -480,6 +485,37 @@ ppca_status ppca_get_basis(const ppca_handle* h, float* V_out) {
     if (!h || !V_out) return fail(PPCA_ERR_INVALID, "NULL argument");
     if (h->method < 0) return fail(PPCA_ERR_STATE, "no primed basis");
     CUDA_TRY(cudaMemcpyAsync(V_out, h->V, (size_t)h->x.d * h->m * sizeof(float), cudaMemcpyDeviceToDevice,
+                             h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_upload(ppca_handle* h, const void* X_host, int64_t ld_host, const float* row_scales_host) {
+    if (!h || !X_host) return fail(PPCA_ERR_INVALID, "NULL argument");
+    const XView& x = h->x;
+    if (ld_host < x.d) return fail(PPCA_ERR_INVALID, "ld_host = %lld < d = %lld", (long long)ld_host, (long long)x.d);
+    if ((x.dtype == PPCA_FP8_E4M3) != (row_scales_host != nullptr))
+        return fail(PPCA_ERR_INVALID, "row_scales_host must be given for FP8 data and only for FP8 data");
+    const size_t esz = (size_t)dtype_size(x.dtype);
+    void* dst = const_cast<void*>(x.ptr);     // the caller's device buffer, written on request
+    if (ld_host == x.ld && x.ld == x.d)
+        CUDA_TRY(cudaMemcpyAsync(dst, X_host, (size_t)x.n * x.d * esz, cudaMemcpyHostToDevice, h->stream));
+    else
+        CUDA_TRY(cudaMemcpy2DAsync(dst, (size_t)x.ld * esz, X_host, (size_t)ld_host * esz, (size_t)x.d * esz,
+                                   (size_t)x.n, cudaMemcpyHostToDevice, h->stream));
+    if (row_scales_host)
+        CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(x.scales), row_scales_host, (size_t)x.n * sizeof(float),
+                                 cudaMemcpyHostToDevice, h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_finalize_host(ppca_handle* h, int32_t k, float* E_host, double* lambda_host,
+                               ppca_precision precision) {
+    if (!h || !E_host || !lambda_host) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "finalize before prime");
+    PPCA_TRY(ppca_finalize(h, k, h->E_res, h->lam_res, precision));
+    CUDA_TRY(cudaMemcpyAsync(E_host, h->E_res, (size_t)k * h->x.d * sizeof(float), cudaMemcpyDeviceToHost,
+                             h->stream));
+    CUDA_TRY(cudaMemcpyAsync(lambda_host, h->lam_res, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost,
                              h->stream));
     return PPCA_OK;
 }

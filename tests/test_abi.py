@@ -67,6 +67,8 @@ def test_argument_checks_need_no_device(lib):
     params = P.ppca_prime_params()
     assert lib.ppca_prime(None, 0, 4, 1, ctypes.byref(params)) == 1
     assert lib.ppca_finalize(None, 1, fake, fake, 0) == 1
+    assert lib.ppca_upload(None, fake, 4, None) == 1
+    assert lib.ppca_finalize_host(None, 1, fake, fake, 0) == 1
     assert lib.ppca_sync(None) == 1
     assert lib.ppca_destroy(None) == 0
     assert lib.ppca_quantize_bf16(None, 4, 4, 4, fake, 4, None) == 1
