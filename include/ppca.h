@@ -226,6 +226,9 @@ typedef struct ppca_schedule {
                               /* data), 2 CUDA cores (any data type)                              */
     int32_t kparts;           /* fused pass: K parts per 128-row tile of Y = X V (1 or 2, 2 only  */
                               /* when d spans two 64-column stages; 0: library default, 1)        */
+    int32_t l2_keep;          /* fused pass: percent (1-100) of each row tile's columns loaded    */
+                              /* with the L2 evict_last hint for the consumers' re-read, the rest */
+                              /* evict_first (0: library default, what fits in 70 % of L2)        */
 } ppca_schedule;
 
 /* Set the X-pass schedule of a handle (takes effect at its next pass). */

@@ -90,6 +90,7 @@ class ppca_schedule(ctypes.Structure):
         ("flush", ctypes.c_int32),
         ("engine", ctypes.c_int32),
         ("kparts", ctypes.c_int32),
+        ("l2_keep", ctypes.c_int32),
     ]
 
 
@@ -418,8 +419,8 @@ def ppca_batch_destroy(b: Batch):
 
 
 def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0, flush: int = 0,
-                      engine: int = 0, kparts: int = 0):
-    s = ppca_schedule(fused, producers, window, flush, engine, kparts)
+                      engine: int = 0, kparts: int = 0, l2_keep: int = 0):
+    s = ppca_schedule(fused, producers, window, flush, engine, kparts, l2_keep)
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
 
 

@@ -598,7 +598,7 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
 ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
     if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0 || s->engine < 0 ||
-        s->engine > 2 || s->kparts < 0 || s->kparts > 2)
+        s->engine > 2 || s->kparts < 0 || s->kparts > 2 || s->l2_keep < 0 || s->l2_keep > 100)
         return fail(PPCA_ERR_INVALID, "schedule out of range");
     h->sched.fused = s->fused;
     h->sched.producers = s->producers;
@@ -606,6 +606,7 @@ ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     h->sched.flush = s->flush;
     h->sched.engine = s->engine;
     h->sched.kparts = s->kparts;
+    h->sched.l2_keep = s->l2_keep;
     return PPCA_OK;
 }
 
@@ -619,6 +620,7 @@ ppca_schedule to_abi(const TcSchedule& t) {
     s.flush = t.flush;
     s.engine = t.engine;
     s.kparts = t.kparts;
+    s.l2_keep = t.l2_keep;
     return s;
 }
 
@@ -640,6 +642,9 @@ ppca_status autotune_handle(ppca_handle* h, int m, int64_t rows, int reps, bool 
                 c.kparts = kp;
                 cands.push_back(c);
             }
+            c.l2_keep = 100;                            // every tile protected in L2
+            cands.push_back(c);
+            c.l2_keep = base.l2_keep;
         }
     }
     {

@@ -524,7 +524,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                        int nk, int Dt2, int Sg, int NP, int window, int flush_tiles, int m_pad, int p_stages,
                        int c_stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, float* __restrict__ Zacc,
                        int* __restrict__ ready, int* __restrict__ consumed, int kparts, float* __restrict__ Ypart,
-                       int* __restrict__ arrive, int* __restrict__ pready, int* status) {
+                       int* __restrict__ arrive, int* __restrict__ pready, int kkeep, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t p_a = 128u * 128u;            // 128 rows x 64 columns
@@ -574,9 +574,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
     if (warp == 0) {
         // ---------------- producer TMA
         if (lane == 0 && producer) {
-            // X tiles stay in L2 until their consumers have re-read them (evict_last
-            // here, evict_first on the consumers' reads)
-            const uint64_t keep = tc::policy_evict_last();
+            // The last K-stages of every tile (k >= kkeep) are loaded evict_last, so
+            // they stay in L2 until the consumers re-read them (evict_first there);
+            // the first ones are loaded evict_first.  All 152 tiles in flight
+            // would not fit in L2: protecting all of them lets the oldest parts
+            // of every tile evict one another, protecting a part that fits keeps it.
+            const uint64_t keep = tc::policy_evict_last(), drop_early = tc::policy_evict_first();
             uint32_t it = 0;
             bool ok = true;
             for (int i = blockIdx.x; i < nitems && ok; i += NP) {
@@ -595,7 +598,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
                     }
                     tc::mbar_expect_tx(&hd->pfull[s], p_stage);
                     uint8_t* st = ptiles + (size_t)s * p_stage;
-                    tc::tma_load_2d_hint(st, &tmXa, &hd->pfull[s], k * kBK, t * 128, keep);
+                    tc::tma_load_2d_hint(st, &tmXa, &hd->pfull[s], k * kBK, t * 128, k >= kkeep ? keep : drop_early);
                     tc::tma_load_2d(st + p_a, &tmV, &hd->pfull[s], k * kBK, 0);
                 }
             }
@@ -1454,6 +1457,19 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     if (NP > num_sms) NP = num_sms;
     if (NP > ps.ntiles * kparts) NP = ps.ntiles * kparts;
     int window = sched.window > 0 ? sched.window : (NP + kparts - 1) / kparts + 4 * Sg;
+    // Share of each tile's K-stages loaded evict_last (the rest evict_first):
+    // sched.l2_keep percent, by default what keeps the protected part of the
+    // tiles in flight (NP / kparts tiles of 128 rows) within 70 % of L2.
+    int keep_pct = sched.l2_keep;
+    if (keep_pct <= 0) {
+        int dev = 0, l2 = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        const double inflight = (double)NP / kparts * 128.0 * (double)ps.d * 2.0;
+        keep_pct = (int)std::min(100.0, 100.0 * 0.7 * (double)l2 / std::max(inflight, 1.0));
+        keep_pct = std::max(keep_pct, 1);
+    }
+    const int kkeep = ps.nk - (int)(((int64_t)ps.nk * std::min(keep_pct, 100) + 99) / 100);
     if (window < 1) window = 1;
     const int grid = NP > Dt2 * Sg ? NP : Dt2 * Sg;
     const uint32_t b_piece = (uint32_t)ps.m_pad * 128u;
@@ -1494,7 +1510,7 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     note_launch();
     e = cudaLaunchKernelEx(&cfg, xpass_fused_kernel, tmXa, tmV, tmXb, tmY, ps.ntiles, ps.nk, Dt2, Sg, NP, window,
                            flush_tiles, ps.m_pad, p_stages, c_stages, static_cast<__nv_bfloat16*>(sc.yt), ps.ldy,
-                           static_cast<float*>(sc.zacc), ready, consumed, kparts, Ypart, arrive, pready, status);
+                           static_cast<float*>(sc.zacc), ready, consumed, kparts, Ypart, arrive, pready, kkeep, status);
     if (e != cudaSuccess) return e;
     return launch_zreduce(static_cast<float*>(sc.zacc), Sg, 2 * Dt2, ps.d, m, ps.m_pad, Z, st);
 }

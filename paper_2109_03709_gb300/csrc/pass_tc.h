@@ -22,6 +22,7 @@ struct TcSchedule {
     int flush = 0;          // split-precision passes: K-stages per accumulator flush (0: default)
     int engine = 0;         // 0: library choice, 1: tensor cores, 2: CUDA cores
     int kparts = 0;         // fused kernel: K parts per producer tile (2: two K halves; else 1)
+    int l2_keep = 0;        // fused kernel: percent of a tile's K-stages loaded evict_last (0: from the L2 size)
 };
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms);

@@ -354,3 +354,22 @@ def test_quantize_fp8_bit_exact(P):
     qref, sref = oracle.fp8_row_quantize(X)
     np.testing.assert_array_equal(sc.cpu().numpy(), sref)
     np.testing.assert_array_equal(out.cpu().numpy(), qref)
+
+
+def test_fused_l2_keep_changes_only_cache_hints(P):
+    """The L2 share kept for the consumers' re-read steers eviction hints only:
+    every setting gives the same Z, bit for bit."""
+    n, d, m = 20000, 1024, 64
+    X = np.random.default_rng(9).standard_normal((n, d)) * (0.97 ** np.arange(1, d + 1))[None, :] ** 0.5
+    Xd = dev_matrix(X, "bf16")
+    Vd = dev_basis(synth.initial_basis(d, m, seed=2))
+    h = P.ppca_create(Xd)
+    out = []
+    for keep in (0, 1, 40, 100):
+        P.ppca_set_schedule(h, fused=1, l2_keep=keep)
+        Z = empty_basis(d, m)
+        P.ppca_xpass(h, Vd, m, 0, n, Z, P.PPCA_PREC_FAST)
+        P.ppca_sync(h)
+        out.append(host_basis(Z))
+    for z in out[1:]:
+        assert np.array_equal(z, out[0])
