@@ -691,7 +691,7 @@ def run_ours(args):
     achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
     # DRAM bytes (read + write) of one fused-pass launch on this workload, from the ncu
     # capture in profiles/xpass_fused_bf16_131072x4096_ncu.md (131072 rows, scaled by rows)
-    traffic = 14.12e9 if (cfg.name == "precision_bf16_1000000x4096" and n == 1000000) else None
+    traffic = 12.51e9 if (cfg.name == "precision_bf16_1000000x4096" and n == 1000000) else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": peak_kind,
