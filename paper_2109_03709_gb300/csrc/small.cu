@@ -385,8 +385,8 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
     const int lda = (m + 3) & ~3;           // shared-memory row stride: rows start 16-byte aligned
     float* A = cbs;                         // m x lda; upper triangle, rows of R' overwrite it panel by panel
     float* W = A + m * lda;                 // m x lda, R'^-1 (upper, zero below)
-    float* T = W + m * lda;                 // (kCB x kCB) per block pair of one block diagonal
-    float* dsc = T + 3 * kCB * kCB;         // m: G_ii^-1/2
+    float* T = W + m * lda;                 // (kCB x kCB) per block pair of one block diagonal (<= nb - 1 pairs)
+    float* dsc = T + ((m + kCB - 1) / kCB) * kCB * kCB;   // m: G_ii^-1/2
     __shared__ int bad;
     __shared__ float red[kCBThreads / 32];
     __shared__ float rowsum_max;
@@ -621,33 +621,46 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
     }
 }
 
-// Q = V X with X = R^-1 upper triangular (row-major).  A block takes 16 rows
-// of V (staged in shared memory, read as broadcasts) and thread c computes
-// output column c for them: Q[r, c] = sum_{l <= c} V[r, l] X[l, c], X read
-// from global memory (the same m x m matrix for every block, cached).
-// Q must not alias V.
-constexpr int kApplyRows = 16;
+// Q = V X with X = R^-1 upper triangular (row-major).  A block stages X and
+// 32 rows of V in shared memory; thread (c, h) computes output column c for
+// the 16 rows of half h: Q[r, c] = sum_{l <= c} V[r, l] X[l, c], V's rows
+// read as float4 broadcasts.  The V block starts at a float offset rounded up
+// to a multiple of 4 (16-byte aligned for any m).  Q must not alias V.
+constexpr int kApplyRows = 32;
+constexpr int kApplyHalf = kApplyRows / 2;
 
-__global__ void __launch_bounds__(128) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
+__host__ __device__ inline int apply_xs_floats(int m) { return (m * m + 3) & ~3; }
+
+__global__ void __launch_bounds__(256) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
                                                          int64_t d, int m, float* __restrict__ Q) {
-    __shared__ __align__(16) float vs[128][kApplyRows];
+    extern __shared__ __align__(16) float ars[];
+    float* xs = ars;                          // m x m, X row-major
+    float* vs = ars + apply_xs_floats(m);     // m x kApplyRows, vs[l][r] = V[r0 + r, l]
     const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
+    const int mm = m * m, mm4 = mm / 4;
+    if ((reinterpret_cast<uintptr_t>(Rinv) & 15) == 0) {
+        const float4* x4 = reinterpret_cast<const float4*>(Rinv);
+        for (int e = threadIdx.x; e < mm4; e += blockDim.x) reinterpret_cast<float4*>(xs)[e] = x4[e];
+        for (int e = 4 * mm4 + threadIdx.x; e < mm; e += blockDim.x) xs[e] = Rinv[e];
+    } else {
+        for (int e = threadIdx.x; e < mm; e += blockDim.x) xs[e] = Rinv[e];
+    }
     for (int e = threadIdx.x; e < m * kApplyRows; e += blockDim.x) {
         const int l = e / kApplyRows, r = e % kApplyRows;
-        vs[l][r] = (r0 + r < d) ? V[(int64_t)l * d + r0 + r] : 0.f;
+        vs[e] = (r0 + r < d) ? V[(int64_t)l * d + r0 + r] : 0.f;
     }
     __syncthreads();
-    const int c = threadIdx.x;
+    const int mp = blockDim.x / 2;
+    const int c = threadIdx.x % mp, h = threadIdx.x / mp;
     if (c >= m) return;
-    float acc[kApplyRows];
+    float acc[kApplyHalf];
 #pragma unroll
-    for (int r = 0; r < kApplyRows; ++r) acc[r] = 0.f;
-#pragma unroll 2
+    for (int r = 0; r < kApplyHalf; ++r) acc[r] = 0.f;
     for (int l = 0; l <= c; ++l) {
-        const float x = __ldg(Rinv + l * m + c);
-        const float4* v4 = reinterpret_cast<const float4*>(vs[l]);
+        const float x = xs[l * m + c];
+        const float4* v4 = reinterpret_cast<const float4*>(vs + l * kApplyRows + h * kApplyHalf);
 #pragma unroll
-        for (int q = 0; q < kApplyRows / 4; ++q) {
+        for (int q = 0; q < kApplyHalf / 4; ++q) {
             const float4 v = v4[q];
             acc[4 * q + 0] = __fmaf_rn(v.x, x, acc[4 * q + 0]);
             acc[4 * q + 1] = __fmaf_rn(v.y, x, acc[4 * q + 1]);
@@ -655,25 +668,35 @@ __global__ void __launch_bounds__(128) apply_rinv_kernel(const float* __restrict
             acc[4 * q + 3] = __fmaf_rn(v.w, x, acc[4 * q + 3]);
         }
     }
-    float* out = Q + (int64_t)c * d + r0;
+    const int64_t rb = r0 + h * kApplyHalf;
+    float* out = Q + (int64_t)c * d + rb;
 #pragma unroll
-    for (int r = 0; r < kApplyRows; ++r)
-        if (r0 + r < d) out[r] = acc[r];
+    for (int r = 0; r < kApplyHalf; ++r)
+        if (rb + r < d) out[r] = acc[r];
 }
 
 // ------------------------------------------------------------------ Jacobi
 
 // Parallel-order (round-robin) two-sided Jacobi in FP32 on N = m rounded up to
-// even; the extra index is a decoupled zero row/column.  Each step applies N/2
-// disjoint rotations J: A <- J^T A J is done block by block (every 2x2 block
-// [rows p_t, q_t] x [cols p_u, q_u] needs only rotations t and u), so a step
-// costs two barriers.  A rotation of pair (p, q) is skipped when
-// |a_pq| <= tol * sqrt(|a_pp a_qq|), the relative criterion that keeps small
-// eigenvalues accurate.  NT = 32 runs the whole solve in one warp.
+// even; the extra index is a decoupled zero row/column.  Each step applies the
+// N/2 disjoint rotations J of one round-robin round: A <- J^T A J, U <- U J.
+// Warp w owns the pairs t = w, w + NW, ... of every step: its lanes compute
+// those rotations (classical angle) in registers and broadcast them by
+// shuffles, the warp rotates rows p, q of its pairs, and after a barrier
+// columns p, q of A and U -- two barriers per step, every lane with several
+// independent shared-memory accesses in flight.  The pairs of a step are
+// disjoint, so the row pass of one warp never touches the rows whose
+// entries another warp reads for its angles.  A rotation of pair (p, q) is
+// skipped when |a_pq| <= tol * sqrt(|a_pp a_qq|), the relative criterion that
+// keeps small eigenvalues accurate.  NT = 32 runs the whole solve in one warp
+// (N <= 32).
 constexpr int kJacobiMaxSweeps = 40;
 
 __device__ __forceinline__ int rr_player(int pos, int step, int N) {
-    return pos == 0 ? 0 : ((pos - 1 + step) % (N - 1)) + 1;
+    if (pos == 0) return 0;
+    int x = pos - 1 + step;              // < 2 (N - 1)
+    if (x >= N - 1) x -= N - 1;
+    return x + 1;
 }
 
 template <int NT>
@@ -684,19 +707,20 @@ __device__ __forceinline__ void jbar() {
 template <int NT>
 __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict__ G, int m, float* __restrict__ evals,
                                                         float* __restrict__ Uf, int* sweeps_out, int* status) {
+    constexpr int NW = NT / 32;
+    constexpr int NMAX = NT == 32 ? 32 : kMaxM;           // largest N this instance runs
+    constexpr int KP = (NMAX / 2 + NW - 1) / NW;          // pairs per warp and step
+    constexpr int RPL = NMAX / 32;                        // row / column entries per lane
+    static_assert(KP <= 32, "one lane per owned pair");
     extern __shared__ float js[];
     const int N = m + (m & 1);
     const int H = N / 2;
-    const int S = N + 1;            // padded row stride: row and column sweeps are bank-conflict free
+    const int S = N + 1;            // padded row stride: row and column passes are bank-conflict free
     float* A = js;                  // N x S
     float* U = A + N * S;           // N x S (column j = eigenvector j)
-    float* cs = U + N * S;          // H cosines
-    float* sn = cs + H;             // H sines
-    float* dp = sn + H;             // H new a_pp
-    float* dq = dp + H;             // H new a_qq
-    int* pp = reinterpret_cast<int*>(dq + H);
-    int* qq = pp + H;
     __shared__ int rotated;
+    const unsigned full = 0xffffffffu;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     for (int e = threadIdx.x; e < N * N; e += NT) {
         const int i = e / N, j = e % N;
         A[i * S + j] = (i < m && j < m) ? (float)(0.5 * (G[i * m + j] + G[j * m + i])) : 0.f;
@@ -709,66 +733,94 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
         if (threadIdx.x == 0) rotated = 0;
         jbar<NT>();
         for (int step = 0; step < N - 1; ++step) {
-            // rotations of the N/2 disjoint pairs of this step (classical angle)
-            for (int t = threadIdx.x; t < H; t += NT) {
-                int p = rr_player(t, step, N), q = rr_player(N - 1 - t, step, N);
-                if (p > q) { const int x = p; p = q; q = x; }
-                pp[t] = p;
-                qq[t] = q;
-                const float apq = A[p * S + q], app = A[p * S + p], aqq = A[q * S + q];
-                float c = 1.f, s = 0.f, tt = 0.f;
-                if (fabsf(apq) > 1e-30f && fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
-                    const float tau = (aqq - app) / (2.0f * apq);
-                    if (fabsf(tau) > 1e18f) {
-                        tt = 0.5f / tau;
-                    } else {
-                        tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+            // rotation of the pair t = warp + lane * NW (lanes < KP)
+            int myp = 0, myq = 0;
+            float myc = 1.f, mys = 0.f, mydp = 0.f, mydq = 0.f;
+            {
+                const int t = warp + lane * NW;
+                if (lane < KP && t < H) {
+                    int p = rr_player(t, step, N), q = rr_player(N - 1 - t, step, N);
+                    if (p > q) { const int x = p; p = q; q = x; }
+                    myp = p;
+                    myq = q;
+                    const float apq = A[p * S + q], app = A[p * S + p], aqq = A[q * S + q];
+                    float tt = 0.f;
+                    if (fabsf(apq) > 1e-30f && fabsf(apq) > tol * sqrtf(fabsf(app)) * sqrtf(fabsf(aqq))) {
+                        const float tau = (aqq - app) / (2.0f * apq);
+                        if (fabsf(tau) > 1e18f) {
+                            tt = 0.5f / tau;
+                        } else {
+                            tt = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                        }
+                        myc = 1.0f / sqrtf(1.0f + tt * tt);
+                        mys = tt * myc;
+                        rotated = 1;
                     }
-                    c = 1.0f / sqrtf(1.0f + tt * tt);
-                    s = tt * c;
-                    rotated = 1;
+                    mydp = app - tt * apq;
+                    mydq = aqq + tt * apq;
                 }
-                cs[t] = c;
-                sn[t] = s;
-                dp[t] = app - tt * apq;
-                dq[t] = aqq + tt * apq;
             }
-            jbar<NT>();
             // rows p, q: A <- J^T A
-            for (int t = threadIdx.x / 32; t < H; t += NT / 32) {      // one warp per pair
-                const float s = sn[t];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                if (warp + k * NW >= H) break;
+                const float s = __shfl_sync(full, mys, k);
+                const float c = __shfl_sync(full, myc, k);
+                const int p = __shfl_sync(full, myp, k), q = __shfl_sync(full, myq, k);
                 if (s == 0.f) continue;
-                const float c = cs[t];
-                const int p = pp[t], q = qq[t];
-                for (int j = threadIdx.x % 32; j < N; j += 32) {
-                    const float apj = A[p * S + j], aqj = A[q * S + j];
-                    A[p * S + j] = c * apj - s * aqj;
-                    A[q * S + j] = s * apj + c * aqj;
+                float ap[RPL], aq[RPL];
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int j = lane + 32 * r;
+                    ap[r] = j < N ? A[p * S + j] : 0.f;
+                    aq[r] = j < N ? A[q * S + j] : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int j = lane + 32 * r;
+                    if (j < N) {
+                        A[p * S + j] = c * ap[r] - s * aq[r];
+                        A[q * S + j] = s * ap[r] + c * aq[r];
+                    }
                 }
             }
             jbar<NT>();
             // columns p, q: A <- A J, U <- U J; the pair's own 2x2 block gets the
             // exact zero and the tangent-formula diagonal
-            for (int u = threadIdx.x / 32; u < H; u += NT / 32) {      // one warp per pair
-                const float s = sn[u];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                if (warp + k * NW >= H) break;
+                const float s = __shfl_sync(full, mys, k);
+                const float c = __shfl_sync(full, myc, k);
+                const int p = __shfl_sync(full, myp, k), q = __shfl_sync(full, myq, k);
+                const float dp = __shfl_sync(full, mydp, k), dq = __shfl_sync(full, mydq, k);
                 if (s == 0.f) continue;
-                const float c = cs[u];
-                const int p = pp[u], q = qq[u];
-                for (int i = threadIdx.x % 32; i < N; i += 32) {
+                float aip[RPL], aiq[RPL], uip[RPL], uiq[RPL];
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    const bool in = i < N;
+                    aip[r] = in ? A[i * S + p] : 0.f;
+                    aiq[r] = in ? A[i * S + q] : 0.f;
+                    uip[r] = in ? U[i * S + p] : 0.f;
+                    uiq[r] = in ? U[i * S + q] : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const int i = lane + 32 * r;
+                    if (i >= N) continue;
                     if (i == p) {
-                        A[p * S + p] = dp[u];
+                        A[p * S + p] = dp;
                         A[p * S + q] = 0.f;
                     } else if (i == q) {
                         A[q * S + p] = 0.f;
-                        A[q * S + q] = dq[u];
+                        A[q * S + q] = dq;
                     } else {
-                        const float aip = A[i * S + p], aiq = A[i * S + q];
-                        A[i * S + p] = c * aip - s * aiq;
-                        A[i * S + q] = s * aip + c * aiq;
+                        A[i * S + p] = c * aip[r] - s * aiq[r];
+                        A[i * S + q] = s * aip[r] + c * aiq[r];
                     }
-                    const float uip = U[i * S + p], uiq = U[i * S + q];
-                    U[i * S + p] = c * uip - s * uiq;
-                    U[i * S + q] = s * uip + c * uiq;
+                    U[i * S + p] = c * uip[r] - s * uiq[r];
+                    U[i * S + q] = s * uip[r] + c * uiq[r];
                 }
             }
             jbar<NT>();
@@ -1104,7 +1156,7 @@ cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G,
 cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
                               int* status, cudaStream_t st) {
     const size_t lda = (size_t)((m + 3) & ~3);
-    const size_t smem = ((size_t)2 * m * lda + 3 * kCB * kCB + m) * sizeof(float);
+    const size_t smem = ((size_t)2 * m * lda + (size_t)((m + kCB - 1) / kCB) * kCB * kCB + m) * sizeof(float);
     cudaError_t e = allow_smem(chol_blocked_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
@@ -1122,9 +1174,12 @@ cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Ri
 
 cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st) {
     if (V == Q || m > 128) return cudaErrorInvalidValue;
-    const int threads = (m + 31) / 32 * 32;
+    const int threads = 2 * ((m + 31) / 32 * 32);
+    const size_t smem = ((size_t)apply_xs_floats(m) + (size_t)m * kApplyRows) * sizeof(float);
+    cudaError_t e = allow_smem(apply_rinv_kernel, smem);
+    if (e != cudaSuccess) return e;
     note_launch();
-    apply_rinv_kernel<<<ceil_div_i(d, kApplyRows), threads, 0, st>>>(V, Rinv, d, m, Q);
+    apply_rinv_kernel<<<ceil_div_i(d, kApplyRows), threads, smem, st>>>(V, Rinv, d, m, Q);
     return cudaGetLastError();
 }
 
@@ -1147,7 +1202,7 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
     p += al(m * 8);
     int* sweeps = reinterpret_cast<int*>(p);
     const int N = m + (m & 1);
-    const size_t smem = (size_t)2 * N * (N + 1) * sizeof(float) + (size_t)(N / 2) * (4 * sizeof(float) + 2 * sizeof(int));
+    const size_t smem = (size_t)2 * N * (N + 1) * sizeof(float);
     cudaError_t e;
     if (N <= 32) {
         note_launch();
