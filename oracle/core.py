@@ -41,6 +41,7 @@ __all__ = [
     "power_step", "power_prime", "minibatch_rows", "oja_step", "oja_prime",
     "eigengame_gradients", "eigengame_step", "eigengame_prime",
     "angle", "angles", "lces", "principal_angles", "variance_captured",
+    "splitmix64", "sampled_tiles", "ppca_finalize_rows",
     "bf16_bits_to_f64", "e4m3_decode", "e4m3_encode_rne", "fp8_row_quantize",
 ]
 
@@ -202,6 +203,58 @@ def ppca_finalize_cov(C, n: int, V, k: int):
     w, U = eigh_desc(0.5 * (G + G.T))
     E = sign_fix(Q @ U[:, :k])
     return E, w[:k] / n
+
+
+# ---------------------------------------------------------------------------
+# O2s: the pPCA step on a seeded sample of the rows
+# ---------------------------------------------------------------------------
+#
+# For its large-scale runs the paper projects only 10 % of the data in the
+# full-PCA step (Section 5, ResNet activations) without saying which 10 %.
+# Reading: the rows are taken in blocks of 128 consecutive rows; block t is
+# kept when the t-th output of the SplitMix64 stream seeded with `seed`, as a
+# 53-bit fraction, is below `fraction`; if no block is kept, the block with the
+# smallest output (lowest index among ties) is.  The eigenvalues are those of
+# the sampled Gram matrix divided by the number of sampled rows.
+
+_MASK64 = (1 << 64) - 1
+_GOLDEN = 0x9E3779B97F4A7C15
+
+
+def splitmix64(state: int) -> int:
+    """SplitMix64 output for the stream state after its increment (Steele,
+    Lea and Flood, "Fast splittable pseudorandom number generators", 2014):
+    z = state; z = (z ^ z >> 30) * 0xBF58476D1CE4E5B9; z = (z ^ z >> 27) *
+    0x94D049BB133111EB; z ^ z >> 31, all modulo 2^64."""
+    z = state & _MASK64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK64
+    return z ^ (z >> 31)
+
+
+def sampled_tiles(n: int, fraction: float, seed: int, tile: int = 128):
+    """Indices of the kept 128-row blocks (ascending) and the kept row count."""
+    nt = (n + tile - 1) // tile
+    us = [splitmix64((seed + (t + 1) * _GOLDEN) & _MASK64) for t in range(nt)]
+    keep = [t for t in range(nt) if (us[t] >> 11) * 2.0 ** -53 < fraction]
+    if not keep:
+        keep = [min(range(nt), key=lambda t: (us[t], t))]
+    rows = sum(min(tile, n - t * tile) for t in keep)
+    return keep, rows
+
+
+def ppca_finalize_rows(X, V, k: int, tiles, tile: int = 128):
+    """ppca_finalize restricted to the rows of the given 128-row blocks:
+    G = (X_S Q)^T (X_S Q), eigenvalues / |S|."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    idx = np.concatenate([np.arange(t * tile, min((t + 1) * tile, n)) for t in tiles])
+    Q = orth(V)
+    Y = X[idx] @ Q
+    G = Y.T @ Y
+    w, U = eigh_desc(G)
+    E = sign_fix(Q @ U[:, :k])
+    return E, w[:k] / len(idx)
 
 
 # ---------------------------------------------------------------------------

@@ -426,142 +426,105 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
         if (tid == 0 && fallback) *fallback = 0;
         return;
     }
-    for (int p = 0; p < nb; ++p) {
-        const int p0 = p * kCB, bw = min(kCB, m - p0), p1 = p0 + bw;
-        float* Ap = A + p0 * lda + p0;      // diagonal block, row stride lda
-        float* Wp = W + p0 * lda + p0;
-        // (a) warp 0: the diagonal block as R_pp = S U (U unit upper, S = diag(s))
-        // by an LDL^T elimination, then W_pp = U^-1 S^-1.  Lane j holds column j
-        // in registers, shifted each step so that the active row sits at a[0]
-        // (no dynamic register indexing); rows of U are broadcast by shuffles.
-        if (warp == 0) {
-            const bool own = lane < bw;
-            float a[kCB];
+    // Right-looking Cholesky G' = R^T R (R upper) with the upper triangle held in
+    // registers: the 4 x 4 blocks (bi <= bj) are dealt to the threads, one or two
+    // each.  Step k: every thread takes the pivot from shared memory; the owners
+    // of block row k/4 write row k of R (R_kk = sqrt(a_kk), R_kj = a_kj / R_kk)
+    // into A; after a barrier every thread applies a_ij -= R_ki R_kj to its
+    // blocks and the owner of the next diagonal entry publishes the next pivot.
+    // Two barriers per column, all 512 threads busy in each.
+    {
+        __shared__ float sh_piv;
+        const int nq = (m + 3) / 4;
+        const int nblk = nq * (nq + 1) / 2;
+        int bI[2], bJ[2];
+        float a[2][4][4];
 #pragma unroll
-            for (int i = 0; i < kCB; ++i) a[i] = (own && i <= lane) ? Ap[i * lda + lane] : 0.f;
-            bool brk = false;
-            float dme = 1.f;                         // D_lane
-            for (int c = 0; c < bw; ++c) {
-                float piv = __shfl_sync(full, a[0], c);       // D_c = A_cc after the earlier columns
-                if (!(piv > 0.f)) {
-                    brk = true;
-                    piv = 1e-30f;
+        for (int s2 = 0; s2 < 2; ++s2) {
+            const int b = tid + s2 * kCBThreads;
+            bI[s2] = -1;
+            bJ[s2] = 0;
+            if (b < nblk) {
+                int bi = 0, rem = b;
+                while (rem >= nq - bi) {
+                    rem -= nq - bi;
+                    ++bi;
                 }
-                const float inv = __frcp_rn(piv);
-                const float acj = a[0];                        // A_cj (unscaled), lanes j >= c
-                const float ucj = acj * inv;                   // U_cj
-                if (own && lane > c) Ap[c * lda + lane] = ucj;
-                if (lane == c) dme = piv;
+                bI[s2] = bi;
+                bJ[s2] = bi + rem;
+            }
 #pragma unroll
-                for (int k = 1; k < kCB; ++k) {               // rows i = c + k: A_ij -= U_ci A_cj
-                    const float uci = __shfl_sync(full, ucj, (c + k) & (kCB - 1));
-                    if (c + k < bw && lane >= c + k) a[k] = __fmaf_rn(-uci, acj, a[k]);
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int ii = 4 * bI[s2] + u, jj = 4 * bJ[s2] + v;
+                    a[s2][u][v] = (bI[s2] >= 0 && ii < m && jj < m) ? A[ii * lda + jj] : 0.f;
                 }
-#pragma unroll
-                for (int k = 0; k < kCB - 1; ++k) a[k] = a[k + 1];
-                a[kCB - 1] = 0.f;
-            }
-            const float sme = __fsqrt_rn(dme);                 // s_lane
-            const float isme = __frcp_rn(sme);
-            __syncwarp();
-            // column `lane` of U^-1 (U x = e_lane, column-oriented back substitution), times 1/s_lane;
-            // y_i is kept at register position i + (kCB - 1 - l) while step l runs
-            float y[kCB];
-#pragma unroll
-            for (int k = 0; k < kCB; ++k) y[k] = (k - (kCB - bw) == lane) ? 1.f : 0.f;
-            for (int l = bw - 1; l >= 0; --l) {
-                const float xl = y[kCB - 1];
-                if (own) Wp[l * lda + lane] = (l <= lane) ? xl * isme : 0.f;
-#pragma unroll
-                for (int k = 0; k < kCB - 1; ++k) {           // row i = k + l - (kCB - 1) < l
-                    const int i = k + l - (kCB - 1);
-                    if (i >= 0) y[k] = __fmaf_rn(-Ap[i * lda + l], xl, y[k]);
-                }
-#pragma unroll
-                for (int k = kCB - 1; k > 0; --k) y[k] = y[k - 1];
-                y[0] = 0.f;
-            }
-            __syncwarp();
-            // R_pp = S U: row c scaled by s_c, diagonal s_c
-            for (int c = 0; c < bw; ++c) {
-                const float sc = __shfl_sync(full, sme, c);
-                if (own && lane > c) Ap[c * lda + lane] *= sc;
-                else if (lane == c) Ap[c * lda + c] = sc;
-            }
-            if (lane == 0 && brk) bad = 1;
         }
-        __syncthreads();
-        const int nj = m - p1;
-        if (nj <= 0) continue;
-        const int nq = (nj + 3) / 4;            // column quads of the trailing part
-        // (b) block row of R: R_pj = W_pp^T A_pj; thread = (row i, column quad)
-        {
-            constexpr int kPer = (kCB * 32 + kCBThreads - 1) / kCBThreads;
-            float4 vals[kPer];
+        if (tid == 0) sh_piv = A[0];
+        __syncthreads();                      // blocks loaded: A now receives the rows of R
+        for (int k = 0; k < m; ++k) {
+            float piv = sh_piv;
+            if (!(piv > 0.f)) {
+                piv = 1e-30f;
+                if (tid == 0) bad = 1;
+            }
+            const float rkk = __fsqrt_rn(piv);
+            const float inv = __frcp_rn(rkk);
+            const int kb = k >> 2, ku = k & 3;
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int e = tid + q * kCBThreads;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (e < bw * nq) {
-                    const int i = e / nq, j0 = p1 + (e % nq) * 4;
-                    for (int l = 0; l <= i; ++l) {
-                        const float w = W[(p0 + l) * lda + p0 + i];
-                        const float4 a4 = *reinterpret_cast<const float4*>(A + (p0 + l) * lda + j0);
-                        v.x = __fmaf_rn(w, a4.x, v.x);
-                        v.y = __fmaf_rn(w, a4.y, v.y);
-                        v.z = __fmaf_rn(w, a4.z, v.z);
-                        v.w = __fmaf_rn(w, a4.w, v.w);
+            for (int s2 = 0; s2 < 2; ++s2) {
+                if (bI[s2] != kb) continue;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (u != ku) continue;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int jj = 4 * bJ[s2] + v;
+                        if (jj > k && jj < lda) A[k * lda + jj] = a[s2][u][v] * inv;
+                        else if (jj == k) A[k * lda + k] = rkk;
                     }
                 }
-                vals[q] = v;
             }
             __syncthreads();
+            const int nk = k + 1, nkb = nk >> 2, nku = nk & 3;
 #pragma unroll
-            for (int q = 0; q < kPer; ++q) {
-                const int e = tid + q * kCBThreads;
-                if (e < bw * nq) {
-                    const int i = e / nq, j0 = p1 + (e % nq) * 4;
-                    *reinterpret_cast<float4*>(A + (p0 + i) * lda + j0) = vals[q];
-                }
-            }
-            __syncthreads();
-        }
-        // (c) trailing update A_ij -= sum_c R_ci R_cj on 4 x 4 blocks of the upper triangle
-        {
-            for (int e = tid; e < nq * nq; e += kCBThreads) {
-                const int bi = e / nq, bj = e % nq;
-                if (bi > bj) continue;
-                const int i0 = p1 + bi * 4, j0 = p1 + bj * 4;
-                float acc[4][4];
+            for (int s2 = 0; s2 < 2; ++s2) {
+                if (bI[s2] < 0 || 4 * bI[s2] + 3 <= k) continue;
+                const float4 ri = *reinterpret_cast<const float4*>(A + k * lda + 4 * bI[s2]);
+                const float4 rj = *reinterpret_cast<const float4*>(A + k * lda + 4 * bJ[s2]);
+                const float riv[4] = {ri.x, ri.y, ri.z, ri.w}, rjv[4] = {rj.x, rj.y, rj.z, rj.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-                for (int c = 0; c < bw; ++c) {
-                    const float* r = A + (p0 + c) * lda;
-                    const float4 ri = *reinterpret_cast<const float4*>(r + i0);
-                    const float4 rj = *reinterpret_cast<const float4*>(r + j0);
-                    const float riv[4] = {ri.x, ri.y, ri.z, ri.w}, rjv[4] = {rj.x, rj.y, rj.z, rj.w};
+                    for (int v = 0; v < 4; ++v) {
+                        const int ii = 4 * bI[s2] + u, jj = 4 * bJ[s2] + v;
+                        if (ii > k && jj >= ii) a[s2][u][v] = __fmaf_rn(-riv[u], rjv[v], a[s2][u][v]);
+                    }
+                if (nk < m && bI[s2] == nkb && bJ[s2] == nkb) {
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) acc[u][v] = __fmaf_rn(riv[u], rjv[v], acc[u][v]);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (i0 + u >= m) continue;
-                    float4* dst = reinterpret_cast<float4*>(A + (i0 + u) * lda + j0);
-                    float4 d4 = *dst;
-                    d4.x -= acc[u][0];
-                    d4.y -= acc[u][1];
-                    d4.z -= acc[u][2];
-                    d4.w -= acc[u][3];
-                    *dst = d4;
+                        if (u == nku) sh_piv = a[s2][u][u];
                 }
             }
             __syncthreads();
         }
     }
+    // diagonal blocks of W = R^-1: warp p inverts R_pp, lane j solving for its
+    // column by back substitution (W_lj = 0 below the diagonal, so every lane
+    // runs the same loops)
+    for (int p = warp; p < nb; p += nw) {
+        const int p0 = p * kCB, bw = min(kCB, m - p0);
+        const int jl = lane;
+        if (jl < bw) W[(p0 + jl) * lda + p0 + jl] = __frcp_rn(A[(p0 + jl) * lda + p0 + jl]);
+        for (int ii = bw - 2; ii >= 0; --ii) {
+            float sacc = 0.f;
+            for (int l = ii + 1; l < bw; ++l)
+                sacc = __fmaf_rn(A[(p0 + ii) * lda + p0 + l], jl < bw ? W[(p0 + l) * lda + p0 + jl] : 0.f, sacc);
+            if (jl < bw && jl > ii) W[(p0 + ii) * lda + p0 + jl] = -sacc / A[(p0 + ii) * lda + p0 + ii];
+        }
+    }
+    __syncthreads();
     // off-diagonal blocks of W, one block diagonal sd = q - p at a time; thread = (pair, row i, column quad)
     for (int sd = 1; sd < nb; ++sd) {
         const int npairs = nb - sd;

@@ -184,3 +184,55 @@ def test_principal_angles_known():
     E[:, 1] = [0, math.cos(t[1]), 0, math.sin(t[1]), 0, 0]
     pa = oracle.principal_angles(Q, E)
     np.testing.assert_allclose(pa, sorted(t), rtol=1e-9)
+
+
+# --- pPCA step on a seeded sample of the rows (Section 5: 10 % projected) ---
+
+def test_splitmix64_published_outputs():
+    """The SplitMix64 stream seeded with 0: its first three outputs as published
+    with the generator's reference implementation."""
+    golden = 0x9E3779B97F4A7C15
+    outs = [oracle.splitmix64((j * golden) & ((1 << 64) - 1)) for j in (1, 2, 3)]
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_sampled_tiles_selection_rules():
+    n = 128 * 5000 + 77                              # ragged last block
+    all_t, rows = oracle.sampled_tiles(n, 1.0, 3)
+    assert all_t == list(range(5001)) and rows == n
+    keep, rows = oracle.sampled_tiles(n, 0.1, 3)
+    assert keep == sorted(keep) and keep == oracle.sampled_tiles(n, 0.1, 3)[0]
+    # binomial(5001, 0.1): mean 500, sd 21
+    assert abs(len(keep) - 500.1) < 5 * 21.2
+    assert rows == 128 * len(keep) - (51 if 5000 in keep else 0)
+    assert keep != oracle.sampled_tiles(n, 0.1, 4)[0]
+    one, rows1 = oracle.sampled_tiles(1000, 1e-30, 9)    # nothing passes: one block is kept
+    assert len(one) == 1 and rows1 == (128 if one[0] < 7 else 1000 - 7 * 128)
+
+
+def test_ppca_finalize_rows_all_blocks_is_the_full_step():
+    rng = np.random.default_rng(5)
+    n, d, m, k = 700, 12, 6, 4
+    X = rng.standard_normal((n, d)) * np.linspace(3, 0.5, d)
+    V = rng.standard_normal((d, m))
+    tiles, _ = oracle.sampled_tiles(n, 1.0, 1)
+    E1, l1 = oracle.ppca_finalize_rows(X, V, k, tiles)
+    E0, l0 = oracle.ppca_finalize(X, V, k)
+    np.testing.assert_allclose(l1, l0, rtol=1e-12)
+    np.testing.assert_allclose(E1, E0, atol=1e-10)
+
+
+def test_ppca_finalize_rows_on_repeated_block_matches_full():
+    """Data made of one 128-row block repeated: every block-aligned sample has
+    the same per-row covariance, so the sampled step returns the full result."""
+    rng = np.random.default_rng(6)
+    d, m, k = 10, 5, 3
+    B = rng.standard_normal((128, d)) * np.linspace(2, 0.3, d)
+    X = np.tile(B, (40, 1))
+    V = rng.standard_normal((d, m))
+    E0, l0 = oracle.ppca_finalize(X, V, k)
+    for seed in (1, 2, 3):
+        tiles, rows = oracle.sampled_tiles(X.shape[0], 0.25, seed)
+        E1, l1 = oracle.ppca_finalize_rows(X, V, k, tiles)
+        np.testing.assert_allclose(l1, l0, rtol=1e-12)
+        np.testing.assert_allclose(E1, E0, atol=1e-10)
