@@ -197,6 +197,37 @@ PPCA_API ppca_status ppca_upload(ppca_handle *h, const void *X_host, int64_t ld_
 PPCA_API ppca_status ppca_finalize_host(ppca_handle *h, int32_t k, float *E_host, double *lambda_host,
                                         ppca_precision precision);
 
+/*
+ * pPCA step on a seeded sample of the rows.  For its large runs the paper
+ * projects only 10 % of the data in the full-PCA step, which cuts that step's
+ * cost about tenfold (Section 5, large-scale datasets).  Rows are taken in
+ * blocks of 128 consecutive rows (the last block may be shorter): block t is
+ * kept when the t-th output of the SplitMix64 stream seeded with `seed`
+ * (Steele, Lea and Flood, 2014: z = seed + t' * 0x9E3779B97F4A7C15 for
+ * t' = t + 1, then the published mixing steps), as a 53-bit fraction, is below
+ * `fraction`; if no block is kept, the block with the smallest output is.
+ * Steps 2-5 then run as in ppca_finalize with G = (X_S Q)^T (X_S Q) over the
+ * sampled rows S and lambda = eig(G) / |S|.
+ *   fraction  in (0, 1]; 1 keeps every block (the result equals ppca_finalize's)
+ *   rows_used host, may be NULL: |S|
+ * BF16 or FP32 data (or the ppca_set_refine copy) on tensor cores only:
+ * PPCA_ERR_UNSUPPORTED otherwise.
+ */
+PPCA_API ppca_status ppca_finalize_sampled(ppca_handle *h, int32_t k, float *E, double *lambda,
+                                           ppca_precision precision, double fraction, uint64_t seed,
+                                           int64_t *rows_used);
+
+/*
+ * Variance captured by each of k directions, the evaluation of the paper's
+ * large-scale runs (Section 5.3): var[j] = e_j^T (X^T X) e_j for the columns
+ * e_j of E (device, d x k column-major FP32, taken as given), one pass over X
+ * (the ppca_set_refine copy when set).  var: device, k FP64.  ACCURATE/AUTO:
+ * split-precision products (about 2^-24); FAST: the fast products.  After
+ * ppca_prime, k may not exceed its m (PPCA_ERR_INVALID).
+ */
+PPCA_API ppca_status ppca_variance_captured(ppca_handle *h, const float *E, int32_t k, double *var,
+                                            ppca_precision precision);
+
 /* Device copy of the current primed basis V (d x m column-major FP32). */
 PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
 

@@ -27,7 +27,7 @@ __all__ = [
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
-    "ppca_upload", "ppca_finalize_host", "EXPORTED_SYMBOLS",
+    "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,7 +48,7 @@ EXPORTED_SYMBOLS = [
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
-    "ppca_upload", "ppca_finalize_host",
+    "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured",
 ]
 
 
@@ -131,6 +131,9 @@ _SIGS = {
     "ppca_finalize": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int]),
     "ppca_upload": (_c_status, [_vp, _vp, _i64, _vp]),
     "ppca_finalize_host": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int]),
+    "ppca_finalize_sampled": (_c_status, [_vp, _i32, _vp, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_uint64,
+                                          ctypes.POINTER(_i64)]),
+    "ppca_variance_captured": (_c_status, [_vp, _vp, _i32, _vp, ctypes.c_int]),
     "ppca_get_basis": (_c_status, [_vp, _vp]),
     "ppca_sync": (_c_status, [_vp]),
     "ppca_get_state": (_c_status, [_vp, _vp, ctypes.POINTER(_i64)]),
@@ -301,6 +304,21 @@ def ppca_finalize_host(h: Handle, k: int, E_host, lam_host, precision: int = PPC
     """pPCA step with E (k x d row-major = d x k column-major FP32) and lambda (k FP64) written to host memory."""
     _check(load_library().ppca_finalize_host(h.ptr, k, _ptr(E_host), _ptr(lam_host), precision),
            "ppca_finalize_host")
+
+
+def ppca_finalize_sampled(h: Handle, k: int, E, lam, precision: int = PPCA_PREC_AUTO, fraction: float = 0.1,
+                          seed: int = 0) -> int:
+    """pPCA step over a seeded sample of 128-row blocks; returns the number of sampled rows."""
+    rows = ctypes.c_int64(0)
+    _check(load_library().ppca_finalize_sampled(h.ptr, k, _ptr(E), _ptr(lam), precision, fraction, seed,
+                                                ctypes.byref(rows)), "ppca_finalize_sampled")
+    return rows.value
+
+
+def ppca_variance_captured(h: Handle, E, k: int, var, precision: int = PPCA_PREC_AUTO):
+    """var[j] = e_j^T X^T X e_j for the k columns of E (device (k, d) tensor = d x k column-major)."""
+    _check(load_library().ppca_variance_captured(h.ptr, _ptr(E), k, _ptr(var), precision),
+           "ppca_variance_captured")
 
 
 def ppca_get_basis(h: Handle, V_out):

@@ -88,6 +88,7 @@ struct ppca_handle {
     double* U = nullptr;      // m x m
     float* E_res = nullptr;   // d x m: ppca_finalize_host's eigenvectors before the copy out
     double* lam_res = nullptr;  // m: ppca_finalize_host's eigenvalues
+    int* tile_rows = nullptr;   // ceil(n / 128): first rows of the blocks of a row sample
     float* gram_part = nullptr;
     void* jac = nullptr;
     double* eg = nullptr;
@@ -120,7 +121,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
     size_t need = 5 * dm + al256((size_t)m * m * 8) + 2 * al256((size_t)m * m * 4) + al256((size_t)m * 8) +
                   al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
-                  dm + al256((size_t)m * 8) +
+                  dm + al256((size_t)m * 8) + al256((size_t)((n + 127) / 128) * 4) +
                   al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
                   al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
     if (h->ws_limit > 0 && (int64_t)need > h->ws_limit)
@@ -154,6 +155,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     h->U = reinterpret_cast<double*>(take((size_t)m * m * 8));
     h->E_res = reinterpret_cast<float*>(take((size_t)d * m * 4));
     h->lam_res = reinterpret_cast<double*>(take((size_t)m * 8));
+    h->tile_rows = reinterpret_cast<int*>(take((size_t)((n + 127) / 128) * 4));
     h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
     h->jac = take(jacobi_scratch_bytes(m));
     h->eg = reinterpret_cast<double*>(take(eigengame_scratch_bytes(d, m)));
@@ -505,6 +507,70 @@ ppca_status ppca_upload(ppca_handle* h, const void* X_host, int64_t ld_host, con
     if (row_scales_host)
         CUDA_TRY(cudaMemcpyAsync(const_cast<float*>(x.scales), row_scales_host, (size_t)x.n * sizeof(float),
                                  cudaMemcpyHostToDevice, h->stream));
+    return PPCA_OK;
+}
+
+ppca_status ppca_finalize_sampled(ppca_handle* h, int32_t k, float* E, double* lambda, ppca_precision precision,
+                                  double fraction, uint64_t seed, int64_t* rows_used) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (h->method < 0) return fail(PPCA_ERR_STATE, "finalize before prime");
+    const int m = h->m;
+    if (k < 1 || k > m) return fail(PPCA_ERR_INVALID, "k = %d out of range [1, m = %d]", k, m);
+    if (!E || !lambda) return fail(PPCA_ERR_INVALID, "E or lambda is NULL");
+    if (precision < PPCA_PREC_AUTO || precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", (int)precision);
+    if (!(fraction > 0.0 && fraction <= 1.0)) return fail(PPCA_ERR_INVALID, "fraction must be in (0, 1]");
+    const XView& xf = h->has_ref ? h->xref : h->x;
+    if (!tc_pass_supported(xf, m) || xf.dtype == PPCA_FP8_E4M3 || h->sched.engine == 2)
+        return fail(PPCA_ERR_UNSUPPORTED, "the sampled pPCA step runs on tensor cores over BF16 or FP32 data");
+    const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_ACCURATE : precision;
+    const int64_t d = h->x.d, n = xf.n, nt = (n + 127) / 128;
+    // the kept blocks (the device kernel builds the same list from the same rule)
+    int64_t nsel = 0, rows = 0, best_t = 0;
+    uint64_t best_u = ~0ull;
+    for (int64_t t = 0; t < nt; ++t) {
+        const uint64_t u = sample_block_u(seed, t);
+        if (u < best_u) {
+            best_u = u;
+            best_t = t;
+        }
+        if (sample_block_kept(u, fraction)) {
+            ++nsel;
+            rows += std::min<int64_t>(128, n - t * 128);
+        }
+    }
+    int64_t forced = -1;
+    if (nsel == 0) {
+        forced = best_t;
+        nsel = 1;
+        rows = std::min<int64_t>(128, n - best_t * 128);
+    }
+    CUDA_TRY(sample_blocks(n, fraction, seed, forced, h->tile_rows, h->stream));
+    PPCA_TRY(run_orth(h, h->V, h->Q, m));                                          // step 2: span
+    cudaEvent_t ev_end = nullptr;
+    PPCA_TRY(pass_timer(h, prec, rows, &ev_end));
+    CUDA_TRY(projected_gram_tc_blocks(xf, h->Q, m, h->tile_rows, (int)nsel, h->G, prec, h->sched.flush, h->tc,
+                                      h->status, h->num_sms, h->stream));         // step 3 on the sample
+    if (ev_end) CUDA_TRY(cudaEventRecord(ev_end, h->stream));
+    CUDA_TRY(eigh_small(h->G, m, h->w, h->U, h->jac, h->status, h->stream));       // step 4
+    CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)rows, E, lambda, h->stream));
+    if (rows_used) *rows_used = rows;
+    return PPCA_OK;
+}
+
+ppca_status ppca_variance_captured(ppca_handle* h, const float* E, int32_t k, double* var, ppca_precision precision) {
+    if (!h || !E || !var) return fail(PPCA_ERR_INVALID, "NULL argument");
+    if (k < 1 || k > kMaxM || k > h->x.d) return fail(PPCA_ERR_INVALID, "k = %d out of range", k);
+    if (precision < PPCA_PREC_AUTO || precision > PPCA_PREC_ACCURATE)
+        return fail(PPCA_ERR_INVALID, "unknown precision %d", (int)precision);
+    const ppca_precision prec = precision == PPCA_PREC_AUTO ? PPCA_PREC_ACCURATE : precision;
+    if (h->method >= 0 && k > h->ws_m)      // a larger workspace would drop the primed basis
+        return fail(PPCA_ERR_INVALID, "k = %d exceeds the primed width m = %d", k, h->ws_m);
+    PPCA_TRY(ensure_workspace(h, std::max(k, h->ws_m)));
+    const XView& xf = h->has_ref ? h->xref : h->x;
+    PPCA_TRY(run_gram(h, xf, E, k, 0, xf.n, h->G, prec));                         // G = (X E)^T (X E)
+    CUDA_TRY(cudaMemcpy2DAsync(var, sizeof(double), h->G, (size_t)(k + 1) * sizeof(double), sizeof(double), (size_t)k,
+                               cudaMemcpyDeviceToDevice, h->stream));              // its diagonal
     return PPCA_OK;
 }
 

@@ -128,4 +128,25 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 void note_launch();
 int64_t launches_so_far();
 
+// Row sample of the pPCA step (the paper projects 10 % of the data in its
+// large runs): 128-row block t is kept when the t-th output of the SplitMix64
+// stream seeded with `seed` (Steele, Lea and Flood, 2014), as a 53-bit
+// fraction, is below `fraction`.  Host and device evaluate the same integer
+// arithmetic and the same exact double comparison.
+constexpr uint64_t kSplitMixGolden = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ inline uint64_t splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ inline uint64_t sample_block_u(uint64_t seed, int64_t t) {
+    return splitmix64_mix(seed + (uint64_t)(t + 1) * kSplitMixGolden);
+}
+
+__host__ __device__ inline bool sample_block_kept(uint64_t u, double fraction) {
+    return (double)(u >> 11) * 0x1p-53 < fraction;
+}
+
 }  // namespace ppca

@@ -56,6 +56,11 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
 cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, const double* w, int k,
                             double inv_n, float* E, double* lambda, cudaStream_t st);
 
+// First rows of the kept 128-row blocks of an n-row matrix (ascending), by
+// sample_block_kept; forced >= 0: keep that block alone (no block passed).
+cudaError_t sample_blocks(int64_t n, double fraction, uint64_t seed, int64_t forced, int* tile_rows,
+                          cudaStream_t st);
+
 // Oja/Sanger update: W += c (Z - W triu(S)), S = W^T Z (m x m FP64 row-major), c = lr / b.
 cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c,
                        cudaStream_t st);

@@ -151,7 +151,8 @@ __device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col,
 template <int NX, int NV, bool F32X>
 __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
     ygen_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int ntiles, int nk,
-                int flush, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int* status) {
+                int flush, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy,
+                const int* __restrict__ tile_row, int* status) {
     constexpr int ORD = (NX > NV ? NX : NV) - 1;
     constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
     extern __shared__ uint8_t smem_raw[];
@@ -171,6 +172,9 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
             uint32_t it = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                // Y tile t comes from X rows [xr, xr + 128): consecutive tiles, or
+                // the listed 128-row blocks of a row sample
+                const int xr = tile_row ? tile_row[t] : t * 128;
                 for (int k = 0; k < nk; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
@@ -181,10 +185,10 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                     tc::mbar_expect_tx(&hd->full[s], (F32X ? 2u * kPiece : kPiece) + NV * q_piece);
                     uint8_t* st = tiles + (size_t)s * stage_bytes;
                     if (F32X) {
-                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, t * 128);
-                        tc::tma_load_2d(st + kPiece, &tmX, &hd->full[s], k * kGBK + 32, t * 128);
+                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, xr);
+                        tc::tma_load_2d(st + kPiece, &tmX, &hd->full[s], k * kGBK + 32, xr);
                     } else {
-                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, t * 128);
+                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, xr);
                     }
 #pragma unroll
                     for (int p = 0; p < NV; ++p)
@@ -476,7 +480,8 @@ __global__ void gram_parts_reduce_kernel(const float2* __restrict__ Gpart, int n
 
 template <int NX, int NV, bool F32X>
 cudaError_t launch_ygen(const CUtensorMap& tmX, const CUtensorMap& tmQ, int ntiles, int nk, int flush, int m_pad,
-                        __nv_bfloat16* Yt, int64_t ldy, int* status, int num_sms, cudaStream_t st) {
+                        __nv_bfloat16* Yt, int64_t ldy, const int* tile_row, int* status, int num_sms,
+                        cudaStream_t st) {
     constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
     const uint32_t stage_bytes = x_bytes + NV * (uint32_t)m_pad * 128u;
     int stages = (int)((kGSmemBudget - 2048) / stage_bytes);
@@ -489,7 +494,7 @@ cudaError_t launch_ygen(const CUtensorMap& tmX, const CUtensorMap& tmQ, int ntil
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     note_launch();
     kern<<<grid, F32X ? kGThreadsF32 : kGThreadsBf16, smem, st>>>(tmX, tmQ, ntiles, nk, flush, m_pad, stages, Yt, ldy,
-                                                                 status);
+                                                                 tile_row, status);
     return cudaGetLastError();
 }
 
@@ -497,15 +502,20 @@ inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 }  // namespace
 
-cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
-                              ppca_precision prec, int flush, const TcPassScratch& sc, int* status, int num_sms,
-                              cudaStream_t st) {
+namespace {
+
+// G = (X_S Q)^T (X_S Q) with X_S = rows [r0, r1) (tile_row == nullptr) or the
+// nsel listed 128-row blocks of X (tile_row: device array of their first rows).
+cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r0, int64_t r1,
+                                const int* tile_row, int nsel, double* G, ppca_precision prec, int flush,
+                                const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
     if (r1 <= r0 || m < 1 || m > 128) return cudaErrorInvalidValue;
+    if (tile_row && nsel < 1) return cudaErrorInvalidValue;
     const bool f32 = x.dtype == PPCA_F32;
     const bool accurate = prec != PPCA_PREC_FAST;
     const int m_pad = (int)rup(m, 32);
     const int64_t d = x.d, rows = r1 - r0;
-    const int64_t ldv = rup(d, 8), ldy = rup(rows, 128);
+    const int64_t ldv = rup(d, 8), ldy = tile_row ? (int64_t)nsel * 128 : rup(rows, 128);
     const int ntiles = (int)(ldy / 128), nk = (int)((d + kGBK - 1) / kGBK);
     const int NV = accurate ? 3 : (f32 ? 2 : 1);
     if (flush <= 0) flush = accurate ? (f32 ? 1 : 2) : nk;
@@ -523,11 +533,11 @@ cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0,
         !encode_bf16_2d(&tmY, Yt, ldy, 3ull * m_pad, ldy * 2, 64, m_pad))
         return cudaErrorInvalidValue;
     if (f32) {
-        e = accurate ? launch_ygen<3, 3, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st)
-                     : launch_ygen<2, 2, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st);
+        e = accurate ? launch_ygen<3, 3, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st)
+                     : launch_ygen<2, 2, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st);
     } else {
-        e = accurate ? launch_ygen<1, 3, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st)
-                     : launch_ygen<1, 1, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, status, num_sms, st);
+        e = accurate ? launch_ygen<1, 3, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st)
+                     : launch_ygen<1, 1, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st);
     }
     if (e != cudaSuccess) return e;
     // G = Y^T Y
@@ -545,6 +555,20 @@ cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0,
     note_launch();
     gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
+                              ppca_precision prec, int flush, const TcPassScratch& sc, int* status, int num_sms,
+                              cudaStream_t st) {
+    return projected_gram_impl(x, Q, m, r0, r1, nullptr, 0, G, prec, flush, sc, status, num_sms, st);
+}
+
+cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, const int* tile_row, int nsel, double* G,
+                                     ppca_precision prec, int flush, const TcPassScratch& sc, int* status,
+                                     int num_sms, cudaStream_t st) {
+    return projected_gram_impl(x, Q, m, 0, x.n, tile_row, nsel, G, prec, flush, sc, status, num_sms, st);
 }
 
 }  // namespace ppca

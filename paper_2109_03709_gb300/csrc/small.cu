@@ -1227,6 +1227,54 @@ cudaError_t eigh_small_noalloc(const double* G, int m, double* w, double* U, int
     return eigh_small(G, m, w, U, scratch, status, st);
 }
 
+namespace {
+
+// One CTA walks the blocks in chunks of its size; a block-wide exclusive scan
+// of the keep flags gives each kept block its position, so the list comes out
+// in ascending order.
+constexpr int kSampleThreads = 1024;
+
+__global__ void __launch_bounds__(kSampleThreads) sample_blocks_kernel(int64_t n, double fraction, uint64_t seed,
+                                                                      int64_t forced, int* __restrict__ tile_rows) {
+    __shared__ int warp_sum[kSampleThreads / 32];
+    __shared__ int base;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (forced >= 0) {
+        if (threadIdx.x == 0) tile_rows[0] = (int)(forced * 128);
+        return;
+    }
+    const int64_t nt = (n + 127) / 128;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < nt; c0 += kSampleThreads) {
+        const int64_t t = c0 + threadIdx.x;
+        const bool keep = t < nt && sample_block_kept(sample_block_u(seed, t), fraction);
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) warp_sum[warp] = __popc(ball);
+        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += warp_sum[w];
+        const int pos = base + before + __popc(ball & ((1u << lane) - 1u));
+        if (keep) tile_rows[pos] = (int)(t * 128);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int tot = 0;
+            for (int w = 0; w < kSampleThreads / 32; ++w) tot += warp_sum[w];
+            base += tot;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+cudaError_t sample_blocks(int64_t n, double fraction, uint64_t seed, int64_t forced, int* tile_rows,
+                          cudaStream_t st) {
+    note_launch();
+    sample_blocks_kernel<<<1, kSampleThreads, 0, st>>>(n, fraction, seed, forced, tile_rows);
+    return cudaGetLastError();
+}
+
 cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, const double* w, int k, double inv_n,
                             float* E, double* lambda, cudaStream_t st) {
     note_launch();

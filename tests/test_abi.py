@@ -69,6 +69,8 @@ def test_argument_checks_need_no_device(lib):
     assert lib.ppca_finalize(None, 1, fake, fake, 0) == 1
     assert lib.ppca_upload(None, fake, 4, None) == 1
     assert lib.ppca_finalize_host(None, 1, fake, fake, 0) == 1
+    assert lib.ppca_finalize_sampled(None, 1, fake, fake, 0, 0.1, 1, None) == 1
+    assert lib.ppca_variance_captured(None, fake, 1, fake, 0) == 1
     assert lib.ppca_sync(None) == 1
     assert lib.ppca_destroy(None) == 0
     assert lib.ppca_quantize_bf16(None, 4, 4, 4, fake, 4, None) == 1
