@@ -38,7 +38,7 @@ import numpy as np
 __all__ = [
     "build_native", "jacobi_eigh", "eigh_desc", "sign_fix", "orth", "qr_pos",
     "covariance", "ground_truth", "ppca_finalize", "ppca_finalize_cov",
-    "power_step", "power_prime", "minibatch_rows", "oja_step", "oja_prime",
+    "power_step", "power_prime", "power_seq_prime", "minibatch_rows", "oja_step", "oja_prime",
     "eigengame_gradients", "eigengame_step", "eigengame_prime",
     "angle", "angles", "lces", "principal_angles", "variance_captured",
     "splitmix64", "sampled_tiles", "ppca_finalize_rows",
@@ -273,6 +273,37 @@ def power_prime(X, V0, T: int):
     for _ in range(T):
         Q = power_step(X, Q)
     return Q
+
+
+def power_seq_prime(X, V0, T: int, eps: float):
+    """The power method as Section 2.1 describes it: one direction at a time,
+    x <- M x / |M x| with M = X^T X, each step orthogonalised against the
+    directions already found (the complement of their span), until
+    |x_t - x_{t+1}| < eps or T steps.  Direction j starts from column j of
+    orth(V0); the orthogonalisation is classical Gram-Schmidt applied twice.
+    Returns V (d x m) and the steps taken per direction."""
+    X = np.asarray(X, dtype=np.float64)
+    Q0 = orth(V0)
+    d, m = Q0.shape
+    V = np.zeros((d, m))
+    steps = []
+    for j in range(m):
+        x = Q0[:, j].copy()
+        Vp = V[:, :j]
+        t = 0
+        while t < T:
+            y = X.T @ (X @ x)
+            for _ in range(2):
+                y = y - Vp @ (Vp.T @ y)
+            x_new = y / np.linalg.norm(y)
+            t += 1
+            done = np.linalg.norm(x_new - x) < eps
+            x = x_new
+            if done:
+                break
+        V[:, j] = x
+        steps.append(t)
+    return V, steps
 
 
 def minibatch_rows(t: int, n: int, b: int):

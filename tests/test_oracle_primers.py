@@ -198,3 +198,48 @@ def _no_penalty(Xb, V):
 def test_planted_mistake_in_eigengame_fails_the_ordering_pin():
     X, Q, lam = small_problem(n=2000, d=8, seed=12)
     assert _ordered_convergence_eg(_no_penalty, X, Q, 3) > 0.1
+
+
+# --- sequential power method with epsilon termination (Section 2.1) ---
+
+def test_power_seq_iterates_follow_the_closed_form():
+    """M = diag(l1, l2): from x0 = (cos a, sin a) the power iterate after t steps
+    is proportional to (l1^t cos a, l2^t sin a)."""
+    l1, l2, a = 4.0, 1.0, 0.7
+    X = np.diag(np.sqrt([l1, l2]))
+    V0 = np.array([[math.cos(a)], [math.sin(a)]])
+    for T in (1, 2, 5):
+        V, steps = oracle.power_seq_prime(X, V0, T, 0.0)
+        ref = np.array([l1 ** T * math.cos(a), l2 ** T * math.sin(a)])
+        ref /= np.linalg.norm(ref)
+        np.testing.assert_allclose(V[:, 0], ref, rtol=1e-12)
+        assert steps == [T]
+
+
+def test_power_seq_finds_the_axes_of_a_diagonal_spectrum():
+    rng = np.random.default_rng(2)
+    d, m = 8, 4
+    lam = 2.0 ** -np.arange(d)
+    X = np.diag(np.sqrt(lam))                     # X^T X = diag(lam): eigenvectors are the axes
+    V, steps = oracle.power_seq_prime(X, rng.standard_normal((d, m)), 2000, 1e-12)
+    for j in range(m):
+        assert abs(abs(V[j, j]) - 1.0) < 1e-10
+    assert np.abs(V.T @ V - np.eye(m)).max() < 1e-12
+    # rate lam_{j+1}/lam_j = 1/2: about log2(1/eps) steps each
+    assert all(30 <= s <= 60 for s in steps), steps
+
+
+def test_power_seq_stops_at_the_first_step_below_eps():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((200, 6)) * np.array([3.0, 2.0, 1.5, 1.0, 0.5, 0.2])
+    V0 = rng.standard_normal((6, 2))
+    V, steps = oracle.power_seq_prime(X, V0, 500, 1e-4)
+    # rerun the first direction step by step: the recorded count is the first t with |x_t - x_{t-1}| < eps
+    M = X.T @ X
+    x = oracle.orth(V0)[:, 0]
+    for t in range(1, steps[0] + 1):
+        y = M @ x
+        xn = y / np.linalg.norm(y)
+        diff = np.linalg.norm(xn - x)
+        x = xn
+        assert (diff < 1e-4) == (t == steps[0])
