@@ -77,8 +77,12 @@ typedef enum ppca_dtype {
 typedef enum ppca_method {
     PPCA_POWER = 0,           /* simultaneous (block) power iteration, Section 2.1     */
     PPCA_OJA = 1,             /* generalised Oja / Sanger rule, Section 2.2            */
-    PPCA_EIGENGAME = 2        /* EigenGame utilities (Section 2.3, Eqs. 1-3), SGD with */
+    PPCA_EIGENGAME = 2,       /* EigenGame utilities (Section 2.3, Eqs. 1-3), SGD with */
                               /* Nesterov momentum (Section 5), parallel players        */
+    PPCA_POWER_SEQ = 3        /* the power method of Section 2.1 one direction at a    */
+                              /* time: x <- X^T X x / |X^T X x|, each step kept in the  */
+                              /* complement of the directions found, until             */
+                              /* |x_t - x_{t+1}| < eps or T steps                       */
 } ppca_method;
 
 /* Arithmetic of the X-streaming products (tensor cores, FP32 accumulation). */
@@ -105,6 +109,7 @@ typedef struct ppca_prime_params {
     int64_t t0;               /* step counter of the first step (for resume)            */
     int32_t precision;        /* ppca_precision of the priming passes                   */
     int32_t reserved;         /* must be 0                                              */
+    double eps;               /* POWER_SEQ: termination threshold on |x_t - x_{t+1}|    */
 } ppca_prime_params;
 
 /* Library version, (major << 16) | minor. */
@@ -114,7 +119,8 @@ PPCA_API int32_t ppca_version(void);
 PPCA_API const char *ppca_last_error(void);
 
 /* Defaults: POWER -- nothing; OJA -- batch 256, lr 1, lr_offset 100 (so step t
- * uses 1/(t+100)); EIGENGAME -- batch 1024, lr 0.05, momentum 0.9.  Sets every
+ * uses 1/(t+100)); EIGENGAME -- batch 1024, lr 0.05, momentum 0.9; POWER_SEQ --
+ * eps 1e-6.  Sets every
  * other field to zero / NULL.  Returns PPCA_ERR_INVALID for a NULL p or an
  * unknown method. */
 PPCA_API ppca_status ppca_prime_params_default(ppca_prime_params *p, ppca_method method);
@@ -151,6 +157,14 @@ PPCA_API ppca_status ppca_set_workspace_limit(ppca_handle *h, int64_t bytes);
  *   EIGENGAME  T minibatch steps; every player ascends its utility (Eq. 3)
  *              with M_b = X_b^T X_b / |b|, gradient projected on the sphere's
  *              tangent space, Nesterov momentum, then renormalised.
+ *   POWER_SEQ  the power method as Section 2.1 describes it: direction j
+ *              starts from column j of orth(V0) and takes steps
+ *              x <- P (X^T X x) / |P (X^T X x)|, P the projection on the
+ *              complement of the directions already found (classical
+ *              Gram-Schmidt, twice), until |x_t - x_{t+1}| < p->eps or T steps
+ *              (T is a cap per direction).  The stopping test reads one number
+ *              back per step, so this call blocks the host until it is done.
+ *              ppca_prime_continue is not available for it.
  * Minibatch t covers rows [j b, min((j+1) b, n)), j = t mod ceil(n / b).
  * Requires 1 <= m <= min(d, n - 1, 128) and T >= 0.  p may be NULL (defaults).
  * Resets the handle's priming state (basis, step counter, momentum).

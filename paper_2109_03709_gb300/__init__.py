@@ -18,7 +18,7 @@ import threading
 
 __all__ = [
     "PPCAError", "load_library", "library_path",
-    "PPCA_OK", "PPCA_F32", "PPCA_BF16", "PPCA_FP8_E4M3", "PPCA_POWER", "PPCA_OJA", "PPCA_EIGENGAME",
+    "PPCA_OK", "PPCA_F32", "PPCA_BF16", "PPCA_FP8_E4M3", "PPCA_POWER", "PPCA_OJA", "PPCA_EIGENGAME", "PPCA_POWER_SEQ",
     "PPCA_PREC_AUTO", "PPCA_PREC_FAST", "PPCA_PREC_ACCURATE", "ppca_prime_params",
     "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
@@ -35,7 +35,7 @@ _LIBPATH = os.path.join(_HERE, "_lib", "libppca_gb300.so")
 
 PPCA_OK = 0
 PPCA_F32, PPCA_BF16, PPCA_FP8_E4M3 = 0, 1, 2
-PPCA_POWER, PPCA_OJA, PPCA_EIGENGAME = 0, 1, 2
+PPCA_POWER, PPCA_OJA, PPCA_EIGENGAME, PPCA_POWER_SEQ = 0, 1, 2, 3
 PPCA_PREC_AUTO, PPCA_PREC_FAST, PPCA_PREC_ACCURATE = 0, 1, 2
 
 _STATUS = {0: "PPCA_OK", 1: "PPCA_ERR_INVALID", 2: "PPCA_ERR_OOM", 3: "PPCA_ERR_CUDA", 4: "PPCA_ERR_STATE",
@@ -70,6 +70,7 @@ class ppca_prime_params(ctypes.Structure):
         ("t0", ctypes.c_int64),
         ("precision", ctypes.c_int32),
         ("reserved", ctypes.c_int32),
+        ("eps", ctypes.c_double),
     ]
 
 

@@ -89,6 +89,7 @@ struct ppca_handle {
     float* E_res = nullptr;   // d x m: ppca_finalize_host's eigenvectors before the copy out
     double* lam_res = nullptr;  // m: ppca_finalize_host's eigenvalues
     int* tile_rows = nullptr;   // ceil(n / 128): first rows of the blocks of a row sample
+    double* seq_diff = nullptr; // POWER_SEQ: |x_t - x_{t+1}| of the last step
     float* gram_part = nullptr;
     void* jac = nullptr;
     double* eg = nullptr;
@@ -121,7 +122,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     const int nsplit = simt_pass_nsplit(n, d, m, h->num_sms);
     size_t need = 5 * dm + al256((size_t)m * m * 8) + 2 * al256((size_t)m * m * 4) + al256((size_t)m * 8) +
                   al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
-                  dm + al256((size_t)m * 8) + al256((size_t)((n + 127) / 128) * 4) +
+                  dm + al256((size_t)m * 8) + al256((size_t)((n + 127) / 128) * 4) + al256(8) +
                   al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
                   al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
     if (h->ws_limit > 0 && (int64_t)need > h->ws_limit)
@@ -156,6 +157,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     h->E_res = reinterpret_cast<float*>(take((size_t)d * m * 4));
     h->lam_res = reinterpret_cast<double*>(take((size_t)m * 8));
     h->tile_rows = reinterpret_cast<int*>(take((size_t)((n + 127) / 128) * 4));
+    h->seq_diff = reinterpret_cast<double*>(take(8));
     h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
     h->jac = take(jacobi_scratch_bytes(m));
     h->eg = reinterpret_cast<double*>(take(eigengame_scratch_bytes(d, m)));
@@ -278,9 +280,34 @@ ppca_precision prime_prec(const ppca_handle* h) {
     return p == PPCA_PREC_AUTO ? PPCA_PREC_FAST : (ppca_precision)p;
 }
 
+// The power method of Section 2.1, one direction at a time (T: step cap per
+// direction).  Each step is one X-pass of the direction, then its projection
+// on the complement of the directions found, normalisation and the distance to
+// the previous iterate (power_seq_update, FP64), which is read back for the
+// stopping test.
+ppca_status run_power_seq(ppca_handle* h, int64_t T) {
+    const int m = h->m;
+    const int64_t n = h->x.n, d = h->x.d;
+    const double eps = h->params.eps;
+    for (int j = 0; j < m; ++j) {
+        float* x = h->V + (size_t)j * d;
+        for (int64_t t = 0; t < T; ++t) {
+            PPCA_TRY(run_xpass(h, h->x, x, 1, 0, n, h->Z, prime_prec(h)));      // y = X^T X x
+            CUDA_TRY(power_seq_update(h->V, d, j, h->Z, h->seq_diff, h->stream));
+            ++h->iters;
+            double diff = 0.0;
+            CUDA_TRY(cudaMemcpyAsync(&diff, h->seq_diff, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CUDA_TRY(cudaStreamSynchronize(h->stream));
+            if (diff < eps) break;
+        }
+    }
+    return PPCA_OK;
+}
+
 ppca_status run_steps(ppca_handle* h, int64_t T) {
     const int m = h->m;
     const int64_t n = h->x.n, d = h->x.d;
+    if (h->method == PPCA_POWER_SEQ) return run_power_seq(h, T);
     for (int64_t i = 0; i < T; ++i) {
         switch (h->method) {
         case PPCA_POWER:
@@ -352,6 +379,9 @@ ppca_status ppca_prime_params_default(ppca_prime_params* p, ppca_method method) 
         p->lr = 0.05;
         p->momentum = 0.9;
         break;
+    case PPCA_POWER_SEQ:
+        p->eps = 1e-6;
+        break;
     default:
         return fail(PPCA_ERR_INVALID, "unknown method %d", (int)method);
     }
@@ -420,7 +450,7 @@ static ppca_status check_m(const ppca_handle* h, int32_t m) {
 
 ppca_status ppca_prime(ppca_handle* h, ppca_method method, int32_t m, int64_t T, const ppca_prime_params* p) {
     if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
-    if (method != PPCA_POWER && method != PPCA_OJA && method != PPCA_EIGENGAME)
+    if (method != PPCA_POWER && method != PPCA_OJA && method != PPCA_EIGENGAME && method != PPCA_POWER_SEQ)
         return fail(PPCA_ERR_INVALID, "unknown method %d", (int)method);
     PPCA_TRY(check_m(h, m));
     if (T < 0) return fail(PPCA_ERR_INVALID, "T = %lld < 0", (long long)T);
@@ -433,7 +463,8 @@ ppca_status ppca_prime(ppca_handle* h, ppca_method method, int32_t m, int64_t T,
     if (prm.reserved != 0) return fail(PPCA_ERR_INVALID, "reserved field must be 0");
     if (prm.precision < PPCA_PREC_AUTO || prm.precision > PPCA_PREC_ACCURATE)
         return fail(PPCA_ERR_INVALID, "unknown precision %d", prm.precision);
-    if (method != PPCA_POWER) {
+    if (method == PPCA_POWER_SEQ && !(prm.eps >= 0.0)) return fail(PPCA_ERR_INVALID, "eps must be >= 0");
+    if (method == PPCA_OJA || method == PPCA_EIGENGAME) {
         if (prm.batch <= 0) return fail(PPCA_ERR_INVALID, "batch = %lld must be > 0", (long long)prm.batch);
         if (!(prm.lr > 0.0)) return fail(PPCA_ERR_INVALID, "lr must be > 0");
         if (method == PPCA_OJA && !(prm.lr_offset + (double)prm.t0 > 0.0))
@@ -461,6 +492,8 @@ ppca_status ppca_prime(ppca_handle* h, ppca_method method, int32_t m, int64_t T,
 ppca_status ppca_prime_continue(ppca_handle* h, int64_t T) {
     if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
     if (h->method < 0) return fail(PPCA_ERR_STATE, "ppca_prime was not called");
+    if (h->method == PPCA_POWER_SEQ)
+        return fail(PPCA_ERR_UNSUPPORTED, "the sequential power method runs each direction to completion");
     if (T < 0) return fail(PPCA_ERR_INVALID, "T < 0");
     return run_steps(h, T);
 }
@@ -620,7 +653,7 @@ ppca_status ppca_get_state(ppca_handle* h, void* buf, int64_t* bytes) {
                                    (long long)need);
     StateHeader hd{};
     hd.magic = kStateMagic;
-    hd.version = 1;
+    hd.version = 2;                  // 2: the prime parameters carry eps
     hd.n = h->x.n;
     hd.d = h->x.d;
     hd.method = h->method;
@@ -643,7 +676,7 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
     if (bytes < (int64_t)sizeof(StateHeader)) return fail(PPCA_ERR_INVALID, "state buffer too small");
     StateHeader hd;
     std::memcpy(&hd, buf, sizeof hd);
-    if (hd.magic != kStateMagic || hd.version != 1) return fail(PPCA_ERR_INVALID, "not a ppca state buffer");
+    if (hd.magic != kStateMagic || hd.version != 2) return fail(PPCA_ERR_INVALID, "not a ppca state buffer");
     if (hd.n != h->x.n || hd.d != h->x.d) return fail(PPCA_ERR_INVALID, "state is for another (n, d)");
     PPCA_TRY(check_m(h, hd.m));
     const size_t dm = (size_t)h->x.d * hd.m * sizeof(float);

@@ -56,6 +56,12 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
 cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, const double* w, int k,
                             double inv_n, float* E, double* lambda, cudaStream_t st);
 
+// One step of the sequential power method for direction j of V (d x m
+// column-major FP32): y <- y - V_<j (V_<j^T y) twice, x_new = y / |y|,
+// *diff = |x_new - V[:, j]|, V[:, j] = x_new (FP64 arithmetic; y is modified).
+// A zero y leaves V[:, j] and reports diff 0.
+cudaError_t power_seq_update(float* V, int64_t d, int j, float* y, double* diff, cudaStream_t st);
+
 // First rows of the kept 128-row blocks of an n-row matrix (ascending), by
 // sample_block_kept; forced >= 0: keep that block alone (no block passed).
 cudaError_t sample_blocks(int64_t n, double fraction, uint64_t seed, int64_t forced, int* tile_rows,

@@ -1229,6 +1229,75 @@ cudaError_t eigh_small_noalloc(const double* G, int m, double* w, double* U, int
 
 namespace {
 
+// One step of the sequential power method, in one CTA (the method is meant for
+// the small-scale protocol; every step reads one number back anyway).
+constexpr int kSeqThreads = 1024;
+
+__device__ double seq_block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kSeqThreads / 32; ++w) s += red[w];
+        red[32] = s;
+    }
+    __syncthreads();
+    const double s = red[32];
+    __syncthreads();
+    return s;
+}
+
+__global__ void __launch_bounds__(kSeqThreads) power_seq_kernel(float* __restrict__ V, int64_t d, int j,
+                                                               float* __restrict__ y, double* __restrict__ diff) {
+    __shared__ double red[33];
+    __shared__ double cs[kMaxM];
+    for (int pass = 0; pass < 2; ++pass) {             // classical Gram-Schmidt, twice
+        for (int i = 0; i < j; ++i) {
+            double p = 0.0;
+            for (int64_t r = threadIdx.x; r < d; r += kSeqThreads) p += (double)V[(int64_t)i * d + r] * (double)y[r];
+            const double c = seq_block_sum(p, red);
+            if (threadIdx.x == 0) cs[i] = c;
+        }
+        __syncthreads();
+        for (int64_t r = threadIdx.x; r < d; r += kSeqThreads) {
+            double yr = (double)y[r];
+            for (int i = 0; i < j; ++i) yr -= cs[i] * (double)V[(int64_t)i * d + r];
+            y[r] = (float)yr;
+        }
+        __syncthreads();
+    }
+    double nn = 0.0;
+    for (int64_t r = threadIdx.x; r < d; r += kSeqThreads) nn += (double)y[r] * (double)y[r];
+    nn = seq_block_sum(nn, red);
+    if (!(nn > 0.0)) {                                  // nothing left in the complement
+        if (threadIdx.x == 0) *diff = 0.0;
+        return;
+    }
+    const double inv = 1.0 / sqrt(nn);
+    float* x = V + (int64_t)j * d;
+    double dd = 0.0;
+    for (int64_t r = threadIdx.x; r < d; r += kSeqThreads) {
+        const double e = (double)y[r] * inv - (double)x[r];
+        dd += e * e;
+    }
+    dd = seq_block_sum(dd, red);
+    for (int64_t r = threadIdx.x; r < d; r += kSeqThreads) x[r] = (float)((double)y[r] * inv);
+    if (threadIdx.x == 0) *diff = sqrt(dd);
+}
+
+}  // namespace
+
+cudaError_t power_seq_update(float* V, int64_t d, int j, float* y, double* diff, cudaStream_t st) {
+    if (j < 0 || j >= kMaxM) return cudaErrorInvalidValue;
+    note_launch();
+    power_seq_kernel<<<1, kSeqThreads, 0, st>>>(V, d, j, y, diff);
+    return cudaGetLastError();
+}
+
+namespace {
+
 // One CTA walks the blocks in chunks of its size; a block-wide exclusive scan
 // of the keep flags gives each kept block its position, so the list comes out
 // in ascending order.

@@ -67,6 +67,18 @@ def exact_spectrum_data(n: int, d: int, sigma, seed: int):
     return X, Q
 
 
+def paper_synthetic_spectrum(kind: str, d: int = 50, top: float = 1000.0, bottom: float = 1.0) -> np.ndarray:
+    """The covariance spectra of the paper's synthetic small-scale data (Section 5):
+    d = 50 eigenvalues decaying exponentially ("exponential") or linearly
+    ("linear") over three orders of magnitude, from 1000 to 1."""
+    t = np.arange(d) / (d - 1)
+    if kind == "exponential":
+        return top * (bottom / top) ** t
+    if kind == "linear":
+        return top + (bottom - top) * t
+    raise ValueError(kind)
+
+
 def initial_basis(d: int, m: int, seed: int) -> np.ndarray:
     """Gaussian d x m starting basis (float64)."""
     rng = np.random.default_rng(seed + 7919)

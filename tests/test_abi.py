@@ -43,6 +43,7 @@ def test_version_and_defaults(lib):
     assert oja.batch == 256 and oja.lr == 1.0 and oja.lr_offset == 100.0
     eg = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
     assert eg.batch == 1024 and eg.momentum == 0.9
+    assert P.ppca_prime_params_default(P.PPCA_POWER_SEQ).eps == 1e-6
     with pytest.raises(P.PPCAError) as ei:
         P.ppca_prime_params_default(7)
     assert ei.value.status_name == "PPCA_ERR_INVALID"
