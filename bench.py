@@ -46,6 +46,10 @@ def parse_args(argv=None):
     ap.add_argument("--tune-eg-lr", action="store_true",
                     help="run the EigenGame learning-rate grid of the workload and print the choice")
     ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--runs", type=int, default=10, help="paper_synthetic: runs per method")
+    ap.add_argument("--eg-steps", type=int, default=3000, help="paper_synthetic: EigenGame step budget")
+    ap.add_argument("--oja-steps", type=int, default=500, help="paper_synthetic: Oja step budget")
+    ap.add_argument("--power-cap", type=int, default=5000, help="paper_synthetic: power steps per direction")
     ap.add_argument("--rows", type=int, default=0,
                     help="override n with a smaller row count (for profiler captures of a small case)")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
@@ -527,6 +531,150 @@ def run_large_d(args):
         print(json.dumps(line))
 
 
+def run_paper_synthetic(args):
+    """The paper's small-scale synthetic protocol (Section 5 and its Table 2): 5000 x 50
+    data whose spectrum decays exponentially or linearly from 1000 to 1, k = 16, minibatch
+    1000.  EigenGame (rates 1 .. 1e-6) and Oja (constant rates 1e-3 .. 1e-6): the rate with
+    the least angle error summed over runs, checkpoints and components is kept; then the
+    primer alone and pPCA_l on top of it (l = 0, 2, 4 extra components) run `runs` times
+    each from different V0, evaluated at checkpoints.  The power method one direction at a
+    time (eps 1e-3 .. 1e-7, the eps with the least summed error kept), alone and with
+    pPCA_0.  Reported per method and threshold V: the device time of the priming up to the
+    first checkpoint whose result has its 16 leading directions within V of the truth, plus
+    one pPCA step where it is used; mean and standard deviation over the runs, or n.a. when
+    a run never got there.  The truth is the FP64 eigendecomposition of X^T X (torch)."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    torch.cuda.set_device(0)
+    n, d, k, b = 5000, 50, 16, 1000
+    runs = args.runs
+    thresholds = {"pi/8": math.pi / 8, "pi/32": math.pi / 32, "pi/128": math.pi / 128}
+    stream = torch.cuda.current_stream()
+    acc = P.PPCA_PREC_ACCURATE
+    plans = {"eigengame": (P.PPCA_EIGENGAME, [10.0 ** -i for i in range(7)], args.eg_steps, 25),
+             "oja": (P.PPCA_OJA, [10.0 ** -i for i in range(3, 7)], args.oja_steps, 5)}
+    out = {}
+    for spec in ("exponential", "linear"):
+        X, _ = synth.gaussian_data(n, d, synth.paper_synthetic_spectrum(spec, d), seed=5000 + (spec == "linear"))
+        Xbuf = torch.zeros((n, 52), dtype=torch.float32, device="cuda")   # 16-byte row pitch
+        Xbuf[:, :d] = torch.from_numpy(X.astype(np.float32)).cuda()
+        Xv = Xbuf[:, :d]
+        w, U = torch.linalg.eigh(Xv.double().T @ Xv.double())
+        Et = U.flip(1)[:, :k].contiguous()
+        h = P.ppca_create(Xv, stream=stream)
+        E = torch.empty((k, d), dtype=torch.float32, device="cuda")
+        lam = torch.empty(k, dtype=torch.float64, device="cuda")
+        Vb = torch.empty((k + 4, d), dtype=torch.float32, device="cuda")
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def v0(m, run):
+            return torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, 100 + run).T,
+                                                         dtype=np.float32)).cuda()
+
+        def angles_now(m, with_pca):
+            if with_pca:
+                P.ppca_finalize(h, k, E, lam, acc)
+                P.ppca_sync(h)
+                return lces_of(E, Et, 1.0)[1]
+            P.ppca_get_basis(h, Vb[:m])
+            P.ppca_sync(h)
+            return lces_of(Vb[:k], Et, 1.0)[1]
+
+        def finalize_ms(m):
+            return _events_ms(lambda: P.ppca_finalize(h, k, E, lam, acc), 5, stream)
+
+        def trajectory(method, m, prm, steps, every, run, with_pca):
+            P.ppca_prime(h, method, m, 0, prm, V0=v0(m, run))
+            cum, traj = 0.0, []
+            for _ in range(steps // every):
+                ev0.record(stream)
+                P.ppca_prime_continue(h, every)
+                ev1.record(stream)
+                ev1.synchronize()
+                cum += ev0.elapsed_time(ev1)
+                traj.append((cum, angles_now(m, with_pca)))
+            return traj
+
+        def first_time(traj, tol, extra):
+            for cum, ang in traj:
+                if np.all(ang < tol):
+                    return cum + extra
+            return None
+
+        def summarise(times_by_run):
+            res = {}
+            for name, tol in thresholds.items():
+                ts = [t[name] for t in times_by_run]
+                res[name] = "n.a." if any(t is None for t in ts) else \
+                    {"mean_ms": round(float(np.mean(ts)), 3), "std_ms": round(float(np.std(ts)), 3)}
+            return res
+
+        spec_out = {}
+        for label, (method, grid, steps, every) in plans.items():
+            def params(rate):
+                prm = P.ppca_prime_params_default(method)
+                prm.batch, prm.precision = b, acc
+                if method == P.PPCA_OJA:                   # constant rate: lr / (t + L) with L huge
+                    prm.lr, prm.lr_offset = rate * 1e12, 1e12
+                else:
+                    prm.lr = rate
+                return prm
+            scores = {}
+            for rate in grid:
+                tot = 0.0
+                for run in range(runs):
+                    for _, ang in trajectory(method, k, params(rate), steps, every, run, False):
+                        tot += float(np.sum(ang))
+                scores[rate] = tot if np.isfinite(tot) else float("inf")
+            best = min(scores, key=lambda r: scores[r])
+            entry = {"rate": best, "steps": steps, "checkpoint_every": every}
+            for l in (None, 0, 2, 4):
+                m = k + (l or 0)
+                fin = finalize_ms(m) if l is not None else 0.0
+                per_run = []
+                for run in range(runs):
+                    traj = trajectory(method, m, params(best), steps, every, run, l is not None)
+                    per_run.append({nm: first_time(traj, tol, fin) for nm, tol in thresholds.items()})
+                entry["primer" if l is None else f"pPCA_{l}"] = summarise(per_run)
+            spec_out[label] = entry
+        # the power method, one direction at a time, with eps termination
+        scores, finals = {}, {}
+        for eps in [10.0 ** -i for i in range(3, 8)]:
+            prm = P.ppca_prime_params_default(P.PPCA_POWER_SEQ)
+            prm.eps, prm.precision = eps, acc
+            tot, rec = 0.0, []
+            for run in range(runs):
+                ev0.record(stream)
+                P.ppca_prime(h, P.PPCA_POWER_SEQ, k, args.power_cap, prm, V0=v0(k, run))
+                ev1.record(stream)
+                ev1.synchronize()
+                t = ev0.elapsed_time(ev1)
+                own = angles_now(k, False)
+                pca = angles_now(k, True)
+                tot += float(np.sum(own))
+                rec.append((t, own, pca))
+            scores[eps], finals[eps] = tot, rec
+        best = min(scores, key=lambda e: scores[e])
+        fin = finalize_ms(k)
+        own_runs = [{nm: (t if np.all(o < tol) else None) for nm, tol in thresholds.items()} for t, o, _ in finals[best]]
+        pca_runs = [{nm: (t + fin if np.all(p_ < tol) else None) for nm, tol in thresholds.items()}
+                    for t, _, p_ in finals[best]]
+        spec_out["power"] = {"eps": best, "primer": summarise(own_runs), "pPCA_0": summarise(pca_runs)}
+        out[spec] = spec_out
+        del h
+    line = {"metric": "time to an eigenvector streak of 16 (paper's small-scale synthetic protocol)",
+            "unit": "ms (device)", "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "paper_synthetic_5000x50", "n": n, "d": d, "k": k, "batch": b, "runs": runs,
+                       "precision": "FP32 data, split-precision passes"},
+            "results": out}
+    print(json.dumps(line))
+
+
 def tune_eg_lr(args):
     """The paper's learning-rate protocol for EigenGame (Section 5): run the workload's
     EigenGame priming for every lr in {1, 1e-1, ..., 1e-6}, follow it by the pPCA step and
@@ -854,6 +1002,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload.startswith("largeD"):
         run_large_d(args)
+    elif args.workload == "paper_synthetic":
+        run_paper_synthetic(args)
     else:
         run_ours(args)
 
