@@ -17,6 +17,7 @@
 
 #include "kernels.h"
 #include "pass_tc.h"
+#include "tc_host.h"
 
 using namespace ppca;
 
@@ -258,10 +259,20 @@ ppca_status run_gram(ppca_handle* h, const XView& x, const float* Q, int m, int6
 ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     const int64_t d = h->x.d;
     const float* src = V;
+    // Tall bases (d >= 16384): Gram matrices on the tensor cores (three BF16
+    // pieces, ~2^-24), which the FP32 factorisation cannot tell from exact; the
+    // double-float fallback then recomputes its Gram in double-float (gated on
+    // the rejection flag).  Shorter bases: the CUDA-core double-float Gram, whose
+    // time (~36 us at 4096 x 128) is below the tensor-core path's fixed cost.
+    const bool tc_gram = d >= 16384 && encode_fn() != nullptr && h->sched.engine != 2;
     for (int rep = 0; rep < 2; ++rep) {
         float* dst = rep == 0 ? h->T : Q;
-        CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream, h->Gf));
-        CUDA_TRY(cholesky_adaptive(h->G, h->Gf, m, h->Rf, rep == 0, h->status + 1, h->status, h->stream));
+        if (tc_gram)
+            CUDA_TRY(gram_tc(src, d, m, h->G, h->Gf, h->tc, h->status, h->num_sms, h->stream));
+        else
+            CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream, h->Gf));
+        CUDA_TRY(cholesky_adaptive(h->G, h->Gf, m, h->Rf, rep == 0, h->status + 1, h->status, h->stream,
+                                   tc_gram ? src : nullptr, d, h->gram_part));
         CUDA_TRY(apply_rinv(src, h->Rf, d, m, dst, h->stream));
         src = dst;
     }

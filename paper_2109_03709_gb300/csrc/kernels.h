@@ -27,17 +27,22 @@ cudaError_t xpass_simt(const XView& x, const float* V, int m, int64_t r0, int64_
 // ---- small dense kernels (small.cu) -------------------------------------------
 // G = A^T B in double-float accumulation, A, B d x m column-major FP32,
 // G m x m row-major FP64 (the rounded hi + lo pair) and, when Gf is given, its
-// FP32 rounding.  part: scratch of gram_part_floats(d, m) floats.
+// FP32 rounding.  part: scratch of gram_part_floats(d, m) floats.  run_if:
+// device flag or NULL; when given, both kernels do nothing while *run_if == 0.
 size_t gram_part_floats(int64_t d, int m);
 cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st,
-                    float* Gf = nullptr);
+                    float* Gf = nullptr, const int* run_if = nullptr);
 
 // Cholesky G = R^T R (one CTA), writing X = R^-1 (upper, row-major FP32) to Rinv.
 // FP32 blocked Cholesky of the diagonally scaled G (+ inverse), Rinv = R^-1.  With
 // may_fall_back, a failed or ill-conditioned attempt sets *flag and the
 // double-float Cholesky (launched right after, a no-op when *flag == 0) redoes it.
-cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
-                              int* status, cudaStream_t st);
+// Zdf: when G did not come from gram_df (tensor-core Gram), the d x m matrix
+// whose double-float Gram the fallback recomputes into G first (gated by *flag,
+// part as for gram_df); NULL otherwise.
+cudaError_t cholesky_adaptive(double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
+                              int* status, cudaStream_t st, const float* Zdf = nullptr, int64_t d = 0,
+                              float* part = nullptr);
 // Q = V R^-1 as a product with the triangular inverse; Q must not alias V.
 cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st);
 

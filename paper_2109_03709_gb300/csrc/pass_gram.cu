@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
 
 // G[i][j] = (sum_p part_p[i][j] + sum_p part_p[j][i]) / 2 in FP64.
 __global__ void gram_parts_reduce_kernel(const float2* __restrict__ Gpart, int nparts, int m, int m_pad,
-                                         double* __restrict__ G) {
+                                         double* __restrict__ G, float* __restrict__ Gf) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= m * m) return;
     const int i = e / m, j = e % m;
@@ -476,6 +476,7 @@ __global__ void gram_parts_reduce_kernel(const float2* __restrict__ Gpart, int n
         s += ((double)a.x + (double)a.y) + ((double)b.x + (double)b.y);
     }
     G[e] = 0.5 * s;
+    if (Gf) Gf[e] = (float)(0.5 * s);
 }
 
 template <int NX, int NV, bool F32X>
@@ -553,7 +554,7 @@ cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     note_launch();
-    gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G);
+    gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G, nullptr);
     return cudaGetLastError();
 }
 
@@ -569,6 +570,37 @@ cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, cons
                                      ppca_precision prec, int flush, const TcPassScratch& sc, int* status,
                                      int num_sms, cudaStream_t st) {
     return projected_gram_impl(x, Q, m, 0, x.n, tile_row, nsel, G, prec, flush, sc, status, num_sms, st);
+}
+
+// G = Z^T Z for a d x m column-major FP32 Z (CholeskyQR's Gram matrix) on the
+// tensor cores: Z is split into three BF16 pieces (the layout of the projected
+// Gram's Y pieces, K = d), G = sum over the six piece products with a + b <= 2,
+// flushed into double-float partials every K-stage, summed and symmetrised in
+// FP64; Gf receives the FP32 rounding of G.
+cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, const TcPassScratch& sc, int* status,
+                    int num_sms, cudaStream_t st) {
+    if (m < 1 || m > 128 || d < 1) return cudaErrorInvalidValue;
+    const int m_pad = (int)rup(m, 32);
+    const int64_t ldv = rup(d, 8);
+    __nv_bfloat16* Zp = static_cast<__nv_bfloat16*>(sc.vp);
+    cudaError_t e = launch_split_v(Z, d, m, m_pad, ldv, 3, Zp, st);
+    if (e != cudaSuccess) return e;
+    CUtensorMap tmY;
+    if (!encode_bf16_2d(&tmY, Zp, (uint64_t)d, 3ull * m_pad, ldv * 2, 64, m_pad)) return cudaErrorInvalidValue;
+    const int kst = (int)((d + kGBK - 1) / kGBK);
+    const int grid = kst < num_sms ? kst : num_sms;
+    const int gstages = 4;
+    const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
+    e = cudaFuncSetAttribute(gram_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    float2* parts = static_cast<float2*>(sc.zacc);
+    note_launch();
+    gram_y_kernel<<<grid, kGThreadsBf16, smem, st>>>(tmY, kst, 1, m_pad, gstages, parts, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launch();
+    gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G, Gf);
+    return cudaGetLastError();
 }
 
 }  // namespace ppca

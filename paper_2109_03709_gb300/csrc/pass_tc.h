@@ -35,6 +35,11 @@ bool tc_pass_supported(const XView& x, int m);
 cudaError_t projected_gram_tc(const XView& x, const float* Q, int m, int64_t r0, int64_t r1, double* G,
                               ppca_precision prec, int flush, const TcPassScratch& s, int* status, int num_sms,
                               cudaStream_t st);
+// G = Z^T Z (m x m FP64, and its FP32 rounding in Gf) for Z d x m column-major
+// FP32 on the tensor cores: three BF16 pieces of Z, six piece products, about
+// 2^-24 relative to |z_i| |z_j|.  Uses s.vp and s.zacc.
+cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, const TcPassScratch& s, int* status,
+                    int num_sms, cudaStream_t st);
 // The same over the nsel 128-row blocks of X whose first rows are listed in
 // tile_row (device array, rows < n; a block past row n - 1 reads zeros).
 cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, const int* tile_row, int nsel, double* G,

@@ -40,7 +40,8 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 }
 
 __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t d, int m,
-                               float* __restrict__ part, int64_t slice_rows) {
+                               float* __restrict__ part, int64_t slice_rows, const int* run_if) {
+    if (run_if && *run_if == 0) return;       // only needed when the FP32 factorisation was rejected
     __shared__ float As[32][kGramTile + 1];
     __shared__ float Bs[32][kGramTile + 1];
     const int ti = blockIdx.x, tj = blockIdx.y, p = blockIdx.z;
@@ -102,7 +103,8 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
 }
 
 __global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, bool sym, double* __restrict__ G,
-                                   float* __restrict__ Gf) {
+                                   float* __restrict__ Gf, const int* run_if) {
+    if (run_if && *run_if == 0) return;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * m) return;
     const int i = idx / m, j = idx % m;
@@ -1105,19 +1107,19 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 size_t gram_part_floats(int64_t d, int m) { return (size_t)gram_nslices(d) * m * m * 2; }
 
 cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st,
-                    float* Gf) {
+                    float* Gf, const int* run_if) {
     const int P = gram_nslices(d);
     const int64_t slice = (d + P - 1) / P;
     const int T = (m + kGramTile - 1) / kGramTile;
     note_launch();
-    gram_df_kernel<<<dim3(T, T, P), 256, 0, st>>>(A, B, d, m, part, slice);
+    gram_df_kernel<<<dim3(T, T, P), 256, 0, st>>>(A, B, d, m, part, slice, run_if);
     note_launch();
-    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G, Gf);
+    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G, Gf, run_if);
     return cudaGetLastError();
 }
 
-cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
-                              int* status, cudaStream_t st) {
+cudaError_t cholesky_adaptive(double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
+                              int* status, cudaStream_t st, const float* Zdf, int64_t d, float* part) {
     const size_t lda = (size_t)((m + 3) & ~3);
     const size_t smem = ((size_t)2 * m * lda + (size_t)((m + kCB - 1) / kCB) * kCB * kCB + m) * sizeof(float);
     cudaError_t e = allow_smem(chol_blocked_kernel, smem);
@@ -1127,6 +1129,10 @@ cudaError_t cholesky_adaptive(const double* G, const float* Gf, int m, float* Ri
                                                       may_fall_back ? 0 : 1);
     e = cudaGetLastError();
     if (e != cudaSuccess || !may_fall_back) return e;
+    if (Zdf) {       // G came from the tensor cores: the fallback needs the double-float Gram
+        e = gram_df(Zdf, Zdf, d, m, G, part, st, nullptr, flag);
+        if (e != cudaSuccess) return e;
+    }
     const size_t smem_df = (size_t)3 * m * m * sizeof(float);
     e = allow_smem(cholesky_kernel<true>, smem_df);
     if (e != cudaSuccess) return e;

@@ -205,6 +205,28 @@ def test_cholesky_qr2_matches_thin_qr(P, d, m):
     assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-5
 
 
+@pytest.mark.parametrize("kappa", [10.0, 1e3, 1e5])
+def test_cholesky_qr2_tall_basis_tensor_core_gram(P, kappa):
+    """d >= 16384: the Gram matrices come from the tensor cores (three BF16
+    pieces); at kappa = 1e5 the FP32 factorisation is rejected and the
+    double-float fallback recomputes its Gram in double-float."""
+    d, m = 20000, 48
+    rng = np.random.default_rng(int(kappa))
+    U, _ = np.linalg.qr(rng.standard_normal((d, m)))
+    W, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    V = (U * np.logspace(0, -np.log10(kappa), m)[None, :]) @ W.T
+    Vd = dev_basis(V)
+    Qd = empty_basis(d, m)
+    h = P.ppca_create(dev_matrix(np.zeros((2, d)), "f32"))
+    P.ppca_orthonormalize(h, Vd, Qd, m)
+    P.ppca_sync(h)
+    Q = host_basis(Qd)
+    assert np.abs(Q.T @ Q - np.eye(m)).max() <= 1e-5
+    assert oracle.principal_angles(Q, host_basis(Vd)).max() <= kappa * 1e-7 + 1e-5
+    if kappa <= 1e3:
+        assert np.abs(Q - oracle.orth(host_basis(Vd))).max() <= kappa * 1e-6
+
+
 def test_cholesky_qr2_ill_conditioned(P):
     d, m = 512, 32
     rng = np.random.default_rng(1)
