@@ -262,8 +262,8 @@ ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     // Tall bases (d >= 16384): Gram matrices on the tensor cores (three BF16
     // pieces, ~2^-24), which the FP32 factorisation cannot tell from exact; the
     // double-float fallback then recomputes its Gram in double-float (gated on
-    // the rejection flag).  Shorter bases: the CUDA-core double-float Gram, whose
-    // time (~36 us at 4096 x 128) is below the tensor-core path's fixed cost.
+    // the rejection flag).  Shorter bases: the CUDA-core double-float Gram (the
+    // two break even near d = 4096; at 262144 x 64 the tensor cores halve CholeskyQR2).
     const bool tc_gram = d >= 16384 && encode_fn() != nullptr && h->sched.engine != 2;
     for (int rep = 0; rep < 2; ++rep) {
         float* dst = rep == 0 ? h->T : Q;

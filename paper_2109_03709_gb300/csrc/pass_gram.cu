@@ -588,7 +588,11 @@ cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, cons
     CUtensorMap tmY;
     if (!encode_bf16_2d(&tmY, Zp, (uint64_t)d, 3ull * m_pad, ldv * 2, 64, m_pad)) return cudaErrorInvalidValue;
     const int kst = (int)((d + kGBK - 1) / kGBK);
-    const int grid = kst < num_sms ? kst : num_sms;
+    // eight K-stages per CTA: fewer double-float partials (m_pad^2 x 8 B each) to
+    // write and sum; measured best of 1-16 at d = 16384 and 262144
+    int grid = kst / 8;
+    if (grid > num_sms) grid = num_sms;
+    if (grid < 1) grid = 1;
     const int gstages = 4;
     const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
     e = cudaFuncSetAttribute(gram_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
