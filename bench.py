@@ -45,7 +45,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-lces", action="store_true", help="skip the time-to-LCES comparison")
     ap.add_argument("--tune-eg-lr", action="store_true",
                     help="run the EigenGame learning-rate grid of the workload and print the choice")
-    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--runs", type=int, default=10, help="paper_synthetic: runs per method")
     ap.add_argument("--eg-steps", type=int, default=3000, help="paper_synthetic: EigenGame step budget")
     ap.add_argument("--oja-steps", type=int, default=500, help="paper_synthetic: Oja step budget")
@@ -63,6 +63,22 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks of the process group (x itself without one): the
+    job's time is its slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(bytes_per_rank: float, seconds: float, ws: int) -> float:
+    """GB/s of the whole job: the bytes every rank streamed over the slowest rank's time."""
+    return bytes_per_rank * ws / seconds / 1e9
 
 
 def measured_peaks():
@@ -842,13 +858,9 @@ def run_ours(args):
     tm = P.ppca_get_timing(h)
     P.ppca_set_timing(h, False)
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms_max / args.steps
-    value = bytes_per_step * args.steps * ws / (ms_max / 1e3) / 1e9
+    value = whole_job_rate(bytes_per_step * args.steps, ms_max / 1e3, ws)
 
     # roofline of the dominant kernel: the fused X-pass, as timed by the library's events
     peaks, peak_kind = measured_peaks()
@@ -897,12 +909,8 @@ def run_ours(args):
             e2e_step(i)
         for hb in hs:
             P.ppca_sync(hb)
-        dt = (time.perf_counter() - t0) / args.e2e_steps
-        if dist:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": round(bytes_per_step * ws / dt / 1e9, 1), "unit": "GB/s",
+        dt = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, dist, "cuda")
+        e2e = {"value": round(whole_job_rate(bytes_per_step, dt, ws), 1), "unit": "GB/s",
                "h2d_bytes_per_step": bytes_per_pass, "d2h_bytes_per_step": k * d * 4 + k * 8,
                "ms_per_step": round(dt * 1e3, 3), "steps": args.e2e_steps,
                "form": "ppca_upload + ppca_prime + ppca_finalize_host on two handles and streams; "
