@@ -473,8 +473,14 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
                     widen16(raw, lo, hi);
                     uint8_t* arow = st + raw_bytes + (q >> 2) * 8192 + r * 128;
                     const int c = 2 * (q & 3);
-                    *reinterpret_cast<uint4*>(arow + ((c ^ (r & 7)) << 4)) = lo;
-                    *reinterpret_cast<uint4*>(arow + (((c + 1) ^ (r & 7)) << 4)) = hi;
+                    // lanes q and q + 4 write the same row of the two boxes (8 KB apart, the
+                    // same banks): the second box stores its odd chunk first, so the eight
+                    // lanes of each 16-byte store phase touch eight different chunks
+                    // (selects, not a branch: each store stays one instruction for the warp)
+                    const bool first_box = q < 4;
+                    const int c1 = first_box ? c : c + 1, c2 = first_box ? c + 1 : c;
+                    *reinterpret_cast<uint4*>(arow + ((c1 ^ (r & 7)) << 4)) = first_box ? lo : hi;
+                    *reinterpret_cast<uint4*>(arow + ((c2 ^ (r & 7)) << 4)) = first_box ? hi : lo;
                 }
                 tc::fence_proxy_async_shared();
                 tc::mbar_arrive(&hd->xform[st_i]);
@@ -1370,6 +1376,29 @@ cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int6
     return cudaGetLastError();
 }
 
+// Row groups of the Z = X^T Y kernels, whose tasks are (128-column slice, row
+// group) and whose CTAs each run whole tasks: Sg minimises a CTA's share,
+// ceil(Dt Sg / num_sms) / Sg, within kst (a K-stage per group at least) and the
+// capacity of the double-float partials (Dt * 128 * m_pad float2 per group);
+// the smallest such Sg.  (Dt = 32 on 152 SMs: 9 groups, 2 tasks per CTA, not 4
+// groups on 128 CTAs.)
+int choose_row_groups(int Dt, int kst, int num_sms, size_t z_bytes, int m_pad) {
+    const size_t per_group = (size_t)Dt * 128 * (size_t)m_pad * 8;
+    int cap = (int)std::min<size_t>(z_bytes / per_group, (size_t)std::max(kst, 1));
+    if (cap < 1) cap = 1;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int sg = 1; sg <= cap && sg <= 4 * num_sms; ++sg) {
+        const int64_t ntask = (int64_t)Dt * sg;
+        const double cost = (double)((ntask + num_sms - 1) / num_sms) / sg;
+        if (cost < best_cost * (1.0 - 1e-9)) {
+            best_cost = cost;
+            best = sg;
+        }
+    }
+    return best;
+}
+
 cudaError_t launch_zreduce(const float* Zacc, int Sg, int Dt, int64_t d, int m, int m_pad, float* Z, cudaStream_t st) {
     const int64_t total = d * m;
     int blocks = (int)((total + 255) / 256);
@@ -1429,9 +1458,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         e = cudaFuncSetAttribute(xty_tc_kernel<S, FP8X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int kst = (int)(ps.ldy / kBK);
-        Sg = ps.Dt >= num_sms ? 1 : num_sms / ps.Dt;
-        if (Sg > kst) Sg = kst;
-        if (Sg < 1) Sg = 1;
+        Sg = choose_row_groups(ps.Dt, kst, num_sms, sc.z_bytes, ps.m_pad);
         const int ntask = ps.Dt * Sg;
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
@@ -1563,9 +1590,7 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         e = cudaFuncSetAttribute(xty_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         const int kst = (int)(ldy / kBK32);
-        Sg = Dt >= num_sms ? 1 : num_sms / Dt;
-        if (Sg > kst) Sg = kst;
-        if (Sg < 1) Sg = 1;
+        Sg = choose_row_groups(Dt, kst, num_sms, sc.z_bytes, m_pad);
         const int ntask = Dt * Sg;
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
