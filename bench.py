@@ -147,8 +147,9 @@ class ClockSampler:
 
 # --------------------------------------------------------------------------- CPU leg (oracle)
 
-def cpu_leg(workload: str, rows: int, passes: int):
-    """The FP64 oracle's power pass on a bounded row sample of the workload (run in a subprocess)."""
+def cpu_leg(workload: str, rows: int, passes: int, warmup: int = 0):
+    """The FP64 oracle's power pass on a bounded row sample of the workload (run in a subprocess,
+    with the BLAS thread counts set to every host core)."""
     import numpy as np
 
     import oracle
@@ -160,6 +161,8 @@ def cpu_leg(workload: str, rows: int, passes: int):
         import torch
         X = torch.from_numpy(X).to(torch.bfloat16).double().numpy()
     Q = oracle.orth(synth.initial_basis(d, m, cfg.seed))
+    for _ in range(warmup):
+        oracle.power_step(X, Q)
     t0 = time.perf_counter()
     for _ in range(passes):
         Q = oracle.power_step(X, Q)
@@ -168,14 +171,14 @@ def cpu_leg(workload: str, rows: int, passes: int):
     print(json.dumps({"gbs": gbs, "seconds": dt, "rows": rows, "passes": passes}))
 
 
-def run_cpu_leg(workload: str, rows: int, passes: int):
+def run_cpu_leg(workload: str, rows: int, passes: int, warmup: int = 0):
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[v] = str(cores)
     env["CUDA_VISIBLE_DEVICES"] = ""
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-leg", "--workload", workload,
-                        "--cpu-rows", str(rows), "--cpu-passes", str(passes)],
+                        "--cpu-rows", str(rows), "--cpu-passes", str(passes), "--warmup", str(warmup)],
                        capture_output=True, text=True, env=env, timeout=1800)
     if r.returncode != 0:
         return None, cores, r.stderr[-500:]
@@ -960,32 +963,21 @@ def run_ours(args):
 # --------------------------------------------------------------------------- reference arm (oracle)
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands, timed on the host cores (BLAS on every
+    core, in a subprocess like the main arm's CPU leg) on a bounded row sample of the workload;
+    one step = one oracle power pass (X^T X Q + MGS2) over the sample.  Rank 0 only."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    import numpy as np
-
-    import oracle
     import synth
     cfg = synth.CONFIGS[args.workload]
-    rows = 8192
-    X, _ = synth.gaussian_data(rows, cfg.d, cfg.lam(), cfg.seed)
-    if cfg.dtype == "bf16":
-        import torch
-        X = torch.from_numpy(X).to(torch.bfloat16).double().numpy()
-    Q0 = oracle.orth(synth.initial_basis(cfg.d, cfg.m, cfg.seed))
-
-    def step():
-        return oracle.power_step(X, Q0)
-
-    for _ in range(args.warmup):
-        step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        step()
-    dt = (time.perf_counter() - t0) / args.steps
+    rows = 32768
+    out, cores, err = run_cpu_leg(args.workload, rows, args.steps, args.warmup)
+    if out is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle leg failed: {err}"}))
+        return
+    dt = out["seconds"] / args.steps
     value = rows * cfg.d * BYTES[cfg.dtype] / dt / 1e9
-    cores = os.cpu_count() or 1
     line = {"impl": "reference", "metric": "X-pass HBM GB/s; time to LCES=k (BF16 vs FP32, same GPU, angle tol)",
             "value": round(value, 4), "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1000,7 +992,7 @@ def run_reference(args):
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_leg:
-        cpu_leg(args.workload, args.cpu_rows, args.cpu_passes)
+        cpu_leg(args.workload, args.cpu_rows, args.cpu_passes, args.warmup)
         return
     if args.tune_eg_lr:
         tune_eg_lr(args)
