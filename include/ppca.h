@@ -62,7 +62,7 @@ typedef enum ppca_status {
     PPCA_ERR_STATE = 4,       /* call out of order (e.g. finalize before prime)        */
     PPCA_ERR_NUMERICAL = 5,   /* device reported a breakdown (see ppca_sync)           */
     PPCA_ERR_TIMEOUT = 6,     /* a bounded device-side wait ran out (see ppca_sync)    */
-    PPCA_ERR_UNSUPPORTED = 7  /* valid request this build does not implement           */
+    PPCA_ERR_UNSUPPORTED = 7  /* valid request the library does not implement          */
 } ppca_status;
 
 /* Storage type of X. */

@@ -67,7 +67,7 @@ def build(verbose_ptxas: bool = False) -> str:
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= max(os.path.getmtime(o) for o in objs):
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    # static CUDA runtime; the driver entry points (TMA descriptors) are fetched
+    # static CUDA runtime; the CUDA driver API entry points (TMA descriptors) are fetched
     # at run time with cudaGetDriverEntryPoint, so libcuda is not a link dependency
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
