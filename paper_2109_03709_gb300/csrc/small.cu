@@ -428,15 +428,19 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
         if (tid == 0 && fallback) *fallback = 0;
         return;
     }
-    // Right-looking Cholesky G' = R^T R (R upper) with the upper triangle held in
-    // registers: the 4 x 4 blocks (bi <= bj) are dealt to the threads, one or two
-    // each.  Step k: every thread takes the pivot from shared memory; the owners
-    // of block row k/4 write row k of R (R_kk = sqrt(a_kk), R_kj = a_kj / R_kk)
-    // into A; after a barrier every thread applies a_ij -= R_ki R_kj to its
-    // blocks and the owner of the next diagonal entry publishes the next pivot.
-    // Two barriers per column, all 512 threads busy in each.
+    // Right-looking blocked Cholesky G' = R^T R (R upper) with the upper triangle
+    // held in registers: the 4 x 4 blocks (bi <= bj) are dealt to the threads, one
+    // or two each.  Block step kb: the owner of the diagonal block factors it
+    // alone (four pivots, in registers) and writes R_kk and 1 / diag(R_kk) to
+    // shared memory; after a barrier the owners of block row kb solve
+    // R_kb,j = R_kk^-T A_kb,j for their blocks and write them into A; after a
+    // second barrier every thread applies the rank-4 update A_ij -= R_kb,i^T R_kb,j
+    // to its blocks below block row kb, and the owner of the next diagonal block
+    // factors it right after its own update.  Two barriers per four columns.
+    // Rows at or past m (the padding of the last block) are never read or
+    // written; their R entries count as zero.
     {
-        __shared__ float sh_piv;
+        __shared__ float sh_rinv[4];
         const int nq = (m + 3) / 4;
         const int nblk = nq * (nq + 1) / 2;
         int bI[2], bJ[2];
@@ -463,53 +467,98 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
                     a[s2][u][v] = (bI[s2] >= 0 && ii < m && jj < m) ? A[ii * lda + jj] : 0.f;
                 }
         }
-        if (tid == 0) sh_piv = A[0];
         __syncthreads();                      // blocks loaded: A now receives the rows of R
-        for (int k = 0; k < m; ++k) {
-            float piv = sh_piv;
-            if (!(piv > 0.f)) {
-                piv = 1e-30f;
-                if (tid == 0) bad = 1;
+        // factor diagonal block kb in place (the caller owns it, slot s2) and publish it
+        auto factor_diag = [&](int s2, int kb) {
+            const int k0 = 4 * kb;
+            float rd[4][4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) rd[c][v] = 0.f;
+                float inv = 0.f;
+                if (k0 + c < m) {
+                    float piv = a[s2][c][c];
+                    if (!(piv > 0.f)) {
+                        piv = 1e-30f;
+                        bad = 1;
+                    }
+                    const float r = __fsqrt_rn(piv);
+                    inv = __frcp_rn(r);
+                    rd[c][c] = r;
+#pragma unroll
+                    for (int v = c + 1; v < 4; ++v) rd[c][v] = a[s2][c][v] * inv;
+#pragma unroll
+                    for (int u = c + 1; u < 4; ++u)
+#pragma unroll
+                        for (int v = u; v < 4; ++v) a[s2][u][v] = __fmaf_rn(-rd[c][u], rd[c][v], a[s2][u][v]);
+                }
+                sh_rinv[c] = inv;
             }
-            const float rkk = __fsqrt_rn(piv);
-            const float inv = __frcp_rn(rkk);
-            const int kb = k >> 2, ku = k & 3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (k0 + c < m) *reinterpret_cast<float4*>(A + (k0 + c) * lda + k0) =
+                                    make_float4(rd[c][0], rd[c][1], rd[c][2], rd[c][3]);
+        };
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+            if (bI[s2] == 0 && bJ[s2] == 0) factor_diag(s2, 0);
+        for (int kb = 0; kb < nq; ++kb) {
+            const int k0 = 4 * kb;
+            __syncthreads();                  // R_kk and its inverse diagonal are published
+            // block row kb: R_kb,j = R_kk^-T A_kb,j (forward substitution over its four rows)
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
-                if (bI[s2] != kb) continue;
+                if (bI[s2] != kb || bJ[s2] == kb) continue;
+                float rdk[4][4], rr[4][4], ri[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (u != ku) continue;
+                for (int c = 0; c < 4; ++c) {
+                    const float4 t = (k0 + c < m) ? *reinterpret_cast<const float4*>(A + (k0 + c) * lda + k0)
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                    rdk[c][0] = t.x; rdk[c][1] = t.y; rdk[c][2] = t.z; rdk[c][3] = t.w;
+                    ri[c] = sh_rinv[c];
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const int jj = 4 * bJ[s2] + v;
-                        if (jj > k && jj < lda) A[k * lda + jj] = a[s2][u][v] * inv;
-                        else if (jj == k) A[k * lda + k] = rkk;
+                        float val = a[s2][c][v];
+#pragma unroll
+                        for (int l = 0; l < c; ++l) val = __fmaf_rn(-rdk[l][c], rr[l][v], val);
+                        rr[c][v] = val * ri[c];
                     }
-                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (k0 + c < m) *reinterpret_cast<float4*>(A + (k0 + c) * lda + 4 * bJ[s2]) =
+                                        make_float4(rr[c][0], rr[c][1], rr[c][2], rr[c][3]);
             }
-            __syncthreads();
-            const int nk = k + 1, nkb = nk >> 2, nku = nk & 3;
+            __syncthreads();                  // block row kb of R is published
+            // rank-4 update of the blocks below block row kb, then the next diagonal block
 #pragma unroll
             for (int s2 = 0; s2 < 2; ++s2) {
-                if (bI[s2] < 0 || 4 * bI[s2] + 3 <= k) continue;
-                const float4 ri = *reinterpret_cast<const float4*>(A + k * lda + 4 * bI[s2]);
-                const float4 rj = *reinterpret_cast<const float4*>(A + k * lda + 4 * bJ[s2]);
-                const float riv[4] = {ri.x, ri.y, ri.z, ri.w}, rjv[4] = {rj.x, rj.y, rj.z, rj.w};
+                if (bI[s2] <= kb) continue;
+                float ri[4][4], rj[4][4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const bool live = k0 + c < m;
+                    const float4 x = live ? *reinterpret_cast<const float4*>(A + (k0 + c) * lda + 4 * bI[s2])
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                    const float4 y = live ? *reinterpret_cast<const float4*>(A + (k0 + c) * lda + 4 * bJ[s2])
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+                    ri[c][0] = x.x; ri[c][1] = x.y; ri[c][2] = x.z; ri[c][3] = x.w;
+                    rj[c][0] = y.x; rj[c][1] = y.y; rj[c][2] = y.z; rj[c][3] = y.w;
+                }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        const int ii = 4 * bI[s2] + u, jj = 4 * bJ[s2] + v;
-                        if (ii > k && jj >= ii) a[s2][u][v] = __fmaf_rn(-riv[u], rjv[v], a[s2][u][v]);
-                    }
-                if (nk < m && bI[s2] == nkb && bJ[s2] == nkb) {
+                        float acc = a[s2][u][v];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (u == nku) sh_piv = a[s2][u][u];
-                }
+                        for (int c = 0; c < 4; ++c) acc = __fmaf_rn(-ri[c][u], rj[c][v], acc);
+                        a[s2][u][v] = acc;
+                    }
+                if (bI[s2] == kb + 1 && bJ[s2] == kb + 1) factor_diag(s2, kb + 1);
             }
-            __syncthreads();
         }
     }
     // diagonal blocks of W = R^-1: warp p inverts R_pp, lane j solving for its
