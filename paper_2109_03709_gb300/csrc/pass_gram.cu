@@ -519,7 +519,13 @@ cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r
     const int64_t ldv = rup(d, 8), ldy = tile_row ? (int64_t)nsel * 128 : rup(rows, 128);
     const int ntiles = (int)(ldy / 128), nk = (int)((d + kGBK - 1) / kGBK);
     const int NV = accurate ? 3 : (f32 ? 2 : 1);
-    if (flush <= 0) flush = accurate ? (f32 ? 1 : 2) : nk;
+    // K-stages per fold of the FP32 tensor-core accumulator into the double-float
+    // running sums.  A fold costs ~10 instructions per accumulator element and is
+    // what bounds the kernel's time at short intervals; each accumulating MMA adds
+    // ~2e-8 relative drift.  BF16 data: every 4 stages (three piece products,
+    // 48 MMAs; measured drift ~1e-6 scaled entrywise); FP32 data: every stage
+    // (six piece products, 24 MMAs).
+    if (flush <= 0) flush = accurate ? (f32 ? 1 : 4) : nk;
     __nv_bfloat16* Qp = static_cast<__nv_bfloat16*>(sc.vp);
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
     cudaError_t e = launch_split_v(Q, d, m, m_pad, ldv, NV, Qp, st);
