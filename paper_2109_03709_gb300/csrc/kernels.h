@@ -27,7 +27,8 @@ cudaError_t xpass_simt(const XView& x, const float* V, int m, int64_t r0, int64_
 // ---- small dense kernels (small.cu) -------------------------------------------
 // G = A^T B in double-float accumulation, A, B d x m column-major FP32,
 // G m x m row-major FP64 (the rounded hi + lo pair) and, when Gf is given, its
-// FP32 rounding.  part: scratch of gram_part_floats(d, m) floats.  run_if:
+// FP32 rounding.  part: scratch of gram_part_floats(d, m) floats (enough for
+// every m' <= m as well).  run_if:
 // device flag or NULL; when given, both kernels do nothing while *run_if == 0.
 size_t gram_part_floats(int64_t d, int m);
 cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st,
@@ -78,7 +79,7 @@ cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int
 
 // EigenGame update from Z = X_b^T X_b V and C = V^T Z (both unnormalised by b):
 // MV = Z / b, Riemannian gradient, Nesterov momentum (buf), step lr, renormalise.
-// colnorm: m doubles of scratch.
+// colnorm: eigengame_scratch_bytes(d, m) bytes of scratch.
 size_t eigengame_scratch_bytes(int64_t d, int m);
 cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double* C, int64_t d, int m,
                              double inv_b, double lr, double mu, double* colnorm, cudaStream_t st);

@@ -28,9 +28,22 @@ namespace {
 constexpr int kGramTile = 32;        // output tile of gram_df
 constexpr int kGramRows = 128;       // rows of A/B per slice
 
-inline int gram_nslices(int64_t d) {
-    int p = (int)((d + kGramRows - 1) / kGramRows);
-    return p < 1 ? 1 : (p > 128 ? 128 : p);
+// Row slices of gram_df: one per kGramRows rows, at most 1024 / T^2 (at least
+// 128) for T x T output tiles, so that a narrow basis over many rows still
+// fills the GPU.
+inline int gram_nslices(int64_t d, int m) {
+    const int T = (m + kGramTile - 1) / kGramTile;
+    const int cap = 1024 / (T * T) > 128 ? 1024 / (T * T) : 128;
+    const int64_t p = (d + kGramRows - 1) / kGramRows;
+    return p < 1 ? 1 : (p > cap ? cap : (int)p);
+}
+
+// Threads that reduce one output of gram_reduce_kernel: a power of two up to
+// 32 leaving each at least four partials.
+inline int gram_reduce_lanes(int P) {
+    int L = 1;
+    while (L < 32 && P / (2 * L) >= 4) L *= 2;
+    return L;
 }
 
 // Exact product of two floats as an unevaluated sum p + e (FMA-based TwoProduct).
@@ -102,23 +115,34 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
         }
 }
 
-__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, bool sym, double* __restrict__ G,
-                                   float* __restrict__ Gf, const int* run_if) {
+// L consecutive threads (L a power of two dividing 32) reduce one output: lane
+// l sums slices l, l + L, ... in order, then the lanes are combined by a fixed
+// shuffle tree, all in double-float.
+__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, int L, bool sym,
+                                   double* __restrict__ G, float* __restrict__ Gf, const int* run_if) {
     if (run_if && *run_if == 0) return;
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= m * m) return;
-    const int i = idx / m, j = idx % m;
-    const int src = (sym && i / kGramTile > j / kGramTile) ? j * m + i : idx;
-    float hi = 0.f, lo = 0.f;
-    for (int p = 0; p < P; ++p) {
-        const float2 o = reinterpret_cast<const float2*>(part)[(int64_t)p * m * m + src];
-        df_add(hi, lo, o.x);
-        lo = __fadd_rn(lo, o.y);
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int idx = (int)(g / L), lane = (int)(g % L);
+    const bool live = idx < m * m;               // whole groups are live or not: shuffles stay uniform
+    dfloat q = {0.f, 0.f};
+    if (live) {
+        const int i = idx / m, j = idx % m;
+        const int src = (sym && i / kGramTile > j / kGramTile) ? j * m + i : idx;
+        for (int p = lane; p < P; p += L) {
+            const float2 o = reinterpret_cast<const float2*>(part)[(int64_t)p * m * m + src];
+            q = df_addx(q, df_norm(o.x, o.y));
+        }
     }
-    float s, e;
-    two_sum(hi, lo, s, e);
-    G[idx] = (double)s + (double)e;
-    if (Gf) Gf[idx] = s;
+    for (int o = L / 2; o > 0; o >>= 1) {
+        dfloat r;
+        r.hi = __shfl_down_sync(0xffffffffu, q.hi, o, L);
+        r.lo = __shfl_down_sync(0xffffffffu, q.lo, o, L);
+        q = df_addx(q, r);
+    }
+    if (live && lane == 0) {
+        G[idx] = (double)q.hi + (double)q.lo;
+        if (Gf) Gf[idx] = q.hi;
+    }
 }
 
 // ------------------------------------------------------------------ Cholesky
@@ -1005,16 +1029,20 @@ __global__ void eg_coef_kernel(const double* __restrict__ C, int m, double inv_b
     }
 }
 
+// Column norms: each block writes, per column, the double-float sum of its
+// rows' squares (exact FMA squares, a fixed shuffle tree per warp, the warps
+// in order); colnorm_reduce_kernel adds the blocks' sums.  All in FP32
+// arithmetic: GB300's FP64 rate is a small fraction of its FP32 rate.
 __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, const float* __restrict__ Z,
                                const float* __restrict__ coef_g, const float* __restrict__ alpha_g, int64_t d, int m,
-                               float inv_b, float lr, float mu, double* __restrict__ colpart) {
+                               float inv_b, float lr, float mu, float2* __restrict__ colpart) {
     extern __shared__ float sm[];
     float* coef = sm;                      // m x m
     float* alpha = coef + m * m;           // m
     float* mv = alpha + m;                 // m x kRowThreads
-    __shared__ double red[kMaxM];
+    __shared__ float2 red[kRowThreads / 32][kMaxM];
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) coef[e] = coef_g[e];
-    for (int e = threadIdx.x; e < m; e += blockDim.x) { alpha[e] = alpha_g[e]; red[e] = 0.0; }
+    for (int e = threadIdx.x; e < m; e += blockDim.x) alpha[e] = alpha_g[e];
     __syncthreads();
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int t = threadIdx.x;
@@ -1033,27 +1061,64 @@ __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, c
             vn = __fmaf_rn(lr, __fmaf_rn(mu, b, g), v);           // Nesterov step
             V[(int64_t)j * d + r] = vn;
         }
-        // column norm^2 partial of this block
-        double x = (double)vn * (double)vn;
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffff, x, o);
-        if ((t & 31) == 0) atomicAdd(&red[j], x);   // within the block only: fixed set of warps
+        // this block's part of the column's squared norm
+        const float p = __fmul_rn(vn, vn);
+        dfloat q = df_norm(p, __fmaf_rn(vn, vn, -p));
+        for (int o = 16; o > 0; o >>= 1) {
+            dfloat r;
+            r.hi = __shfl_down_sync(0xffffffffu, q.hi, o);
+            r.lo = __shfl_down_sync(0xffffffffu, q.lo, o);
+            q = df_addx(q, r);
+        }
+        if ((t & 31) == 0) red[t >> 5][j] = make_float2(q.hi, q.lo);
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < m; j += blockDim.x) colpart[(int64_t)blockIdx.x * m + j] = red[j];
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        dfloat q = df_norm(red[0][j].x, red[0][j].y);
+        for (int w = 1; w < kRowThreads / 32; ++w) q = df_addx(q, df_norm(red[w][j].x, red[w][j].y));
+        colpart[(int64_t)blockIdx.x * m + j] = make_float2(q.hi, q.lo);
+    }
 }
 
-__global__ void colnorm_reduce_kernel(const double* __restrict__ colpart, int nblk, int m, double* __restrict__ nrm) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= m) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += colpart[(int64_t)b * m + j];
-    nrm[j] = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
+// One block per column: thread t adds blocks t, t + blockDim, ... in order,
+// then a fixed tree in shared memory; the column's scale 1/norm is written as
+// a pair of floats (hi, lo) with hi + lo = 1/norm to about 2^-48.
+constexpr int kNormThreads = 256;
+__global__ void colnorm_reduce_kernel(const float2* __restrict__ colpart, int nblk, int m, float2* __restrict__ inv) {
+    __shared__ float2 s[kNormThreads];
+    const int j = blockIdx.x, t = threadIdx.x;
+    dfloat q = {0.f, 0.f};
+    for (int b = t; b < nblk; b += kNormThreads) {
+        const float2 o = colpart[(int64_t)b * m + j];
+        q = df_addx(q, df_norm(o.x, o.y));
+    }
+    s[t] = make_float2(q.hi, q.lo);
+    __syncthreads();
+    for (int h = kNormThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            q = df_addx(df_norm(s[t].x, s[t].y), df_norm(s[t + h].x, s[t + h].y));
+            s[t] = make_float2(q.hi, q.lo);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double n2 = (double)s[0].x + (double)s[0].y;
+        const double r = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+        const float hi = (float)r;
+        inv[j] = make_float2(hi, (float)(r - (double)hi));
+    }
 }
 
-__global__ void colscale_kernel(float* __restrict__ V, int64_t d, int m, const double* __restrict__ inv) {
+// V[:, j] *= 1/norm_j: the product with the pair (hi, lo) rounded once (the
+// FMA gives v*hi's exact error; v*lo and that error are added before rounding).
+__global__ void colscale_kernel(float* __restrict__ V, int64_t d, const float2* __restrict__ inv) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= d) return;
-    for (int j = 0; j < m; ++j) V[(int64_t)j * d + r] = (float)((double)V[(int64_t)j * d + r] * inv[j]);
+    const float2 s = inv[blockIdx.y];
+    float* v = V + (int64_t)blockIdx.y * d + r;
+    const float x = *v;
+    const float p = __fmul_rn(x, s.x);
+    *v = __fadd_rn(p, __fmaf_rn(x, s.y, __fmaf_rn(x, s.x, -p)));
 }
 
 // ------------------------------------------------------------------ Philox + Box-Muller
@@ -1153,17 +1218,26 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 
 // ============================================================================ launchers
 
-size_t gram_part_floats(int64_t d, int m) { return (size_t)gram_nslices(d) * m * m * 2; }
+// The workspace sized for m also serves every narrower basis.
+size_t gram_part_floats(int64_t d, int m) {
+    size_t most = 0;
+    for (int w = 1; w <= m; ++w) {
+        const size_t f = (size_t)gram_nslices(d, w) * w * w * 2;
+        most = f > most ? f : most;
+    }
+    return most;
+}
 
 cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G, float* part, cudaStream_t st,
                     float* Gf, const int* run_if) {
-    const int P = gram_nslices(d);
+    const int P = gram_nslices(d, m);
     const int64_t slice = (d + P - 1) / P;
     const int T = (m + kGramTile - 1) / kGramTile;
     note_launch();
     gram_df_kernel<<<dim3(T, T, P), 256, 0, st>>>(A, B, d, m, part, slice, run_if);
+    const int L = gram_reduce_lanes(P);
     note_launch();
-    gram_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(part, P, m, A == B, G, Gf, run_if);
+    gram_reduce_kernel<<<ceil_div_i((int64_t)m * m * L, 256), 256, 0, st>>>(part, P, m, L, A == B, G, Gf, run_if);
     return cudaGetLastError();
 }
 
@@ -1419,7 +1493,7 @@ cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int
 
 cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double* C, int64_t d, int m, double inv_b,
                              double lr, double mu, double* colnorm, cudaStream_t st) {
-    // colnorm scratch layout: [coef m*m f32][alpha m f32][inv m f64][partials nblk*m f64]
+    // colnorm scratch layout: [coef m*m f32][alpha m f32][inv m float2][partials nblk*m float2]
     const int nblk = ceil_div_i(d, kRowThreads);
     char* p = reinterpret_cast<char*>(colnorm);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -1427,9 +1501,9 @@ cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double*
     p += al((size_t)m * m * 4);
     float* alpha = reinterpret_cast<float*>(p);
     p += al((size_t)m * 4);
-    double* inv = reinterpret_cast<double*>(p);
+    float2* inv = reinterpret_cast<float2*>(p);
     p += al((size_t)m * 8);
-    double* part = reinterpret_cast<double*>(p);
+    float2* part = reinterpret_cast<float2*>(p);
     note_launch();
     eg_coef_kernel<<<1, 256, 0, st>>>(C, m, inv_b, coef, alpha);
     const size_t smem = (size_t)m * m * 4 + (size_t)m * 4 + (size_t)m * kRowThreads * 4;
@@ -1439,9 +1513,9 @@ cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double*
     eg_step_kernel<<<nblk, kRowThreads, smem, st>>>(V, buf, Z, coef, alpha, d, m, (float)inv_b, (float)lr,
                                                      (float)mu, part);
     note_launch();
-    colnorm_reduce_kernel<<<1, 128, 0, st>>>(part, nblk, m, inv);
+    colnorm_reduce_kernel<<<m, kNormThreads, 0, st>>>(part, nblk, m, inv);
     note_launch();
-    colscale_kernel<<<ceil_div_i(d, 256), 256, 0, st>>>(V, d, m, inv);
+    colscale_kernel<<<dim3(ceil_div_i(d, 256), m), 256, 0, st>>>(V, d, inv);
     return cudaGetLastError();
 }
 
