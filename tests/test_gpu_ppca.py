@@ -8,7 +8,8 @@
 * the whole pipeline vs the ground truth on the 4096 x 256 workload: the same
   LCES as the oracle's own pipeline, eigenvalues within 1e-5;
 * Oja and EigenGame trajectories vs the oracle's, step by step, for a few
-  steps (FP32 vs FP64: <= 1e-4 entrywise after 5 steps);
+  steps (FP32 vs FP64: <= 1e-4 entrywise after 5 steps); EigenGame also on a
+  32768 x 16 basis (1e-4 of the largest entry; unit columns to 1e-6);
 * priming state: finalize does not change it; checkpoint/resume is bit-exact;
 * host-side errors: finalize before prime, workspace cap, bad k.
 """
@@ -166,6 +167,32 @@ def test_eigengame_trajectory_parity(P):
         Vg = get_basis(P, h, d, m)
         Vo = oracle.eigengame_prime(Xs, host_basis(V0d), 500, steps, 0.02, 0.9)
         assert np.abs(Vg - Vo).max() <= 1e-4
+
+
+def test_eigengame_trajectory_parity_long_narrow_basis(P):
+    """A 32768 x 16 basis: the Gram C = V^T Z is summed over 256 row slices
+    (32 lanes per output in the reduction) and the column norms over 512
+    blocks, the many-slice forms of both reductions.  Entries are ~1/sqrt(d),
+    so the bound is relative to the largest; the renormalised columns have
+    unit norm to FP32 rounding."""
+    import torch
+    n, d, m, b = 600, 32768, 16, 300
+    X = synth.hadamard_rotated_data_torch(n, d, 2.0 * 0.9995 ** np.arange(1, d + 1), 9, "cpu",
+                                          torch.float32)[0].numpy()
+    Xd = dev_matrix(X, "f32")
+    Xs = stored_f64(Xd)
+    V0d = dev_basis(synth.initial_basis(d, m, 11))
+    prm = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
+    prm.batch = b
+    prm.lr = 0.02
+    prm.precision = P.PPCA_PREC_ACCURATE
+    h = P.ppca_create(Xd)
+    for steps in [1, 3]:
+        P.ppca_prime(h, P.PPCA_EIGENGAME, m, steps, prm, V0=V0d)
+        Vg = get_basis(P, h, d, m)
+        Vo = oracle.eigengame_prime(Xs, host_basis(V0d), b, steps, 0.02, 0.9)
+        assert np.abs(Vg - Vo).max() <= 1e-4 * np.abs(Vo).max()
+        assert np.abs(np.linalg.norm(Vg, axis=0) - 1.0).max() <= 1e-6
 
 
 def test_host_side_errors(P, c1):
