@@ -37,7 +37,7 @@ import numpy as np
 
 __all__ = [
     "build_native", "jacobi_eigh", "eigh_desc", "sign_fix", "orth", "qr_pos",
-    "covariance", "ground_truth", "ppca_finalize", "ppca_finalize_cov",
+    "covariance", "ground_truth", "ppca_finalize",
     "power_step", "power_prime", "power_seq_prime", "minibatch_rows", "oja_step", "oja_prime",
     "eigengame_gradients", "eigengame_step", "eigengame_prime",
     "angle", "angles", "lces", "principal_angles", "variance_captured",
@@ -192,15 +192,6 @@ def ppca_finalize(X, V, k: int):
     Y = X @ Q
     G = Y.T @ Y
     w, U = eigh_desc(G)
-    E = sign_fix(Q @ U[:, :k])
-    return E, w[:k] / n
-
-
-def ppca_finalize_cov(C, n: int, V, k: int):
-    """Same as ppca_finalize, from a precomputed covariance C = X^T X."""
-    Q = orth(V)
-    G = Q.T @ np.asarray(C, dtype=np.float64) @ Q
-    w, U = eigh_desc(0.5 * (G + G.T))
     E = sign_fix(Q @ U[:, :k])
     return E, w[:k] / n
 
