@@ -263,10 +263,13 @@ typedef struct ppca_schedule {
     int32_t producers;        /* CTAs running Y = X V in the fused pass (0: one per SM)           */
     int32_t window;           /* tiles a producer may run ahead of the slowest consumer (0: the  */
                               /* tiles being produced plus four per consumer row group)           */
-    int32_t flush;            /* split-precision passes and the fused pass's Z = X^T Y: K-stages  */
-                              /* (64 wide) an FP32 tensor-core accumulator takes before it is     */
-                              /* folded into a double-float sum (0: library default; larger =     */
-                              /* fewer folds, less accurate)                                      */
+    int32_t flush;            /* projected Gram (split-precision Y = X Q) and the fused pass's    */
+                              /* Z = X^T Y: K-stages (64 wide) an FP32 tensor-core accumulator    */
+                              /* takes before it is folded into a double-float sum (0: library    */
+                              /* default -- 4 for BF16 data and 1 for FP32 data in the projected  */
+                              /* Gram, 4096 (2048 row tiles) in the fused pass; larger = fewer    */
+                              /* folds, less accurate).  The two-kernel X-passes fold at fixed    */
+                              /* intervals.                                                       */
     int32_t engine;           /* X-pass engine: 0 library choice, 1 tensor cores (BF16 / FP32     */
                               /* data), 2 CUDA cores (any data type)                              */
     int32_t kparts;           /* fused pass: K parts per 128-row tile of Y = X V (1 or 2, 2 only  */

@@ -19,7 +19,7 @@ struct TcSchedule {
     int fused = -1;         // 1: fused single-read kernel, 0: two GEMM kernels, -1: choose
     int producers = 0;      // CTAs running the Y = X V pipeline in the fused kernel
     int window = 0;         // tiles a producer may run ahead of the slowest consumer
-    int flush = 0;          // split-precision passes: K-stages per accumulator flush (0: default)
+    int flush = 0;          // projected Gram and fused pass: K-stages per accumulator fold (0: default)
     int engine = 0;         // 0: library choice, 1: tensor cores, 2: CUDA cores
     int kparts = 0;         // fused kernel: K parts per producer tile (2: two K halves; else 1)
     int l2_keep = 0;        // fused kernel: percent of a tile's K-stages loaded evict_last (0: from the L2 size)
