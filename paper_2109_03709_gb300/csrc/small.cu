@@ -256,14 +256,14 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
 
 // Blocked Cholesky in FP32 of the diagonally scaled Gram matrix G' = D G D
 // (D = diag(G)^-1/2, so G' has a unit diagonal), with the triangular inverse
-// W = R'^-1 built block by block; writes Rinv = D W, so V Rinv = V R^-1 for
-// G = R^T R.  Panels of 32 columns:
-//   (a) warp 0 factors the 32 x 32 diagonal block (lane j holds column j,
-//       pivots and rows broadcast by shuffles) and inverts it;
-//   (b) the block row of R: R_pj = W_pp^T A_pj;
-//   (c) the trailing update A_ij -= R_pi^T R_pj.
-// Then the off-diagonal blocks of W, one block diagonal at a time:
-// W_pq = -W_pp sum_{p<l<=q} R_pl W_lq.  Ten to twenty barriers in all.
+// W = R'^-1; writes Rinv = D W, so V Rinv = V R^-1 for G = R^T R.
+//   * near_identity (second CholeskyQR pass): when max|G' - I| <= kSeriesMax
+//     the factor comes from the series below (chol_series) and nothing else runs;
+//   * otherwise R' by a right-looking blocked Cholesky on 4 x 4 blocks held in
+//     registers (two barriers per four columns, described at the loop);
+//   * W's 32 x 32 diagonal blocks by back substitution, one warp per block,
+//     then its off-diagonal blocks one block diagonal at a time:
+//     W_pq = -W_pp sum_{p<l<=q} R_pl W_lq.
 // With `fallback` set (first CholeskyQR pass, V possibly ill-conditioned) the
 // kernel bounds kappa(G') <= (max row sum |G'|) ||W||_F^2 (Gershgorin for
 // lambda_max; trace(G'^-1) = ||W||_F^2 >= 1/lambda_min).  A non-positive
