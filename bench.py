@@ -971,7 +971,7 @@ def run_reference(args):
         return
     import synth
     cfg = synth.CONFIGS[args.workload]
-    rows = 32768
+    rows = args.cpu_rows
     out, cores, err = run_cpu_leg(args.workload, rows, args.steps, args.warmup)
     if out is None:
         print(json.dumps({"impl": "reference", "unavailable": f"oracle leg failed: {err}"}))

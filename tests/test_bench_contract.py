@@ -1,0 +1,32 @@
+"""The reference arm's JSON line on CPU: `bench.py --impl reference` times the
+FP64 oracle on a small row sample and prints one line with the keys and types
+of the bench contract (the GPU arm's line is checked on the GPU by running it)."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--workload", "power_fp32_4096x256", "--cpu-rows", "1024"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and "unavailable" not in j
+    for key, typ in [("metric", str), ("value", float), ("unit", str), ("n_gpus", int), ("steps", int),
+                     ("warmup", int), ("ms_per_step", float), ("higher_is_better", bool), ("scaling", str),
+                     ("dtype", str), ("data", str), ("config", dict), ("cpu_baseline", dict), ("e2e", dict)]:
+        assert isinstance(j[key], typ), key
+    assert j["vs_baseline"] is None
+    assert (j["n_gpus"], j["steps"], j["warmup"]) == (1, 2, 1)
+    assert j["value"] > 0 and j["ms_per_step"] > 0
+    assert j["config"]["workload"] == "power_fp32_4096x256"
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == j["value"] and cb["unit"] == j["unit"]
+    assert cb["cores"] >= 1 and "1024-row" in cb["sample"]
+    assert j["e2e"] == {"value": j["value"], "unit": j["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
