@@ -47,8 +47,11 @@ def test_batch_matches_oracle(cuda_device):
     import paper_2109_03709_gb300 as P
     inst = make_batch(12, seed=404, T=10)
     b = P.ppca_batch_create(inst, slots=4)
+    assert P.ppca_batch_kernel_count(b) == 0          # the graph is captured by the first run
     P.ppca_batch_run(b)
     P.ppca_batch_sync(b)
+    kernels = P.ppca_batch_kernel_count(b)
+    assert kernels >= len(inst) * 10                  # at least one launch per power iteration
     for i, ins in enumerate(inst):
         Xs = ins["X"].double().cpu().numpy()
         Vg = host_basis(ins["V_out"])
@@ -64,6 +67,7 @@ def test_batch_matches_oracle(cuda_device):
     P.ppca_batch_sync(b)
     for ins, e0 in zip(inst, before):
         assert torch.equal(ins["E"], e0)
+    assert P.ppca_batch_kernel_count(b) == kernels    # replayed, not captured again
 
 
 def test_batch_equals_single_handle(cuda_device):

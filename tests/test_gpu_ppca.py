@@ -10,6 +10,7 @@
 * Oja and EigenGame trajectories vs the oracle's, step by step, for a few
   steps (FP32 vs FP64: <= 1e-4 entrywise after 5 steps); EigenGame also on a
   32768 x 16 basis (1e-4 of the largest entry; unit columns to 1e-6);
+* FP8 priming with the pPCA step on the BF16 copy (ppca_set_refine);
 * priming state: finalize does not change it; checkpoint/resume is bit-exact;
 * host-side errors: finalize before prime, workspace cap, bad k.
 """
@@ -93,6 +94,30 @@ def test_power_more_iterations_reaches_full_streak(P, c1):
     E, lam = finalize(P, h, cfg.d, cfg.k)
     Et, lt = oracle.ground_truth(Xs, cfg.k)
     check_against(E, lam, Et, lt, 1e-5, 1e-4)
+
+
+def test_fp8_priming_then_refine_copy_finalize(P):
+    """FP8 data (E4M3 + row scales) primes; the pPCA step reads the BF16 copy
+    set with ppca_set_refine: parity with the oracle's pPCA step on the BF16
+    values from the GPU's own primed basis (eigenvalues 1e-5, angles 1e-4 rad)."""
+    import torch
+    n, d, k, m, T = 3000, 256, 8, 16, 6
+    X, _ = synth.gaussian_data(n, d, 0.9 ** np.arange(1, d + 1), seed=21)
+    Xf = torch.from_numpy(X.astype(np.float32)).cuda()
+    X16 = torch.empty((n, d), dtype=torch.bfloat16, device="cuda")
+    X8 = torch.empty((n, d), dtype=torch.uint8, device="cuda")
+    s = torch.empty(n, dtype=torch.float32, device="cuda")
+    P.ppca_quantize_bf16(Xf, X16)
+    P.ppca_quantize_fp8(Xf, X8, s)
+    torch.cuda.synchronize()
+    h = P.ppca_create(X8, row_scales=s)
+    P.ppca_set_refine(h, X16)
+    P.ppca_prime(h, P.PPCA_POWER, m, T, P.ppca_prime_params_default(P.PPCA_POWER),
+                 V0=dev_basis(synth.initial_basis(d, m, 21)))
+    E, lam = finalize(P, h, d, k, P.PPCA_PREC_ACCURATE)
+    Vg = get_basis(P, h, d, m)
+    Eo, lo = oracle.ppca_finalize(stored_f64(X16), Vg, k)
+    check_against(E, lam, Eo, lo, 1e-5, 1e-4)
 
 
 def test_finalize_does_not_change_priming_state(P, c1):
