@@ -31,6 +31,24 @@ sys.path.insert(0, ROOT)
 
 DEFAULT_WORKLOAD = "precision_bf16_1000000x4096"
 BYTES = {"f32": 4, "bf16": 2, "fp8": 1}
+L2_BYTES = 129e6          # GB300 L2
+
+
+def pass_labels(dtype: str, bytes_per_pass: float) -> dict:
+    """What the power-priming workloads' JSON line says about the passes it timed:
+    the priming and pPCA-step precisions, the dominant kernel and whether X fits in L2."""
+    if dtype == "bf16":
+        prime, fin = "bf16 (fast)", "bf16x3 (split)"
+        kernel = "fused single-read X-pass (xpass_fused_kernel + zreduce + split_v), algorithmic bytes n*d*2 per pass"
+    else:
+        prime, fin = "3xtf32 (fast)", "three bf16 pieces of X and Q, six products (split)"
+        kernel = "3xTF32 X-pass (xv_f32_kernel + xty_f32_kernel + zreduce), algorithmic bytes n*d*4 per pass"
+    if bytes_per_pass > L2_BYTES:
+        l2 = f"inputs ({bytes_per_pass / 1e9:.1f} GB) larger than L2, no flush"
+    else:
+        l2 = (f"inputs ({bytes_per_pass / 1e6:.1f} MB) fit in L2, no flush: latency-bound, the HBM "
+              "fraction is not meaningful")
+    return {"prime_precision": prime, "finalize_precision": fin, "kernel": kernel, "l2": l2}
 
 
 def parse_args(argv=None):
@@ -874,11 +892,11 @@ def run_ours(args):
     # DRAM bytes (read + write) of one fused-pass launch on this workload, from the ncu
     # capture in profiles/xpass_fused_bf16_131072x4096_ncu.md (131072 rows, scaled by rows)
     traffic = 12.51e9 if (cfg.name == "precision_bf16_1000000x4096" and n == 1000000) else None
+    labels = pass_labels(cfg.dtype, bytes_per_pass)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
                 "peak_source": peak_kind,
-                "kernel": "fused single-read X-pass (xpass_fused_kernel + zreduce + split_v), algorithmic "
-                          "bytes n*d*2 per pass",
+                "kernel": labels["kernel"],
                 "pass_ms": round(pass_ms, 4), "passes_timed": tm.passes[fast],
                 "projected_gram_ms": round(split_ms, 4),
                 "step_share_of_passes": round((tm.pass_ms[fast] + tm.pass_ms[split]) / ms, 4)}
@@ -947,9 +965,9 @@ def run_ours(args):
             "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": cfg.dtype, "data": "synthetic",
             "config": {"workload": cfg.name, "n": n, "d": d, "k": k, "l": cfg.l, "primer": "power", "T": T,
-                       "prime_precision": "bf16 (fast)", "finalize_precision": "bf16x3 (split)",
-                       "parallelism": f"replicas x{ws}",
-                       "l2": f"inputs ({bytes_per_pass / 1e9:.1f} GB) larger than L2, no flush"},
+                       "prime_precision": labels["prime_precision"],
+                       "finalize_precision": labels["finalize_precision"],
+                       "parallelism": f"replicas x{ws}", "l2": labels["l2"]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": tm.launches,
             "lces": lces,

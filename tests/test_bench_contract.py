@@ -30,3 +30,17 @@ def test_reference_arm_prints_one_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == j["value"] and cb["unit"] == j["unit"]
     assert cb["cores"] >= 1 and "1024-row" in cb["sample"]
     assert j["e2e"] == {"value": j["value"], "unit": j["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_pass_labels_of_the_power_workloads():
+    sys.path.insert(0, ROOT)
+    import bench
+    main = bench.pass_labels("bf16", 1000000 * 4096 * 2)
+    assert main == {"prime_precision": "bf16 (fast)", "finalize_precision": "bf16x3 (split)",
+                    "kernel": "fused single-read X-pass (xpass_fused_kernel + zreduce + split_v), algorithmic "
+                              "bytes n*d*2 per pass",
+                    "l2": "inputs (8.2 GB) larger than L2, no flush"}
+    small = bench.pass_labels("f32", 4096 * 256 * 4)          # 4.2 MB: L2-resident
+    assert small["prime_precision"] == "3xtf32 (fast)" and "xv_f32_kernel" in small["kernel"]
+    assert small["l2"].startswith("inputs (4.2 MB) fit in L2") and "not meaningful" in small["l2"]
+    assert bench.pass_labels("f32", 100000 * 1024 * 4)["l2"] == "inputs (0.4 GB) larger than L2, no flush"
