@@ -189,12 +189,30 @@ def _check(status: int, func: str):
         raise PPCAError(status, func, msg.decode() if msg else "")
 
 
-def _ptr(t) -> int | None:
-    if t is None:
-        return None
-    if isinstance(t, int):
+def _arg(t, what: str, on_device: bool, itemsize: int | None, contiguous: bool) -> int | None:
+    """Address of a tensor argument, refused here if it cannot be what the library
+    reads or writes there: memory on the wrong side (a host tensor where a kernel
+    would write through the address, or the reverse), the wrong element size, or
+    a non-contiguous layout where the call takes no leading dimension.  None and
+    integer addresses are passed through unchecked."""
+    if t is None or isinstance(t, int):
         return t
+    if bool(t.is_cuda) != on_device:
+        raise ValueError(f"{what} must be in {'device' if on_device else 'host'} memory "
+                         f"({'a CUDA' if on_device else 'a CPU'} tensor)")
+    if itemsize is not None and t.element_size() != itemsize:
+        raise TypeError(f"{what} must have {itemsize}-byte elements, not {t.dtype}")
+    if contiguous and not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
     return t.data_ptr()
+
+
+def _dev(t, what: str, itemsize: int | None = None, contiguous: bool = True) -> int | None:
+    return _arg(t, what, True, itemsize, contiguous)
+
+
+def _host(t, what: str, itemsize: int | None = None, contiguous: bool = True) -> int | None:
+    return _arg(t, what, False, itemsize, contiguous)
 
 
 def _stream_ptr(stream) -> int | None:
@@ -259,8 +277,8 @@ def ppca_create(X, row_scales=None, stream=None, *, n=None, d=None, ld=None, dty
             raise ValueError("X must be row-major (unit column stride)")
         dtype = _dtype_code(X)
     out = ctypes.c_void_p()
-    _check(lib.ppca_create(ctypes.byref(out), _ptr(X), n, d, ld, dtype, _ptr(row_scales), _stream_ptr(stream)),
-           "ppca_create")
+    _check(lib.ppca_create(ctypes.byref(out), _dev(X, "X", contiguous=False), n, d, ld, dtype,
+                           _dev(row_scales, "row_scales", 4), _stream_ptr(stream)), "ppca_create")
     return Handle(out.value, [X, row_scales])
 
 
@@ -270,7 +288,8 @@ def ppca_set_refine(h: Handle, X_refine, ld=None, dtype=None):
         return
     ld = X_refine.stride(0) if ld is None else ld
     dtype = _dtype_code(X_refine) if dtype is None else dtype
-    _check(load_library().ppca_set_refine(h.ptr, _ptr(X_refine), ld, dtype), "ppca_set_refine")
+    _check(load_library().ppca_set_refine(h.ptr, _dev(X_refine, "X_refine", contiguous=False), ld, dtype),
+           "ppca_set_refine")
     h._keep.append(X_refine)
 
 
@@ -282,7 +301,7 @@ def ppca_prime(h: Handle, method: int, m: int, T: int, params: ppca_prime_params
     if params is None:
         params = ppca_prime_params_default(method)
     if V0 is not None:
-        params.V0 = _ptr(V0)
+        params.V0 = _dev(V0, "V0", 4)
     _check(load_library().ppca_prime(h.ptr, method, m, T, ctypes.byref(params)), "ppca_prime")
 
 
@@ -291,39 +310,41 @@ def ppca_prime_continue(h: Handle, T: int):
 
 
 def ppca_finalize(h: Handle, k: int, E, lam, precision: int = PPCA_PREC_AUTO):
-    _check(load_library().ppca_finalize(h.ptr, k, _ptr(E), _ptr(lam), precision), "ppca_finalize")
+    _check(load_library().ppca_finalize(h.ptr, k, _dev(E, "E", 4), _dev(lam, "lam", 8), precision),
+           "ppca_finalize")
 
 
 def ppca_upload(h: Handle, X_host, row_scales_host=None, ld_host: int | None = None):
     """Copy host X (a CPU tensor or array pointer of the handle's dtype) into the handle's device X."""
     if ld_host is None:
         ld_host = X_host.stride(0)
-    _check(load_library().ppca_upload(h.ptr, _ptr(X_host), ld_host, _ptr(row_scales_host)), "ppca_upload")
+    _check(load_library().ppca_upload(h.ptr, _host(X_host, "X_host", contiguous=False), ld_host,
+                                      _host(row_scales_host, "row_scales_host", 4)), "ppca_upload")
 
 
 def ppca_finalize_host(h: Handle, k: int, E_host, lam_host, precision: int = PPCA_PREC_AUTO):
     """pPCA step with E (k x d row-major = d x k column-major FP32) and lambda (k FP64) written to host memory."""
-    _check(load_library().ppca_finalize_host(h.ptr, k, _ptr(E_host), _ptr(lam_host), precision),
-           "ppca_finalize_host")
+    _check(load_library().ppca_finalize_host(h.ptr, k, _host(E_host, "E_host", 4), _host(lam_host, "lam_host", 8),
+                                             precision), "ppca_finalize_host")
 
 
 def ppca_finalize_sampled(h: Handle, k: int, E, lam, precision: int = PPCA_PREC_AUTO, fraction: float = 0.1,
                           seed: int = 0) -> int:
     """pPCA step over a seeded sample of 128-row blocks; returns the number of sampled rows."""
     rows = ctypes.c_int64(0)
-    _check(load_library().ppca_finalize_sampled(h.ptr, k, _ptr(E), _ptr(lam), precision, fraction, seed,
-                                                ctypes.byref(rows)), "ppca_finalize_sampled")
+    _check(load_library().ppca_finalize_sampled(h.ptr, k, _dev(E, "E", 4), _dev(lam, "lam", 8), precision, fraction,
+                                                seed, ctypes.byref(rows)), "ppca_finalize_sampled")
     return rows.value
 
 
 def ppca_variance_captured(h: Handle, E, k: int, var, precision: int = PPCA_PREC_AUTO):
     """var[j] = e_j^T X^T X e_j for the k columns of E (device (k, d) tensor = d x k column-major)."""
-    _check(load_library().ppca_variance_captured(h.ptr, _ptr(E), k, _ptr(var), precision),
+    _check(load_library().ppca_variance_captured(h.ptr, _dev(E, "E", 4), k, _dev(var, "var", 8), precision),
            "ppca_variance_captured")
 
 
 def ppca_get_basis(h: Handle, V_out):
-    _check(load_library().ppca_get_basis(h.ptr, _ptr(V_out)), "ppca_get_basis")
+    _check(load_library().ppca_get_basis(h.ptr, _dev(V_out, "V_out", 4)), "ppca_get_basis")
 
 
 def ppca_sync(h: Handle):
@@ -351,21 +372,21 @@ def ppca_destroy(h: Handle):
 
 
 def ppca_xpass(h: Handle, V, m: int, r0: int, r1: int, Z, precision: int = PPCA_PREC_AUTO):
-    _check(load_library().ppca_xpass(h.ptr, _ptr(V), m, r0, r1, _ptr(Z), precision), "ppca_xpass")
+    _check(load_library().ppca_xpass(h.ptr, _dev(V, "V", 4), m, r0, r1, _dev(Z, "Z", 4), precision), "ppca_xpass")
 
 
 def ppca_projected_gram(h: Handle, Q, m: int, r0: int, r1: int, G, precision: int = PPCA_PREC_AUTO):
     """G (m x m FP64, device) = (X[r0:r1] Q)^T (X[r0:r1] Q) over the data the pPCA step reads."""
-    _check(load_library().ppca_projected_gram(h.ptr, _ptr(Q), m, r0, r1, _ptr(G), precision),
+    _check(load_library().ppca_projected_gram(h.ptr, _dev(Q, "Q", 4), m, r0, r1, _dev(G, "G", 8), precision),
            "ppca_projected_gram")
 
 
 def ppca_orthonormalize(h: Handle, V, Q, m: int):
-    _check(load_library().ppca_orthonormalize(h.ptr, _ptr(V), _ptr(Q), m), "ppca_orthonormalize")
+    _check(load_library().ppca_orthonormalize(h.ptr, _dev(V, "V", 4), _dev(Q, "Q", 4), m), "ppca_orthonormalize")
 
 
 def ppca_eigh(h: Handle, G, m: int, w, U):
-    _check(load_library().ppca_eigh(h.ptr, _ptr(G), m, _ptr(w), _ptr(U)), "ppca_eigh")
+    _check(load_library().ppca_eigh(h.ptr, _dev(G, "G", 8), m, _dev(w, "w", 8), _dev(U, "U", 8)), "ppca_eigh")
 
 
 class Batch:
@@ -391,17 +412,17 @@ def ppca_batch_create(instances, slots: int = 0, stream=None) -> Batch:
     keep = []
     for i, ins in enumerate(instances):
         X = ins["X"]
-        arr[i].X = _ptr(X)
+        arr[i].X = _dev(X, f"instance {i} X", contiguous=False)
         arr[i].n, arr[i].d = X.shape
         arr[i].ld = X.stride(0)
         arr[i].dtype = _dtype_code(X)
         arr[i].k, arr[i].m, arr[i].T = ins["k"], ins["m"], ins["T"]
-        arr[i].row_scales = _ptr(ins.get("row_scales"))
-        arr[i].V0 = _ptr(ins.get("V0"))
+        arr[i].row_scales = _dev(ins.get("row_scales"), f"instance {i} row_scales", 4)
+        arr[i].V0 = _dev(ins.get("V0"), f"instance {i} V0", 4)
         arr[i].seed = ins.get("seed", 0)
-        arr[i].E = _ptr(ins["E"])
-        arr[i].lambda_ = _ptr(ins["lam"])
-        arr[i].V_out = _ptr(ins.get("V_out"))
+        arr[i].E = _dev(ins["E"], f"instance {i} E", 4)
+        arr[i].lambda_ = _dev(ins["lam"], f"instance {i} lam", 8)
+        arr[i].V_out = _dev(ins.get("V_out"), f"instance {i} V_out", 4)
         keep.append(ins)
     out = ctypes.c_void_p()
     _check(load_library().ppca_batch_create(ctypes.byref(out), arr, len(instances), slots, _stream_ptr(stream)),
@@ -457,20 +478,23 @@ def ppca_eigh_noalloc(G, m: int, w, U, status=None, stream=None):
     capturing a CUDA graph); calls that overlap on the same GPU race on the
     shared scratch and must be ordered by the caller.
     """
-    _check(load_library().ppca_eigh_noalloc(_ptr(G), m, _ptr(w), _ptr(U), _ptr(status), _stream_ptr(stream)),
+    _check(load_library().ppca_eigh_noalloc(_dev(G, "G", 8), m, _dev(w, "w", 8), _dev(U, "U", 8),
+                                            _dev(status, "status", 4), _stream_ptr(stream)),
            "ppca_eigh_noalloc")
 
 
 def ppca_quantize_bf16(X, out, stream=None):
     n, d = X.shape
-    _check(load_library().ppca_quantize_bf16(_ptr(X), n, d, X.stride(0), _ptr(out), out.stride(0),
+    _check(load_library().ppca_quantize_bf16(_dev(X, "X", 4, contiguous=False), n, d, X.stride(0),
+                                             _dev(out, "out", 2, contiguous=False), out.stride(0),
                                              _stream_ptr(stream)), "ppca_quantize_bf16")
 
 
 def ppca_quantize_fp8(X, out, scales, stream=None):
     n, d = X.shape
-    _check(load_library().ppca_quantize_fp8(_ptr(X), n, d, X.stride(0), _ptr(out), out.stride(0), _ptr(scales),
-                                            _stream_ptr(stream)), "ppca_quantize_fp8")
+    _check(load_library().ppca_quantize_fp8(_dev(X, "X", 4, contiguous=False), n, d, X.stride(0),
+                                            _dev(out, "out", 1, contiguous=False), out.stride(0),
+                                            _dev(scales, "scales", 4), _stream_ptr(stream)), "ppca_quantize_fp8")
 
 
 def ppca_set_timing(h: Handle, enable: bool = True):
