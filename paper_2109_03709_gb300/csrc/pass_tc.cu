@@ -1,4 +1,6 @@
-// pass_tc.cu -- tensor-core X-pass for BF16 data: Z = X^T (X V) on tcgen05 + TMA.
+// pass_tc.cu -- tensor-core X-pass Z = X^T (X V) on tcgen05 + TMA: BF16 data
+// (the two kernels below, and the fused single-read pass further down), FP8
+// E4M3 data (widened to BF16 in shared memory) and FP32 data (3xTF32).
 //
 // The product X^T X V (Section 2.1's M x with M = X^T X; the minibatch sums
 // of Sections 2.2-2.3; the projection of Algorithm 1, step 3) is computed as
