@@ -2,8 +2,10 @@
 //
 // Algorithm 1 (primed PCA) maps onto the calls as follows:
 //   step 1 PRIMING            ppca_prime / ppca_prime_continue
-//   steps 2-5 span, project,  ppca_finalize: Q = orth(V); Z = X^T X Q (one pass);
-//   full-PCA, return          G = Q^T Z; G = U diag(w) U^T; E = Q U[:, :k]
+//   steps 2-5 span, project,  ppca_finalize: Q = orth(V); G = (X Q)^T (X Q) in
+//   full-PCA, return          one pass (on the CUDA-core engine and for FP8 data
+//                             without a refine copy: Z = X^T X Q, G = Q^T Z);
+//                             G = U diag(w) U^T; E = Q U[:, :k]; lambda = w / n
 #include <algorithm>
 #include <atomic>
 #include <cstdarg>

@@ -1,4 +1,4 @@
-// pass_tc.h -- tensor-core (tcgen05 + TMA) X-pass for BF16 data (internal).
+// pass_tc.h -- tensor-core (tcgen05 + TMA) X-passes and projected Gram (internal).
 #pragma once
 
 #include "common.cuh"
