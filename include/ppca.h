@@ -409,9 +409,13 @@ PPCA_API ppca_status ppca_xpass(ppca_handle *h, const float *V, int32_t m, int64
 
 /*
  * Orthonormalise the columns of V (d x m column-major, device) into Q (may
- * alias V): thin QR with positive diagonal by CholeskyQR2 -- G = V^T V in FP64,
- * G = R^T R (Cholesky, FP64), V <- V R^-1, twice.  A non-positive pivot
- * (rank-deficient V) is reported as PPCA_ERR_NUMERICAL by ppca_sync.
+ * alias V): thin QR with positive diagonal by CholeskyQR2 -- G = V^T V, G = R^T R,
+ * V <- V R^-1, twice.  G is accumulated in double-float FP32 (for d >= 16384 from
+ * three BF16 pieces on the tensor cores); the first factorisation runs in FP32
+ * on the diagonally scaled G and is redone in double-float when its
+ * conditioning bound fails; the second, of a matrix within rounding of the
+ * identity, in FP32 (a series when close enough).  A numerically rank-deficient
+ * V (pivot below 1e-15 trace(G)) is reported as PPCA_ERR_NUMERICAL by ppca_sync.
  */
 PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *Q, int32_t m);
 
