@@ -423,7 +423,11 @@ PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *
  * Symmetric eigensolve of an m x m FP64 matrix (the full-PCA of step 4):
  * G (device, m x m, symmetric) -> w (device, m, descending) and U (device,
  * m x m column-major, column j = unit eigenvector of w[j], sign convention as
- * above).  1 <= m <= 128.  G is not modified.
+ * above).  1 <= m <= 128.  G is not modified.  Parallel-order two-sided Jacobi
+ * sweeps in FP32 on one CTA, a rotation skipped when its off-diagonal entry is
+ * below the relative threshold (which keeps small eigenvalues accurate); the
+ * eigenvalues are the FP64 Rayleigh quotients of the FP32 eigenvectors.  A
+ * sweep cap reached is reported by ppca_sync.
  */
 PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, double *w, double *U);
 
