@@ -44,3 +44,12 @@ def test_pass_labels_of_the_power_workloads():
     assert small["prime_precision"] == "3xtf32 (fast)" and "xv_f32_kernel" in small["kernel"]
     assert small["l2"].startswith("inputs (4.2 MB) fit in L2") and "not meaningful" in small["l2"]
     assert bench.pass_labels("f32", 100000 * 1024 * 4)["l2"] == "inputs (0.4 GB) larger than L2, no flush"
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--workload", "power_fp32_4096x256", "--cpu-rows", "512"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
