@@ -18,7 +18,8 @@ import threading
 
 __all__ = [
     "PPCAError", "load_library", "library_path",
-    "PPCA_OK", "PPCA_F32", "PPCA_BF16", "PPCA_FP8_E4M3", "PPCA_POWER", "PPCA_OJA", "PPCA_EIGENGAME", "PPCA_POWER_SEQ",
+    "PPCA_OK", "PPCA_ERR_INVALID", "PPCA_ERR_OOM", "PPCA_ERR_CUDA", "PPCA_ERR_STATE", "PPCA_ERR_NUMERICAL",
+    "PPCA_ERR_TIMEOUT", "PPCA_ERR_UNSUPPORTED", "PPCA_F32", "PPCA_BF16", "PPCA_FP8_E4M3", "PPCA_POWER", "PPCA_OJA", "PPCA_EIGENGAME", "PPCA_POWER_SEQ",
     "PPCA_PREC_AUTO", "PPCA_PREC_FAST", "PPCA_PREC_ACCURATE", "ppca_prime_params",
     "ppca_version", "ppca_last_error", "ppca_prime_params_default", "ppca_create", "ppca_set_refine",
     "ppca_set_workspace_limit", "ppca_prime", "ppca_prime_continue", "ppca_finalize", "ppca_get_basis",
@@ -34,6 +35,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "_lib", "libppca_gb300.so")
 
 PPCA_OK = 0
+(PPCA_ERR_INVALID, PPCA_ERR_OOM, PPCA_ERR_CUDA, PPCA_ERR_STATE, PPCA_ERR_NUMERICAL, PPCA_ERR_TIMEOUT,
+ PPCA_ERR_UNSUPPORTED) = range(1, 8)
 PPCA_F32, PPCA_BF16, PPCA_FP8_E4M3 = 0, 1, 2
 PPCA_POWER, PPCA_OJA, PPCA_EIGENGAME, PPCA_POWER_SEQ = 0, 1, 2, 3
 PPCA_PREC_AUTO, PPCA_PREC_FAST, PPCA_PREC_ACCURATE = 0, 1, 2

@@ -76,3 +76,48 @@ def test_argument_checks_need_no_device(lib):
     assert lib.ppca_destroy(None) == 0
     assert lib.ppca_quantize_bf16(None, 4, 4, 4, fake, 4, None) == 1
     assert lib.ppca_quantize_fp8(fake, 4, 8, 4, fake, 8, fake, None) == 1   # ld_in < d
+
+
+def test_every_handle_or_batch_call_rejects_null(lib):
+    """Each entry point that takes a handle or a batch answers a NULL one with
+    PPCA_ERR_INVALID before any CUDA call (so no device is needed here)."""
+    import paper_2109_03709_gb300 as P
+    fake = 1 << 20
+    i64, i32 = ctypes.c_int64(0), ctypes.c_int32(0)
+    sched, timing = P.ppca_schedule(), P.ppca_timing()
+    out = ctypes.c_void_p(123)
+    statuses = {
+        "ppca_set_refine": lib.ppca_set_refine(None, fake, 4, P.PPCA_F32),
+        "ppca_set_workspace_limit": lib.ppca_set_workspace_limit(None, 0),
+        "ppca_prime_continue": lib.ppca_prime_continue(None, 1),
+        "ppca_get_basis": lib.ppca_get_basis(None, fake),
+        "ppca_set_schedule": lib.ppca_set_schedule(None, ctypes.byref(sched)),
+        "ppca_autotune": lib.ppca_autotune(None, 4, 0, 1, ctypes.byref(sched)),
+        "ppca_set_timing": lib.ppca_set_timing(None, 1),
+        "ppca_get_timing": lib.ppca_get_timing(None, ctypes.byref(timing)),
+        "ppca_get_state": lib.ppca_get_state(None, None, ctypes.byref(i64)),
+        "ppca_set_state": lib.ppca_set_state(None, fake, 64),
+        "ppca_xpass": lib.ppca_xpass(None, fake, 4, 0, 1, fake, 0),
+        "ppca_projected_gram": lib.ppca_projected_gram(None, fake, 4, 0, 1, fake, 0),
+        "ppca_orthonormalize": lib.ppca_orthonormalize(None, fake, fake, 4),
+        "ppca_eigh": lib.ppca_eigh(None, fake, 4, fake, fake),
+        "ppca_eigh_noalloc": lib.ppca_eigh_noalloc(None, 4, fake, fake, None, None),
+        "ppca_batch_create": lib.ppca_batch_create(ctypes.byref(out), None, 0, 0, None),
+        "ppca_batch_run": lib.ppca_batch_run(None),
+        "ppca_batch_autotune": lib.ppca_batch_autotune(None, 1, ctypes.byref(i32)),
+        "ppca_batch_kernel_count": lib.ppca_batch_kernel_count(None, ctypes.byref(i64)),
+        "ppca_batch_sync": lib.ppca_batch_sync(None),
+    }
+    for name, st in statuses.items():
+        assert st == P.PPCA_ERR_INVALID, name
+    assert out.value is None                      # ppca_batch_create cleared *out
+    assert lib.ppca_batch_destroy(None) == P.PPCA_OK
+
+
+def test_binding_constants_match_the_header_enums():
+    import paper_2109_03709_gb300 as P
+    text = open(HEADER).read()
+    values = {name: int(v) for name, v in re.findall(r"^\s+(PPCA_[A-Z0-9_]+)\s*=\s*(\d+)", text, flags=re.M)}
+    assert len(values) == 19
+    for name, v in values.items():
+        assert getattr(P, name) == v, name
