@@ -118,6 +118,6 @@ def test_binding_constants_match_the_header_enums():
     import paper_2109_03709_gb300 as P
     text = open(HEADER).read()
     values = {name: int(v) for name, v in re.findall(r"^\s+(PPCA_[A-Z0-9_]+)\s*=\s*(\d+)", text, flags=re.M)}
-    assert len(values) == 19
+    assert len(values) == 18               # status 8, dtype 3, method 4, precision 3
     for name, v in values.items():
         assert getattr(P, name) == v, name
