@@ -5,6 +5,9 @@
 * the pPCA output lies in span(V), is orthonormal, depends only on span(V), and
   equals the top-k eigenpairs of P_V X^T X P_V (computed separately in d dims);
 * exact recovery when span(V) is a dominant eigenspace (Theorem 4.4's limit);
+* four planted mistakes in the step (no orthonormalisation, transposed
+  rotation, eigenvalues not divided by n, ascending order) fail the
+  projected-problem pin;
 * Cauchy interlacing of the Ritz values;
 * the LCES worked example of Section 5.3.
 """
@@ -123,6 +126,51 @@ def test_ppca_output_in_span_orthonormal_and_top_eigs_of_projected_cov():
     # residual of the projected problem
     R = P @ C @ P @ E - E * (lam * n)[None, :]
     assert np.abs(R).max() < 1e-10 * lam[0] * n
+
+
+def _projected_problem_pin(finalize) -> bool:
+    """The pin above as a predicate on a pPCA-step implementation: output in
+    span(V), orthonormal, and the top-k eigenpairs of P_V X^T X P_V / n."""
+    X, V = _problem()
+    n, k = X.shape[0], 4
+    E, lam = finalize(X, V, k)
+    Q = oracle.orth(V)
+    P = Q @ Q.T
+    w_full, U_full = oracle.eigh_desc(P @ oracle.covariance(X) @ P)
+    return bool(np.allclose(E.T @ E, np.eye(k), atol=1e-12) and np.allclose(E - Q @ (Q.T @ E), 0.0, atol=1e-12)
+                and np.allclose(lam * n, w_full[:k], rtol=1e-10)
+                and all(oracle.angle(E[:, i], U_full[:, i]) < 1e-8 for i in range(k)))
+
+
+def _step_parts(X, V):
+    Q = oracle.orth(V)
+    Y = X @ Q
+    w, U = oracle.eigh_desc(Y.T @ Y)
+    return Q, w, U
+
+
+def test_planted_mistakes_in_the_ppca_step_fail_the_projected_problem_pin():
+    assert _projected_problem_pin(oracle.ppca_finalize)
+
+    def no_orthonormalisation(X, V, k):            # G from X V, rotation of V itself
+        Y = X @ V
+        w, U = oracle.eigh_desc(Y.T @ Y)
+        return oracle.sign_fix(V @ U[:, :k]), w[:k] / X.shape[0]
+
+    def transposed_rotation(X, V, k):              # E = Q U^T
+        Q, w, U = _step_parts(X, V)
+        return oracle.sign_fix(Q @ U.T[:, :k]), w[:k] / X.shape[0]
+
+    def eigenvalues_not_divided_by_n(X, V, k):
+        Q, w, U = _step_parts(X, V)
+        return oracle.sign_fix(Q @ U[:, :k]), w[:k]
+
+    def ascending_order(X, V, k):
+        Q, w, U = _step_parts(X, V)
+        return oracle.sign_fix(Q @ U[:, ::-1][:, :k]), w[::-1][:k] / X.shape[0]
+
+    for bad in (no_orthonormalisation, transposed_rotation, eigenvalues_not_divided_by_n, ascending_order):
+        assert not _projected_problem_pin(bad), bad.__name__
 
 
 def test_ppca_depends_only_on_span():

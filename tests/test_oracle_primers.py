@@ -9,7 +9,11 @@
 * convergence rate of simultaneous iteration (Rutishauser's bound);
 * ordered convergence: Sanger and EigenGame find the individual eigenvectors,
   not just the subspace -- and two planted mistakes (Oja's symmetric subspace
-  rule, EigenGame without the penalty) are shown to fail that pin.
+  rule, EigenGame without the penalty) are shown to fail that pin;
+* the sequential power method (Section 2.1): closed-form iterates on a 2 x 2
+  diagonal problem, the axes of a diagonal spectrum found in order, the stop
+  at the first step below eps -- with two planted mistakes (no deflation, the
+  stop test inverted) shown to fail the axes pin.
 """
 import math
 
@@ -227,6 +231,46 @@ def test_power_seq_finds_the_axes_of_a_diagonal_spectrum():
     assert np.abs(V.T @ V - np.eye(m)).max() < 1e-12
     # rate lam_{j+1}/lam_j = 1/2: about log2(1/eps) steps each
     assert all(30 <= s <= 60 for s in steps), steps
+
+
+def _power_seq_axes_pin(power_seq) -> bool:
+    """The pin above as a predicate on an implementation of the sequential power method."""
+    rng = np.random.default_rng(2)
+    d, m = 8, 4
+    X = np.diag(np.sqrt(2.0 ** -np.arange(d)))
+    V, steps = power_seq(X, rng.standard_normal((d, m)), 2000, 1e-12)
+    return bool(all(abs(abs(V[j, j]) - 1.0) < 1e-10 for j in range(m))
+                and np.abs(V.T @ V - np.eye(m)).max() < 1e-12 and all(30 <= s <= 60 for s in steps))
+
+
+def _power_seq_variant(X, V0, T, eps, deflate=True, stop_below=True):
+    """The sequential power method with switches that plant a mistake."""
+    Q0 = oracle.orth(V0)
+    d, m = Q0.shape
+    V, steps = np.zeros((d, m)), []
+    for j in range(m):
+        x, Vp, t = Q0[:, j].copy(), V[:, :j], 0
+        while t < T:
+            y = X.T @ (X @ x)
+            if deflate:
+                for _ in range(2):
+                    y = y - Vp @ (Vp.T @ y)
+            xn = y / np.linalg.norm(y)
+            t += 1
+            diff = np.linalg.norm(xn - x)
+            x = xn
+            if (diff < eps) if stop_below else (diff >= eps):
+                break
+        V[:, j] = x
+        steps.append(t)
+    return V, steps
+
+
+def test_planted_mistakes_in_power_seq_fail_the_axes_pin():
+    assert _power_seq_axes_pin(oracle.power_seq_prime)
+    assert _power_seq_axes_pin(_power_seq_variant)                       # switches off: the method
+    assert not _power_seq_axes_pin(lambda *a: _power_seq_variant(*a, deflate=False))
+    assert not _power_seq_axes_pin(lambda *a: _power_seq_variant(*a, stop_below=False))
 
 
 def test_power_seq_stops_at_the_first_step_below_eps():
