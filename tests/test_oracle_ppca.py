@@ -8,6 +8,9 @@
 * four planted mistakes in the step (no orthonormalisation, transposed
   rotation, eigenvalues not divided by n, ascending order) fail the
   projected-problem pin;
+* the row-sampled step: SplitMix64's published outputs, the selection rules,
+  and the support pin (data only inside the sample: eigenvalues scaled by
+  n/|S|; only outside: zero), which two planted mistakes fail;
 * Cauchy interlacing of the Ritz values;
 * the LCES worked example of Section 5.3.
 """
@@ -268,6 +271,44 @@ def test_ppca_finalize_rows_all_blocks_is_the_full_step():
     E0, l0 = oracle.ppca_finalize(X, V, k)
     np.testing.assert_allclose(l1, l0, rtol=1e-12)
     np.testing.assert_allclose(E1, E0, atol=1e-10)
+
+
+def _sample_support_pin(finalize_rows) -> bool:
+    """Data nonzero only inside the sampled blocks: the sampled step equals the
+    full step with eigenvalues scaled by n / |S| (same Gram matrix, other row
+    count); data nonzero only outside them: every sampled eigenvalue is 0."""
+    rng = np.random.default_rng(12)
+    n, d, m, k = 128 * 12 + 50, 9, 5, 3                   # ragged last block
+    tiles, rows = oracle.sampled_tiles(n, 0.3, 7)
+    inside = np.zeros(n, dtype=bool)
+    for t in tiles:
+        inside[t * 128:min((t + 1) * 128, n)] = True
+    X = rng.standard_normal((n, d)) * np.linspace(2.0, 0.4, d)
+    V = rng.standard_normal((d, m))
+    X_in, X_out = X * inside[:, None], X * (~inside)[:, None]
+    E_full, l_full = oracle.ppca_finalize(X_in, V, k)
+    E_s, l_s = finalize_rows(X_in, V, k, tiles)
+    _, l_zero = finalize_rows(X_out, V, k, tiles)
+    return bool(rows == inside.sum() and np.allclose(l_s, l_full * n / rows, rtol=1e-12)
+                and max(oracle.angle(E_s[:, i], E_full[:, i]) for i in range(k)) < 1e-9
+                and np.abs(l_zero).max() == 0.0)
+
+
+def test_ppca_finalize_rows_sees_exactly_the_sampled_blocks():
+    assert _sample_support_pin(oracle.ppca_finalize_rows)
+
+    def divides_by_n(X, V, k, tiles, tile=128):
+        E, lam = oracle.ppca_finalize_rows(X, V, k, tiles, tile)
+        rows = sum(min((t + 1) * tile, X.shape[0]) - t * tile for t in tiles)
+        return E, lam * rows / X.shape[0]
+
+    def ignores_the_sample(X, V, k, tiles, tile=128):
+        E, lam = oracle.ppca_finalize(X, V, k)
+        rows = sum(min((t + 1) * tile, X.shape[0]) - t * tile for t in tiles)
+        return E, lam * X.shape[0] / rows
+
+    for bad in (divides_by_n, ignores_the_sample):
+        assert not _sample_support_pin(bad), bad.__name__
 
 
 def test_ppca_finalize_rows_on_repeated_block_matches_full():
