@@ -111,6 +111,22 @@ def test_variance_restricted_to_S():
         assert math.isclose(oracle.variance_captured(Xt, v), oracle.variance_captured(X, v), rel_tol=1e-12)
 
 
+def test_variance_captured_closed_forms():
+    """An axis direction captures its column's sum of squares; an exact
+    eigenvector of X^T X captures its eigenvalue; the direction's length and
+    sign do not matter."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((40, 5))
+    for j in range(5):
+        e = np.zeros(5)
+        e[j] = 1.0
+        assert math.isclose(oracle.variance_captured(X, e), float((X[:, j] ** 2).sum()), rel_tol=1e-14)
+    sigma = np.array([3.0, 2.0, 0.5])
+    Xe, Q = synth.exact_spectrum_data(30, 3, sigma, seed=2)
+    for j in range(3):
+        assert math.isclose(oracle.variance_captured(Xe, -7.0 * Q[:, j]), sigma[j] ** 2, rel_tol=1e-12)
+
+
 def test_ppca_output_in_span_orthonormal_and_top_eigs_of_projected_cov():
     X, V = _problem()
     n, d = X.shape
