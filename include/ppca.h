@@ -112,17 +112,19 @@ typedef struct ppca_prime_params {
     double eps;               /* POWER_SEQ: termination threshold on |x_t - x_{t+1}|    */
 } ppca_prime_params;
 
-/* Library version, (major << 16) | minor. */
+/* Library version, (major << 16) | minor.  Infrastructure: no counterpart in the paper. */
 PPCA_API int32_t ppca_version(void);
 
-/* Message for the last non-OK status returned to the calling thread. */
+/* Message for the last non-OK status returned to the calling thread (infrastructure:
+ * no counterpart in the paper). */
 PPCA_API const char *ppca_last_error(void);
 
 /* Defaults: POWER -- nothing; OJA -- batch 256, lr 1, lr_offset 100 (so step t
  * uses 1/(t+100)); EIGENGAME -- batch 1024, lr 0.05, momentum 0.9; POWER_SEQ --
  * eps 1e-6.  Sets every
  * other field to zero / NULL.  Returns PPCA_ERR_INVALID for a NULL p or an
- * unknown method. */
+ * unknown method.  The momentum 0.9 is Section 5's; the paper tunes the rates
+ * per data set (Section 5), so the other values are the library's. */
 PPCA_API ppca_status ppca_prime_params_default(ppca_prime_params *p, ppca_method method);
 
 /*
@@ -141,11 +143,13 @@ PPCA_API ppca_status ppca_create(ppca_handle **out, const void *X, int64_t n, in
 /*
  * Optional second copy of the same data in a wider type (e.g. BF16 when X is
  * FP8) that ppca_finalize reads instead of X.  Same shape n x d; borrowed.
- * Pass NULL to remove it.
+ * Pass NULL to remove it.  Algorithm 1 reads one X throughout; this lets the
+ * priming (step 1) run on a narrower type than the pPCA step (steps 2-5).
  */
 PPCA_API ppca_status ppca_set_refine(ppca_handle *h, const void *X_refine, int64_t ld, ppca_dtype dtype);
 
-/* Cap the handle's workspace (bytes, 0 = no cap); exceeding it gives PPCA_ERR_OOM. */
+/* Cap the handle's workspace (bytes, 0 = no cap); exceeding it gives PPCA_ERR_OOM.
+ * Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_set_workspace_limit(ppca_handle *h, int64_t bytes);
 
 /*
@@ -174,7 +178,8 @@ PPCA_API ppca_status ppca_prime(ppca_handle *h, ppca_method method, int32_t m, i
 
 /*
  * Continue the current priming run for T more steps / iterations (same method
- * and parameters), so that pPCA can be evaluated along the priming trajectory.
+ * and parameters), so that pPCA can be evaluated along the priming trajectory
+ * (Section 5 evaluates it at checkpoints of one priming run).
  */
 PPCA_API ppca_status ppca_prime_continue(ppca_handle *h, int64_t T);
 
@@ -191,7 +196,8 @@ PPCA_API ppca_status ppca_finalize(ppca_handle *h, int32_t k, float *E, double *
                           ppca_precision precision);
 
 /*
- * Host-buffer entry points, for data that lives in host memory.  Both are
+ * Host-buffer entry points (Algorithm 1's input, and its steps 2-5), for data
+ * that lives in host memory.  Both are
  * stream-ordered on the handle's stream and asynchronous when the host buffers
  * are page-locked (cudaHostAlloc / cudaHostRegister); with pageable memory the
  * copies complete before the call returns.  Results are valid after ppca_sync.
@@ -242,11 +248,12 @@ PPCA_API ppca_status ppca_finalize_sampled(ppca_handle *h, int32_t k, float *E, 
 PPCA_API ppca_status ppca_variance_captured(ppca_handle *h, const float *E, int32_t k, double *var,
                                             ppca_precision precision);
 
-/* Device copy of the current primed basis V (d x m column-major FP32). */
+/* Device copy of the current primed basis V (d x m column-major FP32): the
+ * output of Algorithm 1, step 1. */
 PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
 
 /* Wait for the handle's stream; return the first device-side error, if any,
- * and clear it. */
+ * and clear it.  Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_sync(ppca_handle *h);
 
 /*
@@ -256,7 +263,8 @@ PPCA_API ppca_status ppca_sync(ppca_handle *h);
  * tile (or for one half of its columns, kparts = 2, the two halves summed in
  * FP32) while consumer pipelines, each owning a 256-column slice of Z for the
  * whole pass, re-read the tile from L2 for Z += X^T Y.  The unfused form runs
- * the two products as separate kernels (X read twice).
+ * the two products as separate kernels (X read twice).  An implementation
+ * choice of the product of Sections 2.1-2.3; no counterpart in the paper.
  */
 typedef struct ppca_schedule {
     int32_t fused;            /* 1: fused single-read pass; 0: two kernels; -1: library default */
@@ -279,7 +287,8 @@ typedef struct ppca_schedule {
                               /* evict_first (0: library default, what fits in 70 % of L2)        */
 } ppca_schedule;
 
-/* Set the X-pass schedule of a handle (takes effect at its next pass). */
+/* Set the X-pass schedule of a handle (takes effect at its next pass).
+ * Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
 
 /*
@@ -289,7 +298,7 @@ PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
  * or two kernels -- taking the fastest of `reps` timed runs after a warm-up
  * each, then set the winner on the handle and copy it to *best (may be NULL).
  * Uses the handle's scratch buffers (not the primed basis); blocks the host
- * until the handle's stream is idle.
+ * until the handle's stream is idle.  Infrastructure: no counterpart in the paper.
  */
 PPCA_API ppca_status ppca_autotune(ppca_handle *h, int32_t m, int64_t rows, int32_t reps, ppca_schedule *best);
 
@@ -303,22 +312,26 @@ typedef struct ppca_timing {
 } ppca_timing;
 
 /* enable != 0: record a CUDA event pair around every X-pass of this handle,
- * on its stream, and reset the counters; enable == 0: stop recording. */
+ * on its stream, and reset the counters; enable == 0: stop recording.
+ * Measurement infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_set_timing(ppca_handle *h, int32_t enable);
 
-/* Synchronise the handle's stream and report the counters since the reset. */
+/* Synchronise the handle's stream and report the counters since the reset
+ * (measurement infrastructure: no counterpart in the paper). */
 PPCA_API ppca_status ppca_get_timing(ppca_handle *h, ppca_timing *out);
 
 /*
  * Checkpoint of the priming state (basis, momentum, step counter, method and
  * parameters) to host memory.  With buf == NULL, *bytes receives the size
  * needed.  ppca_set_state restores it into a handle over the same (n, d).
- * Synchronises the handle's stream.
+ * Synchronises the handle's stream.  Section 5 evaluates pPCA at checkpoints of
+ * one priming run; this lets such a run stop and resume.
  */
 PPCA_API ppca_status ppca_get_state(ppca_handle *h, void *buf, int64_t *bytes);
 PPCA_API ppca_status ppca_set_state(ppca_handle *h, const void *buf, int64_t bytes);
 
-/* Free the handle and its workspace (after the stream's work completes). */
+/* Free the handle and its workspace (after the stream's work completes).
+ * Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_destroy(ppca_handle *h);
 
 /* ---------------------------------------------------------------------------
@@ -347,14 +360,16 @@ typedef struct ppca_batch ppca_batch;
  * Validate `count` instance descriptors (copied; the buffers they point to are
  * borrowed and must stay valid) and set up `slots` concurrent slots (0 = 8),
  * each with a workspace sized for the largest instance it runs.  No device
- * work is enqueued.
+ * work is enqueued.  Each instance is one Algorithm 1; the paper runs them one
+ * at a time, so the batching itself has no counterpart in the paper.
  */
 PPCA_API ppca_status ppca_batch_create(ppca_batch **out, const ppca_instance_desc *descs, int32_t count,
                                        int32_t slots, void *stream);
 
 /*
- * Run every instance: block power priming (T iterations, FAST precision)
- * then the pPCA step (ACCURATE), writing each instance's E and lambda.  The
+ * Run every instance: block power priming (Algorithm 1, step 1; T iterations,
+ * FAST precision) then the pPCA step (steps 2-5, ACCURATE), writing each
+ * instance's E and lambda.  The
  * first call captures the whole batch -- instances spread round-robin over
  * the slots' streams -- into a CUDA graph; every call launches that graph on
  * the batch's stream (asynchronous).
@@ -368,16 +383,20 @@ PPCA_API ppca_status ppca_batch_run(ppca_batch *b);
  * concurrently) times the candidates on the group's first instance, and every
  * instance of the group then runs with the winner.  Returns the number of
  * groups in *groups (may be NULL).  PPCA_ERR_STATE after the first run.
+ * Infrastructure: no counterpart in the paper.
  */
 PPCA_API ppca_status ppca_batch_autotune(ppca_batch *b, int32_t reps, int32_t *groups);
 
 /* Kernel launches one ppca_batch_run performs (the kernels captured in its graph;
- * 0 before the first run). */
+ * 0 before the first run).  Measurement infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_batch_kernel_count(const ppca_batch *b, int64_t *count);
 
-/* Wait for the batch's stream; report the first device-side error of any slot. */
+/* Wait for the batch's stream; report the first device-side error of any slot.
+ * Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_batch_sync(ppca_batch *b);
 
+/* Free the batch, its graph, streams and workspaces (after its work completes;
+ * NULL is a no-op).  Infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_batch_destroy(ppca_batch *b);
 
 /* ---------------------------------------------------------------------------
@@ -409,7 +428,8 @@ PPCA_API ppca_status ppca_xpass(ppca_handle *h, const float *V, int32_t m, int64
 
 /*
  * Orthonormalise the columns of V (d x m column-major, device) into Q (may
- * alias V): thin QR with positive diagonal by CholeskyQR2 -- G = V^T V, G = R^T R,
+ * alias V) -- Algorithm 1, step 2 (an orthonormal basis of span(V)), and the
+ * orth of Section 2.1's iteration: thin QR with positive diagonal by CholeskyQR2 -- G = V^T V, G = R^T R,
  * V <- V R^-1, twice.  G is accumulated in double-float FP32 (for d >= 16384 from
  * three BF16 pieces on the tensor cores); the first factorisation runs in FP32
  * on the diagonally scaled G and is redone in double-float when its
@@ -420,7 +440,7 @@ PPCA_API ppca_status ppca_xpass(ppca_handle *h, const float *V, int32_t m, int64
 PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *Q, int32_t m);
 
 /*
- * Symmetric eigensolve of an m x m FP64 matrix (the full-PCA of step 4):
+ * Symmetric eigensolve of an m x m FP64 matrix (the full PCA of Algorithm 1, step 4):
  * G (device, m x m, symmetric) -> w (device, m, descending) and U (device,
  * m x m column-major, column j = unit eigenvector of w[j], sign convention as
  * above).  1 <= m <= 128.  G is not modified.  Parallel-order two-sided Jacobi
@@ -432,9 +452,10 @@ PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *
 PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, double *w, double *U);
 
 /*
- * The same symmetric eigensolve as ppca_eigh, for callers that cannot allocate
- * device memory where they need it -- for example code that runs while its
- * stream is being captured into a CUDA graph, code on a latency-critical path
+ * The same symmetric eigensolve as ppca_eigh (Algorithm 1, step 4), for
+ * callers that cannot allocate device memory where they need it -- for
+ * example code that runs while its stream is being captured into a CUDA
+ * graph, code on a latency-critical path
  * that must not call cudaMalloc (which may synchronise the device), or a host
  * program whose device memory is handed out by its own allocator.  The paper
  * has no counterpart of this call; it exists for those callers only.
@@ -459,8 +480,9 @@ PPCA_API ppca_status ppca_eigh_noalloc(const double *G, int32_t m, double *w, do
                                        void *stream);
 
 /*
- * Data-format step: quantise FP32 rows (device, n x d, leading dimension ld_in)
- * to BF16 (round to nearest even) or to FP8 E4M3 with one scale per row,
+ * Data-format step (the storage types of the priming passes; the paper does not
+ * vary the data's precision, so this has no counterpart in the paper): quantise
+ * FP32 rows (device, n x d, leading dimension ld_in) to BF16 (round to nearest even) or to FP8 E4M3 with one scale per row,
  *   scale[r] = max_j |x[r][j]| / 448 (1 for an all-zero row),
  *   code[r][j] = E4M3_RNE(x[r][j] / scale[r])  (both divisions in FP32).
  * Outputs are device arrays with leading dimension ld_out.  stream as above.

@@ -121,3 +121,24 @@ def test_binding_constants_match_the_header_enums():
     assert len(values) == 18               # status 8, dtype 3, method 4, precision 3
     for name, v in values.items():
         assert getattr(P, name) == v, name
+
+
+def test_every_declaration_cites_its_passage_or_says_it_has_none():
+    """Each entry point's comment either cites the passage of the paper that
+    defines what it computes (Section, Algorithm or Eq.) or states that it has
+    no counterpart in the paper (library infrastructure)."""
+    lines = open(HEADER).read().split("\n")
+    missing, text = [], ""
+    for i, line in enumerate(lines):
+        m = re.match(r"PPCA_API\s+[\w\s\*]*?\b(ppca_\w+)\s*\(", line)
+        if not m:
+            continue
+        j, block = i - 1, []
+        while j >= 0 and not lines[j].startswith(("PPCA_API", "typedef", "}")):
+            block.append(lines[j])
+            j -= 1
+        if any(b.strip().startswith(("/*", "*")) for b in block):   # else: shares the previous comment
+            text = " ".join(block)
+        if not re.search(r"Section|Algorithm|Eq\.|no counterpart", text):
+            missing.append(m.group(1))
+    assert missing == [], missing
