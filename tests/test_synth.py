@@ -118,3 +118,28 @@ def test_initial_basis_is_seeded():
     assert a.shape == (30, 4)
     assert np.array_equal(a, synth.initial_basis(30, 4, 9))
     assert not np.array_equal(a, synth.initial_basis(30, 4, 10))
+
+
+def test_workload_configs_are_the_documented_ones():
+    """Shapes, spectra, primer settings and tolerances of the five workloads."""
+    C = synth.CONFIGS
+    c1, c2, c3, c4, c5 = (C[k] for k in ("power_fp32_4096x256", "primers_fp32_100000x1024",
+                                         "precision_bf16_1000000x4096", "batch512_fp32",
+                                         "largeD_bf16_50000x262144"))
+    i = np.arange(1, 4097, dtype=np.float64)
+    assert (c1.n, c1.d, c1.k, c1.l, c1.dtype, c1.primers["power"]["T"]) == (4096, 256, 8, 8, "f32", 10)
+    assert np.array_equal(c1.lam(), 0.9 ** i[:256])
+    assert (c2.n, c2.d, c2.k, c2.l, c2.dtype, c2.primers["power"]["T"]) == (100000, 1024, 32, 32, "f32", 20)
+    assert np.array_equal(c2.lam(), 1.0 / i[:1024])
+    oja, eg = c2.primers["oja"], c2.primers["eigengame"]
+    assert (oja["batch"], oja["epochs"], oja["lr0"], oja["lr_offset"]) == (256, 1, 1.0, 100.0)
+    assert (eg["steps"], eg["batch"], eg["momentum"]) == (200, 1024, 0.9)
+    assert (c3.n, c3.d, c3.k, c3.l, c3.dtype, c3.primers["power"]["T"]) == (1000000, 4096, 64, 64, "bf16", 15)
+    assert np.array_equal(c3.lam(), np.exp(-i / 50.0)) and (c3.eig_rtol, c3.angle_tol) == (1e-4, 1e-3)
+    assert c4.primers["power"]["T"] == 10
+    assert (c5.n, c5.d, c5.k, c5.l, c5.dtype) == (50000, 262144, 32, 32, "bf16")
+    eg5 = c5.primers["eigengame"]
+    assert (eg5["steps"], eg5["batch"], eg5["momentum"]) == (500, 4096, 0.9)
+    assert np.allclose(c5.lam()[:4], np.arange(1, 5) ** -1.5 + 1e-4, rtol=1e-15)
+    assert (c5.eig_rtol, c5.angle_tol) == (1e-3, 1e-2)
+    assert all(c.m == c.k + c.l for c in C.values())
