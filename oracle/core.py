@@ -42,7 +42,7 @@ __all__ = [
     "eigengame_gradients", "eigengame_step", "eigengame_prime",
     "angle", "angles", "lces", "principal_angles", "variance_captured",
     "splitmix64", "sampled_tiles", "ppca_finalize_rows",
-    "bf16_bits_to_f64", "e4m3_decode", "e4m3_encode_rne", "fp8_row_quantize",
+    "bf16_bits_to_f64", "bf16_round_rne", "e4m3_decode", "e4m3_encode_rne", "fp8_row_quantize",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -439,6 +439,23 @@ def bf16_bits_to_f64(bits):
     """bfloat16 bit patterns (uint16) -> exact float64 values."""
     b = np.asarray(bits, dtype=np.uint16).astype(np.uint32) << np.uint32(16)
     return b.view(np.float32).astype(np.float64)
+
+
+def bf16_round_rne(x):
+    """Values -> the nearest bfloat16 value (ties to even mantissa), as float64.
+
+    The input is first taken to FP32 (the precision the data-format step and
+    the tensor-core epilogues round from); the FP32 bit pattern is then rounded
+    at bit 16 to nearest, ties to the even BF16 mantissa.  Finite inputs only
+    (FP32 overflow to infinity is the caller's concern).
+    """
+    f = np.asarray(x, dtype=np.float64).astype(np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    keep = bits >> np.uint64(16)
+    rest = bits & np.uint64(0xFFFF)
+    up = (rest > np.uint64(0x8000)) | ((rest == np.uint64(0x8000)) & ((keep & np.uint64(1)) == np.uint64(1)))
+    keep = keep + up.astype(np.uint64)
+    return bf16_bits_to_f64(keep.astype(np.uint16))
 
 
 def _e4m3_table():

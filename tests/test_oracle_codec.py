@@ -74,3 +74,29 @@ def test_bf16_bits():
     assert v[0] == 1.0 and v[1] == -2.0 and v[2] == 3.140625
     assert v[3] == 2.0 ** -133
     assert v[4] == (2 - 2.0 ** -7) * 2.0 ** 127
+
+
+def test_bf16_round_landmarks_and_ties():
+    """1 + 2^-8 lies halfway between 1 and 1 + 2^-7: ties go to the even
+    mantissa (1); 1 + 3 * 2^-8 lies halfway between 1 + 2^-7 (odd) and
+    1 + 2^-6 (even); just above a tie rounds up; signs and zero pass through;
+    a carry out of the mantissa bumps the exponent."""
+    x = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -8 + 2.0 ** -20, -2.5, 0.0,
+                  2.0 - 2.0 ** -9, 3.0e38])
+    r = oracle.bf16_round_rne(x)
+    np.testing.assert_array_equal(r[:7], [1.0, 1.0, 1.0 + 2.0 ** -6, 1.0 + 2.0 ** -7, -2.5, 0.0, 2.0])
+    assert abs(r[7] - 3.0e38) <= 2.0 ** -8 * 3.0e38
+
+
+def test_bf16_round_matches_torch_library_conversion():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal(50000) * 10.0 ** rng.uniform(-30, 30, 50000)).astype(np.float32)
+    mine = oracle.bf16_round_rne(x)
+    lib = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(mine, lib)
+    # and the relative error bound of round to nearest with 8 significant bits, u = 2^-8
+    # (normal range: below 2^-126 BF16, like FP32, keeps fewer significant bits)
+    xn = x.astype(np.float64)
+    normal = np.isfinite(xn) & (np.abs(xn) >= 2.0 ** -126) & (np.abs(xn) < 3.0e38)
+    assert np.all(np.abs(mine - xn)[normal] <= 2.0 ** -8 * np.abs(xn[normal]))

@@ -7,6 +7,10 @@
   rule (Section 2.2); EigenGame with one player is gradient ascent on
   v^T M v (Eq. 1);
 * convergence rate of simultaneous iteration (Rutishauser's bound);
+* EigenGame's step (Section 5: SGD with Nesterov momentum, on the tangent
+  space) against torch autograd of Eq. 3 and torch.optim.SGD(nesterov=True),
+  with heavy-ball momentum and a missing tangent projection planted as
+  mistakes that fail it;
 * ordered convergence: Sanger and EigenGame find the individual eigenvectors,
   not just the subspace -- and two planted mistakes (Oja's symmetric subspace
   rule, EigenGame without the penalty) are shown to fail that pin;
@@ -202,6 +206,90 @@ def _no_penalty(Xb, V):
 def test_planted_mistake_in_eigengame_fails_the_ordering_pin():
     X, Q, lam = small_problem(n=2000, d=8, seed=12)
     assert _ordered_convergence_eg(_no_penalty, X, Q, 3) > 0.1
+
+
+def _library_eigengame_steps(X, V0, b, steps, lr, momentum):
+    """The same parallel EigenGame steps, built from library parts only: the
+    Euclidean gradient of each player's utility (Eq. 3, the other players held
+    fixed) from torch autograd, its projection on the tangent space of the
+    player's sphere, torch.optim.SGD with Nesterov momentum (ascent: the
+    optimiser descends -U), then each column renormalised."""
+    import torch
+    Vt = torch.tensor(oracle.orth(V0), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.SGD([Vt], lr=lr, momentum=momentum, nesterov=True)
+    Xt = torch.tensor(X, dtype=torch.float64)
+    m = V0.shape[1]
+    for t in range(steps):
+        r0, r1 = oracle.minibatch_rows(t, X.shape[0], b)
+        Xb = Xt[r0:r1]
+        M = Xb.T @ Xb / (r1 - r0)
+        fixed = Vt.detach()
+        total = 0.0
+        for j in range(m):
+            vj = Vt[:, j]
+            u = vj @ M @ vj
+            for i in range(j):
+                vi = fixed[:, i]
+                u = u - (vj @ M @ vi) ** 2 / (vi @ M @ vi)
+            total = total + u
+        opt.zero_grad()
+        (-total).backward()
+        with torch.no_grad():
+            g = Vt.grad
+            g -= Vt * (Vt * g).sum(dim=0, keepdim=True)        # tangent projection of the gradient
+        opt.step()
+        with torch.no_grad():
+            Vt /= Vt.norm(dim=0, keepdim=True)
+    return Vt.detach().numpy()
+
+
+def test_eigengame_nesterov_step_matches_library_sgd():
+    """Section 5 trains with SGD and Nesterov momentum 0.9.  Away from the
+    fixed point (g != 0) three steps of the oracle equal three steps assembled
+    from torch autograd and torch.optim.SGD(nesterov=True) to 1e-12."""
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((300, 7)) * np.linspace(2.0, 0.3, 7)[None, :]
+    V0 = rng.standard_normal((7, 4))
+    Vo = oracle.eigengame_prime(X, V0, b=100, steps=3, lr=0.05, momentum=0.9)
+    Vl = _library_eigengame_steps(X, V0, b=100, steps=3, lr=0.05, momentum=0.9)
+    assert np.abs(Vo - oracle.orth(V0)).max() > 1e-2          # the steps really move the basis
+    np.testing.assert_allclose(Vo, Vl, rtol=0, atol=1e-12)
+
+
+def _heavy_ball_step(X, V, buf, t, b, lr, momentum=0.9):
+    """Planted mistake: heavy-ball momentum (v <- v + lr buf) instead of Nesterov."""
+    r0, r1 = oracle.minibatch_rows(t, X.shape[0], b)
+    grad, _, _ = oracle.eigengame_gradients(X[r0:r1], V)
+    g = grad - V * np.sum(V * grad, axis=0, keepdims=True)
+    buf = momentum * buf + g
+    Vn = V + lr * buf
+    return Vn / np.linalg.norm(Vn, axis=0, keepdims=True), buf
+
+
+def _unprojected_step(X, V, buf, t, b, lr, momentum=0.9):
+    """Planted mistake: the Euclidean gradient, no tangent projection."""
+    r0, r1 = oracle.minibatch_rows(t, X.shape[0], b)
+    g, _, _ = oracle.eigengame_gradients(X[r0:r1], V)
+    buf = momentum * buf + g
+    Vn = V + lr * (g + momentum * buf)
+    return Vn / np.linalg.norm(Vn, axis=0, keepdims=True), buf
+
+
+@pytest.mark.parametrize("planted", [_heavy_ball_step, _unprojected_step])
+def test_planted_mistake_in_eigengame_step_fails_the_library_pin(planted):
+    pytest.importorskip("torch")
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((300, 7)) * np.linspace(2.0, 0.3, 7)[None, :]
+    V0 = rng.standard_normal((7, 4))
+    saved = core.eigengame_step
+    core.eigengame_step = planted
+    try:
+        Vo = oracle.eigengame_prime(X, V0, b=100, steps=3, lr=0.05, momentum=0.9)
+    finally:
+        core.eigengame_step = saved
+    Vl = _library_eigengame_steps(X, V0, b=100, steps=3, lr=0.05, momentum=0.9)
+    assert np.abs(Vo - Vl).max() > 1e-6
 
 
 # --- sequential power method with epsilon termination (Section 2.1) ---
