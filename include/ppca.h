@@ -292,6 +292,18 @@ typedef struct ppca_schedule {
 PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
 
 /*
+ * Limit of every bounded wait inside the library's tensor-core kernels on the
+ * current device, in nanoseconds (0 restores the default, 2 s; at most 60 s).
+ * A wait that runs out sets the handle's device status word to a timeout, the
+ * kernel drains its copies and MMAs in flight, frees its tensor memory and
+ * returns; the next synchronising call returns PPCA_ERR_TIMEOUT and clears the
+ * word, and the handle stays usable.  The limit is a device-wide setting that
+ * holds for later launches until changed; set it while no pass is running.
+ * Infrastructure (fault detection): no counterpart in the paper.
+ */
+PPCA_API ppca_status ppca_set_wait_limit(uint64_t ns);
+
+/*
  * Autotuner: time one fast X-pass over rows [0, rows) of the handle's data
  * (rows = 0: all n) with m directions for every candidate schedule -- engine
  * (tensor cores / CUDA cores) and, for BF16 data, the fused single-read pass
@@ -452,13 +464,12 @@ PPCA_API ppca_status ppca_orthonormalize(ppca_handle *h, const float *V, float *
 PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, double *w, double *U);
 
 /*
- * The same symmetric eigensolve as ppca_eigh (Algorithm 1, step 4), for
- * callers that cannot allocate device memory where they need it -- for
- * example code that runs while its stream is being captured into a CUDA
- * graph, code on a latency-critical path
- * that must not call cudaMalloc (which may synchronise the device), or a host
- * program whose device memory is handed out by its own allocator.  The paper
- * has no counterpart of this call; it exists for those callers only.
+ * The same symmetric eigensolve as ppca_eigh, for callers that cannot
+ * allocate device memory at the point where they need it: a host program
+ * whose device memory is handed out by its own allocator (a fixed budget
+ * carved up front), or code on a latency-critical path where a cudaMalloc,
+ * which may synchronise the device, is not acceptable.  This call has
+ * no counterpart in the paper; it exists for those callers only.
  *
  * It takes no handle and allocates nothing: its scratch is a fixed array of
  * 256 KiB in the library's device memory, which every device that loads the
@@ -471,10 +482,12 @@ PPCA_API ppca_status ppca_eigh(ppca_handle *h, const double *G, int32_t m, doubl
  *           their cap (left unchanged otherwise); the caller clears it
  *   stream  cudaStream_t (as void*) the solve is enqueued on
  * The first call on a device looks up the device address of the scratch array
- * (with that device current); make that first call before any stream capture.
- * Every call on a device shares the one array and leaves its contents behind,
- * so calls that overlap on the same GPU race: order them (one stream, or
- * events).  The outputs are identical to ppca_eigh's for the same input.
+ * (with that device current) and caches it for the process; make that first
+ * call before any stream capture.  A cudaDeviceReset after that first call is
+ * not supported (the cached address would be stale).  Every call on a device
+ * shares the one array and leaves its contents behind, so calls that overlap
+ * on the same GPU race: order them (one stream, or events).  It runs the same
+ * kernels as ppca_eigh, so its outputs equal ppca_eigh's bit for bit.
  */
 PPCA_API ppca_status ppca_eigh_noalloc(const double *G, int32_t m, double *w, double *U, int *status,
                                        void *stream);

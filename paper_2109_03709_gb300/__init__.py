@@ -28,7 +28,8 @@ __all__ = [
     "ppca_eigh", "ppca_quantize_bf16", "ppca_quantize_fp8", "ppca_set_timing", "ppca_get_timing",
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
-    "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "EXPORTED_SYMBOLS",
+    "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "ppca_set_wait_limit",
+    "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -52,6 +53,7 @@ EXPORTED_SYMBOLS = [
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured",
+    "ppca_set_wait_limit",
 ]
 
 
@@ -153,6 +155,7 @@ _SIGS = {
     "ppca_get_timing": (_c_status, [_vp, ctypes.POINTER(ppca_timing)]),
     "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "ppca_set_schedule": (_c_status, [_vp, ctypes.POINTER(ppca_schedule)]),
+    "ppca_set_wait_limit": (_c_status, [ctypes.c_uint64]),
     "ppca_autotune": (_c_status, [_vp, _i32, _i64, _i32, ctypes.POINTER(ppca_schedule)]),
     "ppca_batch_autotune": (_c_status, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ppca_batch_create": (_c_status, [ctypes.POINTER(_vp), ctypes.POINTER(ppca_instance_desc), _i32, _i32, _vp]),
@@ -388,7 +391,24 @@ def ppca_orthonormalize(h: Handle, V, Q, m: int):
     _check(load_library().ppca_orthonormalize(h.ptr, _dev(V, "V", 4), _dev(Q, "Q", 4), m), "ppca_orthonormalize")
 
 
+def _need(t, count: int, what: str):
+    """Refuse a tensor holding fewer than `count` elements (a kernel would run past its end)."""
+    if t is not None and not isinstance(t, int) and t.numel() < count:
+        raise ValueError(f"{what} holds {t.numel()} elements, the call needs {count}")
+
+
+def _on_current_device(t, what: str):
+    """Refuse a CUDA tensor that lives on another GPU than the current one."""
+    if t is not None and not isinstance(t, int) and t.is_cuda:
+        import torch
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{what} is on cuda:{t.device.index}, the current device is "
+                             f"cuda:{torch.cuda.current_device()}")
+
+
 def ppca_eigh(h: Handle, G, m: int, w, U):
+    for t, c, what in ((G, m * m, "G"), (U, m * m, "U"), (w, m, "w")):
+        _need(t, c, what)
     _check(load_library().ppca_eigh(h.ptr, _dev(G, "G", 8), m, _dev(w, "w", 8), _dev(U, "U", 8)), "ppca_eigh")
 
 
@@ -467,6 +487,11 @@ def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: in
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
 
 
+def ppca_set_wait_limit(ns: int = 0):
+    """Limit (ns) of the bounded waits in the tensor-core kernels on the current device; 0 restores 2 s."""
+    _check(load_library().ppca_set_wait_limit(int(ns)), "ppca_set_wait_limit")
+
+
 def ppca_autotune(h: Handle, m: int, rows: int = 0, reps: int = 3) -> ppca_schedule:
     """Time the candidate fast-pass schedules on the handle's data; the fastest is set and returned."""
     best = ppca_schedule()
@@ -477,10 +502,18 @@ def ppca_autotune(h: Handle, m: int, rows: int = 0, reps: int = 3) -> ppca_sched
 def ppca_eigh_noalloc(G, m: int, w, U, status=None, stream=None):
     """Eigensolve without any device allocation (fixed library scratch, m <= 128).
 
-    For callers that cannot allocate device memory where they solve (e.g. while
-    capturing a CUDA graph); calls that overlap on the same GPU race on the
-    shared scratch and must be ordered by the caller.
+    For callers that cannot allocate device memory at the point where they
+    solve (a host program whose device memory is handed out by its own
+    allocator, or a latency-critical path where cudaMalloc may synchronise the
+    device); calls that overlap on the same GPU race on the shared scratch and
+    must be ordered by the caller.  Tensor arguments are refused here when they
+    are too small for m or live on another GPU than the current one (the
+    scratch array used is the current device's).
     """
+    for t, c, what in ((G, m * m, "G"), (U, m * m, "U"), (w, m, "w"), (status, 1, "status")):
+        _need(t, c, what)
+    for t, what in ((G, "G"), (w, "w"), (U, "U"), (status, "status")):
+        _on_current_device(t, what)
     _check(load_library().ppca_eigh_noalloc(_dev(G, "G", 8), m, _dev(w, "w", 8), _dev(U, "U", 8),
                                             _dev(status, "status", 4), _stream_ptr(stream)),
            "ppca_eigh_noalloc")

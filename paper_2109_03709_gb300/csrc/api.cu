@@ -722,6 +722,13 @@ ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     return PPCA_OK;
 }
 
+ppca_status ppca_set_wait_limit(uint64_t ns) {
+    if (ns > 60ull * 1000000000ull) return fail(PPCA_ERR_INVALID, "wait limit %llu ns above 60 s", (unsigned long long)ns);
+    CUDA_TRY(pass_tc_set_wait_limit(ns));
+    CUDA_TRY(pass_gram_set_wait_limit(ns));
+    return PPCA_OK;
+}
+
 namespace {
 
 ppca_schedule to_abi(const TcSchedule& t) {

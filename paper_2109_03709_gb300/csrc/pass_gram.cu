@@ -47,6 +47,7 @@ constexpr int kGSmemBudget = 200 * 1024;
 struct GHeader {
     uint64_t full[kGMaxStages], xform[kGMaxStages], empty[kGMaxStages];
     uint64_t tfull[2], tempty[2];
+    uint64_t drain;                 // the MMA thread's completion barrier after an abort
     uint32_t tmem_base;
     int abort;
     int xform_go;
@@ -74,6 +75,7 @@ __device__ inline void g_prologue(GHeader* hd, int stages, uint32_t tmem_cols, c
             tc::mbar_init(&hd->tfull[i], 1);
             tc::mbar_init(&hd->tempty[i], 128);
         }
+        tc::mbar_init(&hd->drain, 1);
         hd->abort = 0;
         hd->xform_go = 0;
         tc::mbar_init_fence();
@@ -86,7 +88,9 @@ __device__ inline void g_prologue(GHeader* hd, int stages, uint32_t tmem_cols, c
     tc::fence_after_sync();
 }
 
-__device__ inline void g_teardown(GHeader* hd, uint32_t tmem_cols) {
+// After an abort the MMA thread (warp 1, lane 0) first waits for its MMAs.
+__device__ inline void g_teardown(GHeader* hd, uint32_t tmem_cols, int* status) {
+    if (threadIdx.x == 32 && *(volatile int*)&hd->abort) tc::drain_mmas(&hd->drain, status);
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x / 32 == 1) {
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
             }
         }
     }
-    g_teardown(hd, tmem_cols);
+    g_teardown(hd, tmem_cols, status);
 }
 
 // ---------------------------------------------------------------- G = Y^T Y
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
             tc::mbar_arrive(&hd->tempty[b]);
         }
     }
-    g_teardown(hd, tmem_cols);
+    g_teardown(hd, tmem_cols, status);
 }
 
 // G[i][j] = (sum_p part_p[i][j] + sum_p part_p[j][i]) / 2 in FP64.
@@ -612,5 +616,7 @@ cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, cons
     gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G, Gf);
     return cudaGetLastError();
 }
+
+cudaError_t pass_gram_set_wait_limit(uint64_t ns) { return tc::set_wait_limit(ns); }
 
 }  // namespace ppca

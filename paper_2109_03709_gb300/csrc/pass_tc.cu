@@ -49,6 +49,7 @@ struct SmemHeader {
     uint64_t empty[kMaxStages];
     uint64_t tfull[2];
     uint64_t tempty[2];
+    uint64_t drain;                 // the MMA thread's completion barrier after an abort
     uint32_t tmem_base;
     int abort;
 };
@@ -92,6 +93,7 @@ __device__ inline void tc_prologue(SmemHeader* hd, int stages, uint32_t tmem_col
             tc::mbar_init(&hd->tfull[i], 1);
             tc::mbar_init(&hd->tempty[i], 128);
         }
+        tc::mbar_init(&hd->drain, 1);
         hd->abort = 0;
         tc::mbar_init_fence();
         tc::tma_prefetch(m0);
@@ -103,7 +105,9 @@ __device__ inline void tc_prologue(SmemHeader* hd, int stages, uint32_t tmem_col
     tc::fence_after_sync();
 }
 
-__device__ inline void tc_epilogue_teardown(SmemHeader* hd, uint32_t tmem_cols) {
+// After an abort the MMA thread (warp 1, lane 0) first waits for its MMAs.
+__device__ inline void tc_epilogue_teardown(SmemHeader* hd, uint32_t tmem_cols, int* status) {
+    if (threadIdx.x == 32 && *(volatile int*)&hd->abort) tc::drain_mmas(&hd->drain, status);
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x / 32 == 1) {
@@ -317,7 +321,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
             }
         }
     }
-    tc_epilogue_teardown(hd, tmem_cols);
+    tc_epilogue_teardown(hd, tmem_cols, status);
 }
 
 // ---------------------------------------------------------------- Z = X^T Y
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
             }
         }
     }
-    tc_epilogue_teardown(hd, tmem_cols);
+    tc_epilogue_teardown(hd, tmem_cols, status);
 }
 
 // ---------------------------------------------------------------- fused single-read pass
@@ -520,6 +524,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
 struct FusedHeader {
     uint64_t pfull[kMaxStages], pempty[kMaxStages], ptfull[2], ptempty[2];
     uint64_t cfull[kMaxStages], cempty[kMaxStages], ctfull, ctempty;
+    uint64_t pdrain, cdrain;        // the two MMA threads' completion barriers after an abort
     uint32_t tmem_base;
     int abort;
 };
@@ -560,6 +565,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
         }
         tc::mbar_init(&hd->ctfull, 1);
         tc::mbar_init(&hd->ctempty, 128);
+        tc::mbar_init(&hd->pdrain, 1);
+        tc::mbar_init(&hd->cdrain, 1);
         hd->abort = 0;
         tc::mbar_init_fence();
         tc::tma_prefetch(&tmXa);
@@ -833,6 +840,11 @@ __global__ void __launch_bounds__(kFusedThreads, 1)
             }
         }
     }
+    // after an abort each MMA thread (producer: warp 1, consumer: warp 7) waits for its MMAs
+    if (lane == 0 && *abort_flag) {
+        if (warp == 1 && producer) tc::drain_mmas(&hd->pdrain, status);
+        if (warp == 7 && consumer) tc::drain_mmas(&hd->cdrain, status);
+    }
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) {
@@ -857,6 +869,7 @@ constexpr int kBK32 = 32;               // K extent of one stage (32 FP32 = 128 
 struct F32Header {
     uint64_t full[kMaxStages], xform[kMaxStages], empty[kMaxStages];
     uint64_t tfull[2], tempty[2];
+    uint64_t drain;                 // the MMA thread's completion barrier after an abort
     uint32_t tmem_base;
     int abort;
 };
@@ -874,6 +887,7 @@ __device__ inline void f32_prologue(F32Header* hd, int stages, uint32_t tmem_col
             tc::mbar_init(&hd->tfull[i], 1);
             tc::mbar_init(&hd->tempty[i], 128);
         }
+        tc::mbar_init(&hd->drain, 1);
         hd->abort = 0;
         tc::mbar_init_fence();
         tc::tma_prefetch(m0);
@@ -885,7 +899,9 @@ __device__ inline void f32_prologue(F32Header* hd, int stages, uint32_t tmem_col
     tc::fence_after_sync();
 }
 
-__device__ inline void f32_teardown(F32Header* hd, uint32_t tmem_cols) {
+// After an abort the MMA thread (warp 1, lane 0) first waits for its MMAs.
+__device__ inline void f32_teardown(F32Header* hd, uint32_t tmem_cols, int* status) {
+    if (threadIdx.x == 32 && *(volatile int*)&hd->abort) tc::drain_mmas(&hd->drain, status);
     tc::fence_before_sync();
     __syncthreads();
     if (threadIdx.x / 32 == 1) {
@@ -1032,7 +1048,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             if (!ok) break;
         }
     }
-    f32_teardown(hd, tmem_cols);
+    f32_teardown(hd, tmem_cols, status);
 }
 
 // Z = X^T Y for FP32 X.  Stage: [raw X 4 x (32 x 32) 16 KB][A head 16 KB][A residual 16 KB][Y head][Y residual].
@@ -1193,7 +1209,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             }
         }
     }
-    f32_teardown(hd, tmem_cols);
+    f32_teardown(hd, tmem_cols, status);
 }
 
 // V (d x m column-major FP32) -> TF32 head and FP32 residual, [2][m_pad][ldv4], zero padded.
@@ -1644,5 +1660,7 @@ cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t 
     if (fuse) return run_fused(x, V, m, r0, r1, Z, s, sched, status, num_sms, st);
     return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
 }
+
+cudaError_t pass_tc_set_wait_limit(uint64_t ns) { return tc::set_wait_limit(ns); }
 
 }  // namespace ppca

@@ -45,6 +45,10 @@ cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, cons
 cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, const int* tile_row, int nsel, double* G,
                                      ppca_precision prec, int flush, const TcPassScratch& s, int* status,
                                      int num_sms, cudaStream_t st);
+// Limit of the bounded device waits of the tensor-core kernels on the current
+// device (ns = 0: the default 2 s), one setter per translation unit.
+cudaError_t pass_tc_set_wait_limit(uint64_t ns);
+cudaError_t pass_gram_set_wait_limit(uint64_t ns);
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
                      const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st);
 

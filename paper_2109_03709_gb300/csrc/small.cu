@@ -1314,10 +1314,10 @@ cudaError_t eigh_small(const double* G, int m, double* w, double* U, void* scrat
 
 // ---------------------------------------------------------------------------
 // Allocation-free eigensolve.  Some callers cannot allocate device memory at
-// the point where they need the small eigensolve: code running while a stream
-// is being captured into a CUDA graph, code on a latency-critical path where a
-// cudaMalloc (which may synchronise the device) is not acceptable, or hosts
-// whose memory is handed out by their own allocator.  For them the solve's
+// the point where they need the small eigensolve: code on a latency-critical
+// path where a cudaMalloc (which may synchronise the device) is not
+// acceptable, or hosts whose device memory is handed out by their own
+// allocator.  For them the solve's
 // scratch is one file-scope device array, sized for the largest m (128), that
 // every device loading this library keeps until the process exits (each device
 // has its own copy).  On one device the array is shared by all calls: calls
@@ -1335,7 +1335,9 @@ cudaError_t eigh_small_noalloc(const double* G, int m, double* w, double* U, int
     if (m < 1 || m > kMaxM || jacobi_scratch_bytes(m) > kEighNoallocScratchBytes) return cudaErrorInvalidValue;
     // Set-up, once per device and with that device current: host code may not
     // use g_eigh_scratch directly (its host-side name is only a stand-in), so
-    // the device address is looked up and cached.
+    // the device address is looked up and cached for the process (a
+    // cudaDeviceReset after the first call is not supported: the cached
+    // address would be stale).
     static std::mutex mu;
     static void* addr[64] = {};
     int dev = 0;

@@ -50,15 +50,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Limit of every bounded wait that does not name its own (2 s unless set
+// with set_wait_limit; one copy per translation unit and device).
+static __device__ uint64_t g_wait_limit_ns = 2000000000ull;
+
+// Host side: set this translation unit's wait limit on the current device
+// (ns = 0 restores 2 s).
+static inline cudaError_t set_wait_limit(uint64_t ns) {
+    const uint64_t v = ns ? ns : 2000000000ull;
+    return cudaMemcpyToSymbol(g_wait_limit_ns, &v, sizeof v);
+}
+
 // Bounded wait for the phase of parity `parity` to complete.  Returns false
-// (and records kDevWaitTimeout) if it did not within `limit_ns`.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status,
-                                          uint64_t limit_ns = 2000000000ull) {
+// (and records kDevWaitTimeout) if it did not within `limit_ns` (0: the
+// translation unit's wait limit).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* status, uint64_t limit_ns = 0) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer_ns();
+    const uint64_t lim = limit_ns ? limit_ns : *(volatile uint64_t*)&g_wait_limit_ns;
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > limit_ns) {
+        if (globaltimer_ns() - t0 > lim) {
             set_status(status, kDevWaitTimeout);
             return false;
         }
@@ -138,15 +150,16 @@ __device__ __forceinline__ void named_barrier(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
-// Bounded spin until *p >= target (acquire); false (and kDevWaitTimeout) after limit_ns.
-__device__ __forceinline__ bool wait_flag_geq(const int* p, int target, int* status,
-                                              uint64_t limit_ns = 2000000000ull) {
+// Bounded spin until *p >= target (acquire); false (and kDevWaitTimeout) after
+// limit_ns (0: the translation unit's wait limit).
+__device__ __forceinline__ bool wait_flag_geq(const int* p, int target, int* status, uint64_t limit_ns = 0) {
     if (ld_acquire_gpu(p) >= target) return true;
     const uint64_t t0 = globaltimer_ns();
+    const uint64_t lim = limit_ns ? limit_ns : *(volatile uint64_t*)&g_wait_limit_ns;
     while (true) {
         __nanosleep(64);
         if (ld_acquire_gpu(p) >= target) return true;
-        if (globaltimer_ns() - t0 > limit_ns) {
+        if (globaltimer_ns() - t0 > lim) {
             set_status(status, kDevWaitTimeout);
             return false;
         }
@@ -214,6 +227,14 @@ __device__ __forceinline__ void fence_proxy_async_shared() {
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+
+// After an abort: wait (bounded, 100 ms) until every MMA this thread issued
+// has completed, so that TMEM is never freed under a running MMA.  `bar` is
+// an mbarrier (count 1) used for nothing else.
+__device__ __forceinline__ void drain_mmas(uint64_t* bar, int* status) {
+    mma_commit(bar);
+    mbar_wait(bar, 0u, status, 100000000ull);
 }
 
 // 32 lanes x 32 consecutive 32-bit columns: thread (lane) i gets row i.

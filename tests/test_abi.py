@@ -142,3 +142,9 @@ def test_every_declaration_cites_its_passage_or_says_it_has_none():
         if not re.search(r"Section|Algorithm|Eq\.|no counterpart", text):
             missing.append(m.group(1))
     assert missing == [], missing
+
+
+def test_wait_limit_above_a_minute_is_refused(lib):
+    """ppca_set_wait_limit validates its argument before any CUDA call."""
+    import paper_2109_03709_gb300 as P
+    assert lib.ppca_set_wait_limit(61 * 10 ** 9) == P.PPCA_ERR_INVALID

@@ -67,3 +67,22 @@ def test_addresses_and_none_pass_through(P):
     with pytest.raises(ValueError, match="contiguous"):
         P._host(torch.empty((4, 4)).t(), "t", 4)
     assert P._host(torch.empty((4, 4))[:, :2], "t", 4, contiguous=False) is not None
+
+
+def test_undersized_tensors_are_refused_for_the_eigensolves(P):
+    """G and U must hold m*m values, w m and status one: a kernel given a smaller
+    tensor would read or write past its end.  The sizes are checked before
+    anything else, so host tensors show it here without a GPU."""
+    h = P.Handle(0, [])
+    f64 = dict(dtype=torch.float64)
+    m = 4
+    ok = dict(G=torch.empty(m * m, **f64), w=torch.empty(m, **f64), U=torch.empty(m * m, **f64))
+    for bad, small in (("G", torch.empty(m * m - 1, **f64)), ("U", torch.empty(m * m - 1, **f64)),
+                       ("w", torch.empty(m - 1, **f64))):
+        args = dict(ok, **{bad: small})
+        with pytest.raises(ValueError, match=f"{bad} holds"):
+            P.ppca_eigh_noalloc(args["G"], m, args["w"], args["U"])
+        with pytest.raises(ValueError, match=f"{bad} holds"):
+            P.ppca_eigh(h, args["G"], m, args["w"], args["U"])
+    with pytest.raises(ValueError, match="status holds"):
+        P.ppca_eigh_noalloc(ok["G"], m, ok["w"], ok["U"], status=torch.empty(0, dtype=torch.int32))

@@ -1,14 +1,20 @@
-"""The allocation-free eigensolve agrees with the handle-based one.
+"""The allocation-free eigensolve agrees with the handle-based one and with the oracle.
 
 ppca_eigh_noalloc serves callers that cannot allocate device memory where they
-need the small eigensolve (inside a stream capture, on a path where cudaMalloc
-is not acceptable, under a host-owned allocator): its scratch is a fixed
-library array instead of a handle's workspace.  This file is collected last on
-purpose, so that a run stopping at the first failure has run every other test
-before it; it also passes alone in a fresh process.
+need the small eigensolve (a host program whose device memory comes from its
+own allocator, or a latency-critical path where cudaMalloc is not acceptable):
+its scratch is a fixed library array instead of a handle's workspace.  This
+file is collected last on purpose, so that a run stopping at the first failure
+has run every other test before it; it also passes alone in a fresh process.
 
-Tolerances are those of the eigensolver's own test: eigenvalues within 1e-9
-relative, vectors within the FP32-Jacobi angle bound 16 u |G| / gap.
+Checks, on two calls in a row (the second reuses the array the first left
+behind, with a smaller m):
+* the outputs equal ppca_eigh's bit for bit (the same kernels run on the same
+  input; only the scratch differs);
+* against the oracle's FP64 cyclic Jacobi (oracle.eigh_desc): eigenvalues
+  within 1e-9 relative (FP64 Rayleigh quotients of FP32 vectors), vectors
+  within the FP32-Jacobi angle bound 16 u |G| / gap (u = 2^-24);
+* the status word stays 0 on these well-conditioned inputs.
 """
 import numpy as np
 import pytest
@@ -27,7 +33,7 @@ def spd(m, seed):
     return 0.5 * (G + G.T)
 
 
-def test_noalloc_matches_handle_eigh_twice_in_a_row(cuda_device):
+def test_noalloc_matches_handle_eigh_and_oracle_twice_in_a_row(cuda_device):
     import torch
 
     import oracle
@@ -47,13 +53,14 @@ def test_noalloc_matches_handle_eigh_twice_in_a_row(cuda_device):
         U1 = torch.full((m, m), float("nan"), dtype=torch.float64, device="cuda")
         P.ppca_eigh_noalloc(Gd, m, w1, U1, status)
         torch.cuda.synchronize()
-        assert int(status.item()) == 0
-        w0n, w1n = w0.cpu().numpy(), w1.cpu().numpy()
-        U0n, U1n = U0.cpu().numpy().T, U1.cpu().numpy().T
-        np.testing.assert_allclose(w1n, w0n, rtol=1e-9, atol=1e-9 * abs(w0n[0]))
-        gaps = np.minimum(np.abs(np.diff(np.r_[np.inf, w0n])), np.abs(np.diff(np.r_[w0n, -np.inf])))
+        assert int(status.item()) == 0, call
+        assert torch.equal(w1, w0) and torch.equal(U1, U0), call
+        w1n, U1n = w1.cpu().numpy(), U1.cpu().numpy().T
+        wref, Uref = oracle.eigh_desc(G)
+        np.testing.assert_allclose(w1n, wref, rtol=1e-9, atol=1e-9 * abs(wref[0]))
+        gaps = np.minimum(np.abs(np.diff(np.r_[np.inf, wref])), np.abs(np.diff(np.r_[wref, -np.inf])))
         for i in range(m):
-            assert oracle.angle(U1n[:, i], U0n[:, i]) <= 16 * u * w0n[0] / gaps[i] + 1e-6, (call, i)
+            assert oracle.angle(U1n[:, i], Uref[:, i]) <= 16 * u * wref[0] / gaps[i] + 1e-6, (call, i)
 
 
 def test_noalloc_rejects_m_beyond_the_fixed_scratch(cuda_device):
