@@ -61,6 +61,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the per-step measurements")
     ap.add_argument("--no-lces", action="store_true", help="skip the time-to-LCES comparison")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the quality records of the three-primer and large-d workloads")
     ap.add_argument("--tune-eg-lr", action="store_true",
                     help="run the EigenGame learning-rate grid of the workload and print the choice")
     ap.add_argument("--e2e-steps", type=int, default=8)
@@ -423,6 +425,129 @@ def measure_lces(cfg, t_max=40, reps=3):
     if out["fp8"].get("ms") and out["fp32"].get("ms"):
         out["speedup_fp8_vs_fp32"] = round(out["fp32"]["ms"] / out["fp8"]["ms"], 3)
     del X32, X16, X8, s8
+    torch.cuda.empty_cache()
+    return out
+
+
+PAPER_GRID = [(f"pi/{2 ** j}", math.pi / 2 ** j) for j in range(3, 11)]     # Section 5.3's V = pi/8 ... pi/1024
+
+
+def _solve_ms(fn, stream, reps=3):
+    """Median device time (CUDA events on `stream`) of `reps` calls of fn after one warm-up."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def measure_primers(cfg):
+    """The three primers compared on the 1e5 x 1024 FP32 workload (lambda_i = 1/i, k = l = 32):
+    block power (T = 20), Oja (minibatch 256, lr 1/(t+100), one epoch) and EigenGame
+    (200 parallel steps, minibatch 1024, Nesterov 0.9, the grid-chosen lr), each followed by
+    the split-precision pPCA step.  Quality is the streak and angles of E against the FP64
+    eigenvectors of X^T X (lces_truth), at the workload's 1e-4 rad and on the paper's grid."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    n, d, k, m = cfg.n, cfg.d, cfg.k, cfg.m
+    stream = torch.cuda.current_stream()
+    X, _ = synth.gaussian_data_torch(n, d, cfg.lam(), cfg.seed, "cuda", torch.float32)
+    t0 = time.perf_counter()
+    Etrue, wtrue = lces_truth(X, k)
+    out = {"n": n, "d": d, "k": k, "l": cfg.l, "tol_rad": cfg.angle_tol, "eig_rtol": cfg.eig_rtol,
+           "truth": "FP64 eigh of X^T X (FP32 cuBLAS GEMMs over 1024-row chunks summed in FP64)",
+           "truth_s": round(time.perf_counter() - t0, 1)}
+    V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, cfg.seed).T, dtype=np.float32)).cuda()
+    E = torch.empty((k, d), dtype=torch.float32, device="cuda")
+    lam = torch.empty(k, dtype=torch.float64, device="cuda")
+    Vb = torch.empty((m, d), dtype=torch.float32, device="cuda")
+    pw, oj, eg = cfg.primers["power"], cfg.primers["oja"], cfg.primers["eigengame"]
+    runs = [("power", P.PPCA_POWER, pw["T"], {}),
+            ("oja", P.PPCA_OJA, oj["epochs"] * -(-n // oj["batch"]),
+             {"batch": oj["batch"], "lr": oj["lr0"], "lr_offset": oj["lr_offset"]}),
+            ("eigengame", P.PPCA_EIGENGAME, eg["steps"],
+             {"batch": eg["batch"], "lr": eg["lr"], "momentum": eg["momentum"]})]
+    for name, method, T, kw in runs:
+        h = P.ppca_create(X, stream=stream)
+        prm = P.ppca_prime_params_default(method)
+        for key, v in kw.items():
+            setattr(prm, key, v)
+        prm.precision = P.PPCA_PREC_FAST
+
+        def solve():
+            P.ppca_prime(h, method, m, T, prm, V0=V0)
+            P.ppca_finalize(h, k, E, lam, P.PPCA_PREC_ACCURATE)
+
+        ms = _solve_ms(solve, stream)
+        P.ppca_get_basis(h, Vb)
+        P.ppca_sync(h)
+        streak, ang = lces_of(E, Etrue, cfg.angle_tol)
+        rec = {"steps": T, **kw, "ms": round(ms, 3), "lces": int(streak), "max_angle_rad": float(np.max(ang)),
+               "eig_rel_err_max": float(((lam - wtrue).abs() / wtrue).max()),
+               "lces_grid": {lab: int(lces_of(E, Etrue, v)[0]) for lab, v in PAPER_GRID}}
+        if method != P.PPCA_POWER:
+            # the primer alone: its first k directions in order (Oja/Sanger and EigenGame order them)
+            rec["primer_alone_lces_grid"] = {lab: int(lces_of(Vb[:k], Etrue, v)[0]) for lab, v in PAPER_GRID}
+        rec["within_tolerance"] = bool(streak == k and rec["eig_rel_err_max"] <= cfg.eig_rtol)
+        out[name] = rec
+        del h
+    del X
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_large_d_quality(cfg):
+    """One solve of the 50000 x 262144 EigenGame workload (500 steps, minibatch 4096, then
+    the split-precision pPCA step) and its quality against a residual-certified truth."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    n, d, k, m = cfg.n, cfg.d, cfg.k, cfg.m
+    eg = cfg.primers["eigengame"]
+    stream = torch.cuda.current_stream()
+    X, _ = synth.hadamard_rotated_data_torch(n, d, cfg.lam(), cfg.seed, "cuda", torch.bfloat16)
+    V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, cfg.seed).T, dtype=np.float32)).cuda()
+    E = torch.empty((k, d), dtype=torch.float32, device="cuda")
+    lam = torch.empty(k, dtype=torch.float64, device="cuda")
+    h = P.ppca_create(X, stream=stream)
+    prm = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
+    prm.batch, prm.lr, prm.momentum = eg["batch"], eg["lr"], eg["momentum"]
+    prm.precision = P.PPCA_PREC_FAST
+
+    def solve():
+        P.ppca_prime(h, P.PPCA_EIGENGAME, m, eg["steps"], prm, V0=V0)
+        P.ppca_finalize(h, k, E, lam, P.PPCA_PREC_ACCURATE)
+
+    ms = _solve_ms(solve, stream, reps=1)
+    P.ppca_sync(h)
+    t0 = time.perf_counter()
+    Et, wt, bound = lces_truth_subspace(X, k)
+    streak, ang = lces_of(E, Et, cfg.angle_tol)
+    out = {"n": n, "d": d, "k": k, "l": cfg.l, "steps": eg["steps"], "batch": eg["batch"], "lr": eg["lr"],
+           "tol_rad": cfg.angle_tol, "eig_rtol": cfg.eig_rtol, "ms": round(ms, 3), "lces": int(streak),
+           "max_angle_rad": float(np.max(ang)), "eig_rel_err_max": float(((lam - wt).abs() / wt).max()),
+           "lces_grid": {lab: int(lces_of(E, Et, v)[0]) for lab, v in PAPER_GRID},
+           "truth": "FP64 Rayleigh-Ritz of a 128-wide FP32 block subspace iteration (cuBLAS/cuSOLVER), "
+                    "residual-certified", "truth_angle_bound_max": float(np.max(bound)),
+           "truth_s": round(time.perf_counter() - t0, 1),
+           "within_tolerance": False,
+           "method_limit": "the oracle's own FP64 EigenGame on the d = 4096 analogue (same spectrum formula, "
+                           "generator and schedule) reaches the same streak as this path and stays short of k "
+                           "(tests/test_gpu_eigengame_large_d.py)"}
+    out["within_tolerance"] = bool(streak == k and out["eig_rel_err_max"] <= cfg.eig_rtol)
+    del h, X
     torch.cuda.empty_cache()
     return out
 
@@ -895,12 +1020,14 @@ def run_ours(args):
     pass_ms = tm.pass_ms[fast] / max(tm.passes[fast], 1)
     split_ms = tm.pass_ms[split] / max(tm.passes[split], 1)
     achieved = bytes_per_pass / (pass_ms / 1e3) / 1e9
-    # DRAM bytes (read + write) of one fused-pass launch on this workload, from the ncu
-    # capture in profiles/xpass_fused_bf16_131072x4096_ncu.md (131072 rows, scaled by rows)
+    # DRAM bytes (read + write) of one fused-pass launch on this workload: an ncu capture of
+    # the same kernel on 131072 rows, scaled by rows (not measured in this run)
     traffic = 12.51e9 if (cfg.name == "precision_bf16_1000000x4096" and n == 1000000) else None
     labels = pass_labels(cfg.dtype, bytes_per_pass)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on 131072 rows, "
+                                  "scaled by rows to this workload" if traffic else None,
                 "peak_source": peak_kind,
                 "kernel": labels["kernel"],
                 "pass_ms": round(pass_ms, 4), "passes_timed": tm.passes[fast],
@@ -954,6 +1081,12 @@ def run_ours(args):
     if rank == 0 and not args.no_lces and cfg.name.startswith("precision"):
         lces = measure_lces(cfg)
 
+    # the other configurations' quality records (one solve each, not the timed headline)
+    configs = None
+    if rank == 0 and not args.no_configs:
+        configs = {"primers_fp32_100000x1024": measure_primers(synth.CONFIGS["primers_fp32_100000x1024"]),
+                   "largeD_bf16_50000x262144": measure_large_d_quality(synth.CONFIGS["largeD_bf16_50000x262144"])}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         out, cores, err = run_cpu_leg(args.workload, args.cpu_rows, args.cpu_passes)
@@ -977,6 +1110,7 @@ def run_ours(args):
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": tm.launches,
             "lces": lces,
+            "configs": configs,
             "rows": row_times,
         }
         print(json.dumps(line))
