@@ -285,6 +285,9 @@ typedef struct ppca_schedule {
     int32_t l2_keep;          /* fused pass: percent (1-100) of each row tile's columns loaded    */
                               /* with the L2 evict_last hint for the consumers' re-read, the rest */
                               /* evict_first (0: library default, what fits in 70 % of L2)        */
+    int32_t fp8_mma;          /* FP8 data, FAST passes: 0 library default (= 1), 1 the FP8 tensor  */
+                              /* cores (kind::f8f6f4: V and Y as two E4M3 pieces), 2 E4M3 widened */
+                              /* to BF16 in shared memory (kind::f16)                             */
 } ppca_schedule;
 
 /* Set the X-pass schedule of a handle (takes effect at its next pass).

@@ -97,6 +97,7 @@ class ppca_schedule(ctypes.Structure):
         ("engine", ctypes.c_int32),
         ("kparts", ctypes.c_int32),
         ("l2_keep", ctypes.c_int32),
+        ("fp8_mma", ctypes.c_int32),
     ]
 
 
@@ -482,8 +483,8 @@ def ppca_batch_destroy(b: Batch):
 
 
 def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: int = 0, flush: int = 0,
-                      engine: int = 0, kparts: int = 0, l2_keep: int = 0):
-    s = ppca_schedule(fused, producers, window, flush, engine, kparts, l2_keep)
+                      engine: int = 0, kparts: int = 0, l2_keep: int = 0, fp8_mma: int = 0):
+    s = ppca_schedule(fused, producers, window, flush, engine, kparts, l2_keep, fp8_mma)
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
 
 

@@ -710,7 +710,8 @@ ppca_status ppca_set_state(ppca_handle* h, const void* buf, int64_t bytes) {
 ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     if (!h || !s) return fail(PPCA_ERR_INVALID, "NULL argument");
     if (s->fused < -1 || s->fused > 1 || s->producers < 0 || s->window < 0 || s->flush < 0 || s->engine < 0 ||
-        s->engine > 2 || s->kparts < 0 || s->kparts > 2 || s->l2_keep < 0 || s->l2_keep > 100)
+        s->engine > 2 || s->kparts < 0 || s->kparts > 2 || s->l2_keep < 0 || s->l2_keep > 100 || s->fp8_mma < 0 ||
+        s->fp8_mma > 2)
         return fail(PPCA_ERR_INVALID, "schedule out of range");
     h->sched.fused = s->fused;
     h->sched.producers = s->producers;
@@ -719,6 +720,7 @@ ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     h->sched.engine = s->engine;
     h->sched.kparts = s->kparts;
     h->sched.l2_keep = s->l2_keep;
+    h->sched.fp8_mma = s->fp8_mma == 2 ? 0 : 1;
     return PPCA_OK;
 }
 
@@ -740,6 +742,7 @@ ppca_schedule to_abi(const TcSchedule& t) {
     s.engine = t.engine;
     s.kparts = t.kparts;
     s.l2_keep = t.l2_keep;
+    s.fp8_mma = t.fp8_mma == 0 ? 2 : 1;
     return s;
 }
 

@@ -496,6 +496,389 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
     tc_epilogue_teardown(hd, tmem_cols, status);
 }
 
+// ---------------------------------------------------------------- FP8 data on kind::f8f6f4
+//
+// The FAST pass of E4M3 data straight on the FP8 tensor cores, with no
+// widening: X8 (the stored codes) is the A operand as loaded.  V and Y enter
+// as two E4M3 pieces that share one power-of-two scale, hi = E4M3(2^a v) and
+// lo = E4M3(2^a v - hi), so both pieces' MMAs accumulate into one FP32
+// accumulator: X8 (hi + lo) = 2^a X8 V with about 2^-8 relative error per term
+// (a value below 2^-10 of the scaled range keeps an absolute error under
+// 2^-17 of the range).  With X = diag(s) X8,
+//   Y' = diag(s^2) X8 V    (rows r0..r1; xv_f8_kernel, pieces at scale 2^b)
+//   Z  = X8^T Y'           (xty_f8_kernel; X8^T read MN-major)
+// The scales come from three maxima taken before the pass (f8_stats_kernel):
+// 2^a is the largest power of two with max|V| 2^a <= 448, and 2^b the largest
+// with sqrt(d) max_r s_r^2 max_c |v_c| 2^b <= 1, a bound on |Y'| / 448 since
+// |x8_r . v_c| <= |x8_r| |v_c| <= 448 sqrt(d) |v_c|.  f8s[] holds
+// {max|V|, max_c |v_c|^2, max_r s_r^2, 2^(b - a), 2^-b}.
+
+// (e4m3(hi_elem) << 8) | e4m3(lo_elem), round to nearest even, saturating at 448.
+__device__ __forceinline__ uint32_t f32x2_to_e4m3x2(float hi_elem, float lo_elem) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi_elem), "f"(lo_elem));
+    return r;
+}
+
+// Two E4M3 codes (low byte -> .x, high byte -> .y) as exact FP32 values.
+__device__ __forceinline__ float2 e4m3x2_to_f32x2(uint32_t two) {
+    uint32_t h2;
+    float lo, hi;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"((unsigned short)two));
+    asm("{\n\t.reg .f16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+        : "=f"(lo), "=f"(hi)
+        : "r"(h2));
+    return make_float2(lo, hi);
+}
+
+// Two values -> their hi and lo E4M3 pieces (each a code pair, low byte = y0).
+__device__ __forceinline__ void e4m3_pieces(float y0, float y1, uint32_t& hi, uint32_t& lo) {
+    hi = f32x2_to_e4m3x2(y1, y0);
+    const float2 b = e4m3x2_to_f32x2(hi);
+    lo = f32x2_to_e4m3x2(y1 - b.y, y0 - b.x);
+}
+
+// Largest power of two p with p * v <= cap (v > 0), as a float; 1 for v == 0.
+__device__ __forceinline__ float pow2_below(float cap, float v) {
+    if (!(v > 0.f)) return 1.f;
+    int e;
+    frexpf(cap / v, &e);                       // cap / v = f 2^e, f in [0.5, 1)
+    e = e - 1;
+    e = e < -126 ? -126 : (e > 126 ? 126 : e);
+    return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(float* p, float v) {
+    atomicMax(reinterpret_cast<int*>(p), __float_as_int(v));   // non-negative floats order as their bits
+}
+
+// Blocks 0..m-1: column c of V (max |v_kc| and |v_c|^2); the rest: max s_r^2 over rows [0, rows).
+__global__ void f8_stats_kernel(const float* __restrict__ V, int64_t d, int m, const float* __restrict__ scales,
+                                int64_t rows, float* __restrict__ f8s) {
+    __shared__ float red[2][32];
+    float a = 0.f, q = 0.f;
+    if ((int)blockIdx.x < m) {
+        const float* v = V + (int64_t)blockIdx.x * d;
+        for (int64_t k = threadIdx.x; k < d; k += blockDim.x) {
+            const float x = v[k];
+            a = fmaxf(a, fabsf(x));
+            q = fmaf(x, x, q);
+        }
+    } else {
+        for (int64_t r = (int64_t)(blockIdx.x - m) * blockDim.x + threadIdx.x; r < rows;
+             r += (int64_t)(gridDim.x - m) * blockDim.x) {
+            const float sr = scales[r];
+            a = fmaxf(a, sr * sr);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (lane == 0) {
+        red[0][w] = a;
+        red[1][w] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < (int)(blockDim.x / 32); ++i) {
+            a = fmaxf(a, red[0][i]);
+            q += red[1][i];
+        }
+        if ((int)blockIdx.x < m) {
+            atomic_max_nonneg(&f8s[0], a);
+            atomic_max_nonneg(&f8s[1], q);
+        } else {
+            atomic_max_nonneg(&f8s[2], a);
+        }
+    }
+}
+
+// V (d x m column-major FP32) -> hi and lo E4M3 pieces at the shared scale 2^a,
+// [2][m_pad][ldv8] bytes, zero padded; thread (0, 0) also stores 2^(b - a) and 2^-b.
+__global__ void split_v8_kernel(const float* __restrict__ V, int64_t d, int m, int m_pad, int64_t ldv8,
+                                float* __restrict__ f8s, uint8_t* __restrict__ V8) {
+    const float sa = pow2_below(448.f, f8s[0]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const float bound = sqrtf((float)d) * f8s[2] * sqrtf(f8s[1]);
+        const float sb = pow2_below(1.f, bound);
+        f8s[3] = sb / sa;
+        f8s[4] = 1.f / sb;
+    }
+    const int64_t pairs = (int64_t)m_pad * ldv8 / 2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < pairs; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / (ldv8 / 2), k = (e % (ldv8 / 2)) * 2;
+        const float v0 = (c < m && k < d) ? V[c * d + k] * sa : 0.f;
+        const float v1 = (c < m && k + 1 < d) ? V[c * d + k + 1] * sa : 0.f;
+        uint32_t hi, lo;
+        e4m3_pieces(v0, v1, hi, lo);
+        reinterpret_cast<uint16_t*>(V8)[e] = (uint16_t)hi;
+        reinterpret_cast<uint16_t*>(V8 + (int64_t)m_pad * ldv8)[e] = (uint16_t)lo;
+    }
+}
+
+// Y' = diag(s^2) X8 V for 256-row tiles, two M = 128 accumulators sharing each V stage (stage =
+// [X8 rows 0-127][X8 rows 128-255][V hi][V lo], 128 B of K each), so a CTA ingests one byte of V pieces
+// per byte of X; Y' stored as its hi and lo E4M3 pieces at scale 2^b, Y^T layout [2][m_pad][ldy] bytes
+// (ldy a multiple of 256).
+__global__ void __launch_bounds__(kThreads, 1)
+    xv_f8_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
+                 int nk, int m_pad, int stages, uint8_t* __restrict__ Yt, int64_t ldy,
+                 const float* __restrict__ scales, int64_t rows, const float* __restrict__ f8s, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 2u * 128u * 128u;
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = a_bytes + 2u * b_piece;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(2 * m_pad);      // 2 buffers x 2 row halves
+    tc_prologue(hd, stages, tmem_cols, &tmX, &tmV);
+    const uint32_t tmem = hd->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[s], stage_bytes);
+                    uint8_t* st = tiles + (size_t)s * stage_bytes;
+                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * 128, t * 256);
+                    tc::tma_load_2d(st + 16384, &tmX, &hd->full[s], k * 128, t * 256 + 128);
+                    tc::tma_load_2d(st + a_bytes, &tmV, &hd->full[s], k * 128, 0);
+                    tc::tma_load_2d(st + a_bytes + b_piece, &tmV, &hd->full[s], k * 128, m_pad);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_e4m3(128, m_pad, false, false);
+            uint32_t it = 0, tl = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem + b * 2u * (uint32_t)m_pad;
+                for (int k = 0; k < nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                        for (int p = 0; p < 2; ++p) {
+                            const uint64_t bdesc =
+                                tc::smem_desc_sw128(a_addr + a_bytes + p * b_piece + kk * 32, 16, 1024);
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const uint64_t adesc = tc::smem_desc_sw128(a_addr + h * 16384 + kk * 32, 16, 1024);
+                                tc::mma_f8(d_tmem + h * (uint32_t)m_pad, adesc, bdesc, idesc,
+                                           (k != 0 || kk != 0 || p != 0) ? 1u : 0u);
+                            }
+                        }
+                    }
+                    tc::mma_commit(&hd->empty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->tfull[b]);
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const float f = f8s[3];                   // 2^(b - a)
+        uint32_t tl = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+            const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+            if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                hd->abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            for (int h = 0; h < 2; ++h) {
+                const int64_t row = (int64_t)t * 256 + h * 128 + q * 32 + lane;
+                const float sr = row < rows ? scales[row] : 0.f;
+                const float rs = sr * sr * f;
+                const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (b * 2u + h) * (uint32_t)m_pad;
+                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(acc + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; j += 2) {
+                        uint32_t hi, lo;
+                        e4m3_pieces(__uint_as_float(r[j]) * rs, __uint_as_float(r[j + 1]) * rs, hi, lo);
+                        uint8_t* y = Yt + (int64_t)(c0 + j) * ldy + row;
+                        y[0] = (uint8_t)(hi & 0xFFu);
+                        y[ldy] = (uint8_t)(hi >> 8);
+                        y[(int64_t)m_pad * ldy] = (uint8_t)(lo & 0xFFu);
+                        y[(int64_t)m_pad * ldy + ldy] = (uint8_t)(lo >> 8);
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&hd->tempty[b]);
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols, status);
+}
+
+// Z = X8^T Y' for (256-column slice, row group) tasks: two M = 128 accumulators share each Y' stage
+// (stage = [X8 128 rows x columns 0-127, MN-major][columns 128-255][Y' hi][Y' lo]); each FP32
+// accumulator is folded, times 2^-b, into double-float partials [g][column][Dt2 * 256 rows of Z].
+__global__ void __launch_bounds__(kThreads, 1)
+    xty_f8_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Dt2, int Sg,
+                  int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, const float* __restrict__ f8s,
+                  int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 2u * 128u * 128u;
+    const uint32_t b_piece = (uint32_t)m_pad * 128u;
+    const uint32_t stage_bytes = a_bytes + 2u * b_piece;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = tmem_cols_for(2 * m_pad);      // 2 buffers x 2 column halves
+    tc_prologue(hd, stages, tmem_cols, &tmX, &tmY);
+    const uint32_t tmem = hd->tmem_base;
+    const int ntask = Dt2 * Sg;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int s = task % Dt2, g = task / Dt2;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int k = k0; k < k1; ++k, ++it) {
+                    const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[st_i], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[st_i], stage_bytes);
+                    uint8_t* st = tiles + (size_t)st_i * stage_bytes;
+                    tc::tma_load_2d(st, &tmX, &hd->full[st_i], s * 256, k * 128);
+                    tc::tma_load_2d(st + 16384, &tmX, &hd->full[st_i], s * 256 + 128, k * 128);
+                    tc::tma_load_2d(st + a_bytes, &tmY, &hd->full[st_i], k * 128, 0);
+                    tc::tma_load_2d(st + a_bytes + b_piece, &tmY, &hd->full[st_i], k * 128, m_pad);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_e4m3(128, m_pad, true, false);
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+                const int g = task / Dt2;
+                const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+                for (int kb = k0; kb < k1 && ok; kb += flush, ++fb) {
+                    const int ke = kb + flush < k1 ? kb + flush : k1;
+                    const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                    if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d_tmem = tmem + b * 2u * (uint32_t)m_pad;
+                    for (int k = kb; k < ke; ++k, ++it) {
+                        const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                        if (!tc::mbar_wait(&hd->full[st_i], ph, status) || *(volatile int*)&hd->abort) {
+                            hd->abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a_addr = tc::smem_u32(tiles + (size_t)st_i * stage_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+                            for (int p = 0; p < 2; ++p) {
+                                const uint64_t bdesc =
+                                    tc::smem_desc_sw128(a_addr + a_bytes + p * b_piece + kk * 32, 16, 1024);
+#pragma unroll
+                                for (int h = 0; h < 2; ++h) {
+                                    // 32 rows of the MN-major X8 half tile (four 8-row groups of 1 KB)
+                                    const uint64_t adesc =
+                                        tc::smem_desc_sw128(a_addr + h * 16384 + kk * 4096, 16384, 1024);
+                                    tc::mma_f8(d_tmem + h * (uint32_t)m_pad, adesc, bdesc, idesc,
+                                               (k != kb) || kk != 0 || p != 0);
+                                }
+                            }
+                        }
+                        tc::mma_commit(&hd->empty[st_i]);
+                    }
+                    if (ok) tc::mma_commit(&hd->tfull[b]);
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        const float zs_f = f8s[4];                // 2^-b
+        uint32_t fb = 0;
+        bool ok = true;
+        for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
+            const int s = task % Dt2, g = task / Dt2;
+            const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
+            const int64_t zs = (int64_t)Dt2 * 256;    // Z partials [g][column][row]: a warp's rows contiguous
+            for (int kb = k0; kb < k1; kb += flush, ++fb) {
+                const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int h = 0; h < 2; ++h) {
+                    const int64_t j = (int64_t)s * 256 + h * 128 + q * 32 + lane;
+                    float2* z = reinterpret_cast<float2*>(Zacc) + (int64_t)g * m_pad * zs + j;
+                    const uint32_t acc = tmem + ((uint32_t)(q * 32) << 16) + (b * 2u + h) * (uint32_t)m_pad;
+                    for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                        uint32_t r[32];
+                        tc::tmem_ld32(acc + (uint32_t)c0, r);
+                        tc::tmem_ld_wait();
+                        float2* zz = z + (int64_t)c0 * zs;
+                        if (kb == k0) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj)
+                                zz[jj * zs] = make_float2(__uint_as_float(r[jj]) * zs_f, 0.f);
+                        } else {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj) {
+                                float2 v = zz[jj * zs];
+                                df_add(v.x, v.y, __uint_as_float(r[jj]) * zs_f);
+                                zz[jj * zs] = v;
+                            }
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols, status);
+}
+
 // ---------------------------------------------------------------- fused single-read pass
 //
 // One persistent, cooperatively launched kernel; every CTA runs two
@@ -1486,6 +1869,57 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
     return launch_zreduce(Zacc, Sg, ps.Dt, ps.d, m, ps.m_pad, Z, st);
 }
 
+// FAST pass of E4M3 data on the FP8 tensor cores (two kernels, X8 read twice): see xv_f8_kernel.
+cudaError_t run_pass_f8(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
+                        const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+    const int64_t d = x.d, rows = r1 - r0;
+    const int m_pad = m_pad_of(m);
+    const int64_t ldv8 = round_up(d, 16), ldy = round_up(rows, 256);
+    const int Dt2 = (int)((d + 255) / 256), ntiles = (int)(ldy / 256), nk = (int)((d + 127) / 128);
+    uint8_t* V8 = static_cast<uint8_t*>(sc.vp);
+    uint8_t* Y8 = static_cast<uint8_t*>(sc.yt);
+    float* f8s = reinterpret_cast<float*>(sc.flags);
+    float* Zacc = static_cast<float*>(sc.zacc);
+    const float* scales = x.scales + r0;
+    cudaError_t e = cudaMemsetAsync(f8s, 0, 5 * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    f8_stats_kernel<<<m + 64, 256, 0, st>>>(V, d, m, scales, rows, f8s);
+    {
+        const int64_t pairs = (int64_t)m_pad * ldv8 / 2;
+        int blocks = (int)((pairs + 255) / 256);
+        if (blocks > 4096) blocks = 4096;
+        note_launch();
+        split_v8_kernel<<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv8, f8s, V8);
+    }
+    CUtensorMap tmX, tmV, tmY;
+    const void* xbase = static_cast<const uint8_t*>(x.ptr) + r0 * x.ld;
+    if (!encode_2d(&tmX, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, d, rows, x.ld, 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tmV, CU_TENSOR_MAP_DATA_TYPE_UINT8, V8, ldv8, 2 * (uint64_t)m_pad, ldv8, 128, m_pad,
+                   CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tmY, CU_TENSOR_MAP_DATA_TYPE_UINT8, Y8, ldy, 2 * (uint64_t)m_pad, ldy, 128, m_pad,
+                   CU_TENSOR_MAP_SWIZZLE_128B))
+        return cudaErrorInvalidValue;
+    const uint32_t stage_bytes = 2u * 128u * 128u + 2u * (uint32_t)m_pad * 128u;
+    const int stages = stages_for(stage_bytes);
+    const size_t smem = smem_bytes(stages, stage_bytes);
+    e = cudaFuncSetAttribute(xv_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(xty_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    xv_f8_kernel<<<ntiles < num_sms ? ntiles : num_sms, kThreads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages,
+                                                                              Y8, ldy, scales, rows, f8s, status);
+    const int kst = (int)(ldy / 128);
+    // tasks are 256-column slices; a row group's partials hold 2 Dt2 128-column slices
+    const int Sg2 = choose_row_groups(Dt2, kst, num_sms, sc.z_bytes / 2, m_pad);
+    const int ntask = Dt2 * Sg2;
+    note_launch();
+    xty_f8_kernel<<<ntask < num_sms ? ntask : num_sms, kThreads, smem, st>>>(tmX, tmY, Dt2, Sg2, kst, flush, m_pad,
+                                                                             stages, Zacc, f8s, status);
+    return launch_zreduce(Zacc, Sg2, 2 * Dt2, d, m, m_pad, Z, st);
+}
+
 // Fused single-read pass (one piece, BF16): see xpass_fused_kernel.
 cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z,
                       const TcPassScratch& sc, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
@@ -1649,9 +2083,14 @@ cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t 
                      const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
     if (r1 <= r0) return cudaErrorInvalidValue;
     if (x.dtype == PPCA_F32) return run_pass_f32(x, V, m, r0, r1, Z, 64, s, status, num_sms, st);   // FAST only
-    if (x.dtype == PPCA_FP8_E4M3)
-        return prec == PPCA_PREC_ACCURATE ? run_pass<3, true>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st)
-                                          : run_pass<1, true>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
+    if (x.dtype == PPCA_FP8_E4M3) {
+        if (prec == PPCA_PREC_ACCURATE) return run_pass<3, true>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
+        // the FP8 tensor cores when every SM gets row tiles (else the widening two-kernel pass, which splits K)
+        const int64_t ntiles = (r1 - r0 + 127) / 128;
+        if (sched.fp8_mma != 0 && ntiles * 2 > num_sms)
+            return run_pass_f8(x, V, m, r0, r1, Z, 128, s, status, num_sms, st);
+        return run_pass<1, true>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
+    }
     if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
     // The fused pass needs every 128-column slice of d owned by a resident CTA.
     const int Dt = (int)((x.d + 127) / 128);

@@ -23,6 +23,7 @@ struct TcSchedule {
     int engine = 0;         // 0: library choice, 1: tensor cores, 2: CUDA cores
     int kparts = 0;         // fused kernel: K parts per producer tile (2: two K halves; else 1)
     int l2_keep = 0;        // fused kernel: percent of a tile's K-stages loaded evict_last (0: from the L2 size)
+    int fp8_mma = -1;       // FP8 data, FAST: 1 / -1 the FP8 tensor cores (kind::f8f6f4), 0 widening to BF16
 };
 
 size_t tc_pass_scratch_bytes(int64_t n, int64_t d, int m, int num_sms);

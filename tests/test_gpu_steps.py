@@ -7,8 +7,9 @@ Tolerances (derived from the arithmetic; u = 2^-24):
   are compared with the same pass formed exactly in FP64 from BF16-rounded V
   and Y (tau_r = 2^-7 for one-unit flips of Y's rounding, tau_z for
   the FP32 accumulation drift); split-precision and FP32 passes with
-  X^T X V itself.  The normwise errors of the earlier bounds are kept as a
-  second check.
+  X^T X V itself (split precision: the drift of Y's and Z's accumulators
+  relative to their running sums, split_ratio).  The normwise errors of the
+  earlier bounds are kept as a second check.
 * X-pass, FP32 data, ACCURATE (exact FP32 on CUDA cores): FP32 products,
   FP32 chunks of <= 256 terms folded into double-float sums: normwise
   ||dZ|| / ||Z|| <= 2e-5 (about u * (sqrt(d) + 16) with a safety factor ~3).
@@ -28,21 +29,32 @@ import pytest
 import oracle
 import synth
 from gpu_util import dev_basis, dev_matrix, empty_basis, host_basis, normwise, stored_f64
-from xpass_parity import TAU_FAST_R, exact_reference, fast_reference, ratio
+from xpass_parity import TAU_FAST_R, exact_reference, fast_e4m3_reference, fast_reference, ratio, split_ratio
 
 pytestmark = pytest.mark.gpu
 
 # element-wise tolerances (tau_r, tau_z) per pass kind, see tests/xpass_parity.py:
 # FAST BF16 / FP8 against the BF16-rounded exact pass: one-unit flips of Y
 # (2^-7 R) and up to 16384 accumulating MMAs between folds (fused pass,
-# ~2e-8 each: 3.3e-4 -> 5e-4); split precision (three BF16 pieces; the
-# two-kernel pass folds its Z accumulator every 32 K-stages = 384 MMAs, drift
-# ~8e-6 -> 2e-5 |Z|; Y's FP32 rounding 2^-24 of the terms, summed over d ->
-# 2^-18 R); 3xTF32 (dropped lo*lo products ~2^-22 of each term, accumulation
-# over d and n unfolded: 2^-16 R, 5e-5 |Z|); exact FP32 on CUDA cores (FP32
-# products, 256-term chunks folded: 2^-19 R, 1e-6 |Z|).
+# ~2e-8 each: 3.3e-4 -> 5e-4); split precision (three BF16 pieces; Y's
+# accumulator takes 3 d / 16 MMAs unfolded and the two-kernel pass folds its Z
+# accumulator every 32 K-stages = 384 MMAs, drift ~2e-8 per MMA, x2 margin ->
+# tau_z(d); Y's FP32 rounding 2^-24 of the terms, summed over d -> 2^-18 R);
+# 3xTF32 (dropped lo*lo products ~2^-22 of each term, accumulation over d and
+# n unfolded: 2^-16 R, 5e-5 |Z|); exact FP32 on CUDA cores (FP32 products,
+# 256-term chunks folded: 2^-19 R, 1e-6 |Z|).
 TAU_FAST = (TAU_FAST_R, 5e-4)
-TAU_SPLIT = (2.0 ** -18, 2e-5)
+
+
+def tau_split(d):
+    """(tau_y, tau_z) of split_ratio for the two-kernel split-precision pass: Y's
+    accumulator takes 3 ceil(d / 16) MMAs (three pieces, K = 16) unfolded, Z's is
+    folded every 32 K-stages of 64 rows (384 MMAs); ~2e-8 drift per MMA, x2, plus
+    the FP32 roundings (2^-22)."""
+    return (2 * 2e-8 * 3 * -(-d // 16) + 2.0 ** -22, 2 * 2e-8 * 384 + 2.0 ** -22)
+
+
+
 TAU_3XTF32 = (2.0 ** -16, 5e-5)
 TAU_F32_EXACT = (2.0 ** -19, 1e-6)
 
@@ -177,8 +189,7 @@ def test_xpass_bf16(P, n, d, m, r0, r1, prec, tol):
         Zq, R = fast_reference(Xs, host_basis(Vd))
         assert ratio(Zg, Zq, R, *TAU_FAST) <= 1.0
     else:
-        Ze, R = exact_reference(Xs, host_basis(Vd))
-        assert ratio(Zg, Ze, R, *TAU_SPLIT) <= 1.0
+        assert split_ratio(Zg, Xs, host_basis(Vd), *tau_split(d)) <= 1.0
 
 
 FUSED_CASES = [
@@ -388,16 +399,24 @@ FP8_CASES = [
     (257, 64, 1, 0, 257),
     (5000, 1024, 128, 0, 5000),
     (1000, 8192, 64, 0, 512),        # split-K Y = X V
+    # enough row tiles for every SM: the FAST pass runs on the FP8 tensor cores
+    (20000, 1024, 128, 0, 20000),
+    (30001, 200, 33, 5, 29000),      # ragged d, rows and m
+    (12000, 4096, 128, 0, 12000),
+    (40000, 64, 1, 0, 40000),
 ]
 
 
 @pytest.mark.parametrize("n,d,m,r0,r1", FP8_CASES)
 @pytest.mark.parametrize("prec,tol", [("FAST", 1e-2), ("ACCURATE", 2e-5)])
 def test_xpass_fp8_tensor_cores(P, n, d, m, r0, r1, prec, tol):
-    """FP8 E4M3 data with per-row scales on tensor cores: the E4M3 tiles are widened
-    to BF16 in shared memory (exact) and s_r^2 scales Y.  The reference is
-    X^T X V of the dequantised stored values in FP64; FAST rounds Y to BF16
-    (1e-2), ACCURATE splits V and Y into three BF16 pieces (2e-5)."""
+    """FP8 E4M3 data with per-row scales on tensor cores.  With row tiles for
+    every SM the FAST pass runs on kind::f8f6f4 (V and Y' = diag(s^2) X8 V as
+    two E4M3 pieces at a power-of-two scale); otherwise, and for ACCURATE, the
+    E4M3 tiles are widened to BF16 in shared memory (exact) and s_r^2 scales Y.
+    Normwise against X^T X V of the dequantised stored values in FP64 (FAST
+    1e-2, ACCURATE with three BF16 pieces 2e-5), and element by element
+    against the same pass formed exactly from the rounded pieces."""
     import torch
     X, _ = synth.gaussian_data(n, d, 0.97 ** np.arange(1, d + 1), seed=31) if d <= 4096 else \
         (np.random.default_rng(31).standard_normal((n, d)) * (0.9995 ** np.arange(1, d + 1))[None, :], None)
@@ -417,12 +436,15 @@ def test_xpass_fp8_tensor_cores(P, n, d, m, r0, r1, prec, tol):
     # element by element on the unscaled codes with the s_r^2 row factor of the pass
     X8 = oracle.e4m3_decode(codes)[r0:r1]
     s2 = scales.astype(np.float64)[r0:r1] ** 2
-    if prec == "FAST":
+    if prec == "FAST" and (r1 - r0 + 127) // 128 * 2 > torch.cuda.get_device_properties(0).multi_processor_count:
+        # kind::f8f6f4: V and Y as two E4M3 pieces at a power-of-two scale
+        Zq, R = fast_e4m3_reference(X8, scales[r0:r1], host_basis(Vd))
+        assert ratio(host_basis(Zd), Zq, R, *TAU_FAST) <= 1.0
+    elif prec == "FAST":
         Zq, R = fast_reference(X8, host_basis(Vd), row_factor=s2)
         assert ratio(host_basis(Zd), Zq, R, *TAU_FAST) <= 1.0
     else:
-        Ze, R = exact_reference(X8, host_basis(Vd), row_factor=s2)
-        assert ratio(host_basis(Zd), Ze, R, *TAU_SPLIT) <= 1.0
+        assert split_ratio(host_basis(Zd), X8, host_basis(Vd), *tau_split(d), row_factor=s2) <= 1.0
 
 
 def test_quantize_fp8_bit_exact(P):

@@ -15,7 +15,7 @@ import pytest
 
 import oracle
 import synth
-from xpass_parity import TAU_FAST_R, exact_reference, fast_reference, ratio
+from xpass_parity import TAU_FAST_R, exact_reference, fast_reference, ratio, split_ratio
 
 TAU_Z_FAST = 5e-4
 
@@ -108,3 +108,11 @@ def test_accurate_emulation_passes_and_dropped_tile_fails(n, d, m, seed):
     Zref, R = exact_reference(Xs, V32)
     assert ratio(emulate_accurate(Xs, V32), Zref, R, *TAU_ACC) <= 0.5
     assert ratio(emulate_accurate(Xs, V32, drop_tile=2), Zref, R, *TAU_ACC) > 1.0
+
+
+@pytest.mark.parametrize("n,d,m,seed", SHAPES)
+def test_split_criterion_accepts_emulation_and_rejects_dropped_tile(n, d, m, seed):
+    Xs, V32 = problem(n, d, m, seed)
+    tau = (2 * 2e-8 * 3 * -(-d // 16) + 2.0 ** -22, 2 * 2e-8 * 384 + 2.0 ** -22)
+    assert split_ratio(emulate_accurate(Xs, V32), Xs, V32, *tau) <= 0.5
+    assert split_ratio(emulate_accurate(Xs, V32, drop_tile=2), Xs, V32, *tau) > 1.0
