@@ -295,6 +295,39 @@ typedef struct ppca_schedule {
 PPCA_API ppca_status ppca_set_schedule(ppca_handle *h, const ppca_schedule *s);
 
 /*
+ * Row sharding over processes, one GPU each.  The priming passes and the
+ * projected Gram matrix of the pPCA step are sums over the rows of X
+ * (X^T X V = sum_r x_r x_r^T V in Section 2.1's power step and the
+ * minibatch sums of Sections 2.2-2.3; G = sum_r (Q^T x_r)(x_r^T Q) in
+ * Algorithm 1, step 3), so with the rows split over ranks each rank streams
+ * its own rows and one sum across ranks per pass gives every rank the whole
+ * data set's result: Z (d x m FP32) after each priming pass, the minibatch
+ * size of Oja and EigenGame (their minibatch t is the union of every rank's
+ * local minibatch t), and G (m x m FP64) of the pPCA step and of
+ * ppca_variance_captured.  Everything after a sum is identical on every rank.
+ *   fn       sums `count` elements (elem_bytes 4: FP32, 8: FP64) of the
+ *            device buffer `buf` over all ranks, in place: after the work
+ *            already enqueued on `stream` and before the work the library
+ *            enqueues after fn returns (an NCCL all-reduce enqueued on that
+ *            stream, or: synchronise, copy to the host, sum, copy back).  A
+ *            status other than PPCA_OK is returned by the library call.
+ *            NULL: one process again (the other arguments are ignored).
+ *   ctx      passed to fn unchanged.
+ *   n_total  rows of X over all ranks (eigenvalues are eig(X^T X) / n_total).
+ *   staging  optional device buffer of staging_bytes the library copies each
+ *            sum's operand into before fn (and back from after), so fn always
+ *            sees the same buffer (at most d * m * 4 bytes are summed); NULL
+ *            and 0: fn sees the library's own buffers.
+ * Every rank must make the same calls with the same arguments (same m, T,
+ * V0, seeds, precisions).  ppca_xpass and ppca_projected_gram stay local
+ * (the rows of this rank).  Infrastructure (the data-parallel layout of the
+ * method's sums): no counterpart in the paper, which runs on one GPU.
+ */
+typedef ppca_status (*ppca_allreduce_fn)(void *buf, int64_t count, int32_t elem_bytes, void *stream, void *ctx);
+PPCA_API ppca_status ppca_set_allreduce(ppca_handle *h, ppca_allreduce_fn fn, void *ctx, int64_t n_total,
+                                        void *staging, int64_t staging_bytes);
+
+/*
  * Limit of every bounded wait inside the library's tensor-core kernels on the
  * current device, in nanoseconds (0 restores the default, 2 s; at most 60 s).
  * A wait that runs out sets the handle's device status word to a timeout, the

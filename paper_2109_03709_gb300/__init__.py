@@ -29,7 +29,7 @@ __all__ = [
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "ppca_set_wait_limit",
-    "EXPORTED_SYMBOLS",
+    "ppca_set_allreduce", "TorchAllReduce", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,7 +53,7 @@ EXPORTED_SYMBOLS = [
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured",
-    "ppca_set_wait_limit",
+    "ppca_set_wait_limit", "ppca_set_allreduce",
 ]
 
 
@@ -157,6 +157,7 @@ _SIGS = {
     "ppca_eigh_noalloc": (_c_status, [_vp, _i32, _vp, _vp, _vp, _vp]),
     "ppca_set_schedule": (_c_status, [_vp, ctypes.POINTER(ppca_schedule)]),
     "ppca_set_wait_limit": (_c_status, [ctypes.c_uint64]),
+    "ppca_set_allreduce": (_c_status, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "ppca_autotune": (_c_status, [_vp, _i32, _i64, _i32, ctypes.POINTER(ppca_schedule)]),
     "ppca_batch_autotune": (_c_status, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ppca_batch_create": (_c_status, [ctypes.POINTER(_vp), ctypes.POINTER(ppca_instance_desc), _i32, _i32, _vp]),
@@ -491,6 +492,64 @@ def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: in
 def ppca_set_wait_limit(ns: int = 0):
     """Limit (ns) of the bounded waits in the tensor-core kernels on the current device; 0 restores 2 s."""
     _check(load_library().ppca_set_wait_limit(int(ns)), "ppca_set_wait_limit")
+
+
+# ppca_allreduce_fn: (buf, count, elem_bytes, stream, ctx) -> ppca_status
+_ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.c_void_p)
+
+
+class TorchAllReduce:
+    """The sum across ranks for ppca_set_allreduce, done by torch.distributed.
+
+    Owns a staging tensor of `max_bytes` on `device`: the library copies each
+    sum's operand into it and calls back; the callback sums the first `count`
+    elements over `group` with dist.all_reduce (NCCL: on the device; gloo:
+    through a host copy), after synchronising the device so that the library's
+    copy has landed.  An exception inside the callback is kept in `error` and
+    reported to the library as PPCA_ERR_CUDA.
+    """
+
+    def __init__(self, max_bytes: int, device, group=None):
+        import torch
+        self.group = group
+        self.staging = torch.zeros(int(max_bytes), dtype=torch.uint8, device=device)
+        self.error = None
+        self.calls = 0
+        self._cb = _ALLREDUCE_FN(self._call)
+
+    def _call(self, buf, count, elem_bytes, stream, ctx):
+        try:
+            import torch
+            import torch.distributed as dist
+            dt = {4: torch.float32, 8: torch.float64}[int(elem_bytes)]
+            t = self.staging[: int(count) * int(elem_bytes)].view(dt)
+            if t.is_cuda:
+                torch.cuda.synchronize(t.device)
+            if t.is_cuda and dist.get_backend(self.group) == "nccl":
+                dist.all_reduce(t, group=self.group)
+            else:
+                c = t.cpu()
+                dist.all_reduce(c, group=self.group)
+                t.copy_(c)
+            if t.is_cuda:
+                torch.cuda.synchronize(t.device)
+            self.calls += 1
+            return PPCA_OK
+        except Exception as e:          # no exception may cross the C ABI
+            self.error = e
+            return PPCA_ERR_CUDA
+
+
+def ppca_set_allreduce(h: Handle, reducer: "TorchAllReduce | None", n_total: int = 0):
+    """Shard the rows of X over ranks: every pass's sum goes through `reducer` (None: one process)."""
+    if reducer is None:
+        _check(load_library().ppca_set_allreduce(h.ptr, None, None, 0, None, 0), "ppca_set_allreduce")
+        return
+    _check(load_library().ppca_set_allreduce(h.ptr, ctypes.cast(reducer._cb, ctypes.c_void_p), None, int(n_total),
+                                             _dev(reducer.staging, "staging"), reducer.staging.numel()),
+           "ppca_set_allreduce")
+    h._keep.append(reducer)
 
 
 def ppca_autotune(h: Handle, m: int, rows: int = 0, reps: int = 3) -> ppca_schedule:

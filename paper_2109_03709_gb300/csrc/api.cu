@@ -92,7 +92,8 @@ struct ppca_handle {
     float* E_res = nullptr;   // d x m: ppca_finalize_host's eigenvectors before the copy out
     double* lam_res = nullptr;  // m: ppca_finalize_host's eigenvalues
     int* tile_rows = nullptr;   // ceil(n / 128): first rows of the blocks of a row sample
-    double* seq_diff = nullptr; // POWER_SEQ: |x_t - x_{t+1}| of the last step
+    double* seq_diff = nullptr; // POWER_SEQ: |x_t - x_{t+1}| of the last step; [1]: the row count
+                                // summed across ranks (row sharding; the slot holds 256 bytes)
     float* gram_part = nullptr;
     void* jac = nullptr;
     double* eg = nullptr;
@@ -106,6 +107,13 @@ struct ppca_handle {
     int64_t t = 0;            // next minibatch step
     int64_t iters = 0;        // power iterations done
     ppca_prime_params params{};
+
+    // row sharding: sum across ranks (NULL: one process), its context and staging buffer, rows of all ranks
+    ppca_allreduce_fn ar_fn = nullptr;
+    void* ar_ctx = nullptr;
+    void* ar_stage = nullptr;
+    int64_t ar_stage_bytes = 0;
+    int64_t n_total = 0;
 
     // measurement
     bool timing = false;
@@ -258,6 +266,42 @@ ppca_status run_gram(ppca_handle* h, const XView& x, const float* Q, int m, int6
 // on the diagonally scaled Gram matrix and falls back to double-float on the
 // device when its conditioning bound says V is too ill-conditioned for that;
 // the second factors a matrix within rounding of the identity, in FP32.
+// Row sharding: sum `count` elements (elem_bytes 4 or 8) of the device buffer
+// buf over the ranks, through the caller's staging buffer when one was given.
+ppca_status allreduce(ppca_handle* h, void* buf, int64_t count, int32_t elem_bytes) {
+    if (!h->ar_fn) return PPCA_OK;
+    const size_t bytes = (size_t)count * (size_t)elem_bytes;
+    void* target = buf;
+    if (h->ar_stage) {
+        if ((int64_t)bytes > h->ar_stage_bytes)
+            return fail(PPCA_ERR_INVALID, "all-reduce of %zu bytes exceeds the %lld-byte staging buffer", bytes,
+                        (long long)h->ar_stage_bytes);
+        CUDA_TRY(cudaMemcpyAsync(h->ar_stage, buf, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        target = h->ar_stage;
+    }
+    const ppca_status s = h->ar_fn(target, count, elem_bytes, h->stream, h->ar_ctx);
+    if (s != PPCA_OK) return fail(s, "the all-reduce across ranks returned status %d", (int)s);
+    if (h->ar_stage) CUDA_TRY(cudaMemcpyAsync(buf, h->ar_stage, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return PPCA_OK;
+}
+
+// Rows of a minibatch (or a row sample) over all ranks: the local count, summed
+// across ranks when the rows are sharded (one host read-back).
+ppca_status global_rows(ppca_handle* h, int64_t local, int64_t* out) {
+    *out = local;
+    if (!h->ar_fn) return PPCA_OK;
+    double v = (double)local;
+    double* dev = h->seq_diff + 1;
+    CUDA_TRY(cudaMemcpyAsync(dev, &v, sizeof v, cudaMemcpyHostToDevice, h->stream));
+    PPCA_TRY(allreduce(h, dev, 1, 8));
+    CUDA_TRY(cudaMemcpyAsync(&v, dev, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *out = (int64_t)(v + 0.5);
+    return PPCA_OK;
+}
+
+int64_t rows_total(const ppca_handle* h) { return h->ar_fn ? h->n_total : h->x.n; }
+
 ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     const int64_t d = h->x.d;
     const float* src = V;
@@ -306,6 +350,7 @@ ppca_status run_power_seq(ppca_handle* h, int64_t T) {
         float* x = h->V + (size_t)j * d;
         for (int64_t t = 0; t < T; ++t) {
             PPCA_TRY(run_xpass(h, h->x, x, 1, 0, n, h->Z, prime_prec(h)));      // y = X^T X x
+            PPCA_TRY(allreduce(h, h->Z, d, 4));
             CUDA_TRY(power_seq_update(h->V, d, j, h->Z, h->seq_diff, h->stream));
             ++h->iters;
             double diff = 0.0;
@@ -325,6 +370,7 @@ ppca_status run_steps(ppca_handle* h, int64_t T) {
         switch (h->method) {
         case PPCA_POWER:
             PPCA_TRY(run_xpass(h, h->x, h->V, m, 0, n, h->Z, prime_prec(h)));
+            PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // Z over all ranks' rows
             PPCA_TRY(run_orth(h, h->Z, h->V, m));
             ++h->iters;
             break;
@@ -332,9 +378,12 @@ ppca_status run_steps(ppca_handle* h, int64_t T) {
             int64_t r0, r1;
             minibatch(h->t, n, h->params.batch, r0, r1);
             PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
+            PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // the batch of all ranks
+            int64_t b = 0;
+            PPCA_TRY(global_rows(h, r1 - r0, &b));
             CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // S = Y^T Y = W^T Z
             const double lr = h->params.lr / ((double)h->t + h->params.lr_offset);
-            CUDA_TRY(oja_update(h->V, h->Z, h->G, d, m, lr / (double)(r1 - r0), h->stream));
+            CUDA_TRY(oja_update(h->V, h->Z, h->G, d, m, lr / (double)b, h->stream));
             ++h->t;
             break;
         }
@@ -342,8 +391,11 @@ ppca_status run_steps(ppca_handle* h, int64_t T) {
             int64_t r0, r1;
             minibatch(h->t, n, h->params.batch, r0, r1);
             PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
+            PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // the batch of all ranks
+            int64_t b = 0;
+            PPCA_TRY(global_rows(h, r1 - r0, &b));
             CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // C = V^T Z
-            CUDA_TRY(eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)(r1 - r0), h->params.lr,
+            CUDA_TRY(eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)b, h->params.lr,
                                       h->params.momentum, h->eg, h->stream));
             ++h->t;
             break;
@@ -524,8 +576,10 @@ ppca_status ppca_finalize(ppca_handle* h, int32_t k, float* E, double* lambda, p
     PPCA_TRY(run_orth(h, h->V, h->Q, m));                                          // step 2: span
     const XView& xf = h->has_ref ? h->xref : h->x;
     PPCA_TRY(run_gram(h, xf, h->Q, m, 0, n, h->G, prec));                          // step 3: G = (XQ)^T XQ
+    PPCA_TRY(allreduce(h, h->G, (int64_t)m * m, 8));                               // over all ranks' rows
     CUDA_TRY(eigh_small(h->G, m, h->w, h->U, h->jac, h->status, h->stream));       // step 4: full-PCA
-    CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)n, E, lambda, h->stream));   // step 5
+    CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)rows_total(h), E, lambda,
+                             h->stream));                                          // step 5
     return PPCA_OK;
 }
 
@@ -598,6 +652,8 @@ ppca_status ppca_finalize_sampled(ppca_handle* h, int32_t k, float* E, double* l
     CUDA_TRY(projected_gram_tc_blocks(xf, h->Q, m, h->tile_rows, (int)nsel, h->G, prec, h->sched.flush, h->tc,
                                       h->status, h->num_sms, h->stream));         // step 3 on the sample
     if (ev_end) CUDA_TRY(cudaEventRecord(ev_end, h->stream));
+    PPCA_TRY(allreduce(h, h->G, (int64_t)m * m, 8));                               // each rank's sample
+    PPCA_TRY(global_rows(h, rows, &rows));
     CUDA_TRY(eigh_small(h->G, m, h->w, h->U, h->jac, h->status, h->stream));       // step 4
     CUDA_TRY(rotate_and_sign(h->Q, d, m, h->U, h->w, k, 1.0 / (double)rows, E, lambda, h->stream));
     if (rows_used) *rows_used = rows;
@@ -615,6 +671,7 @@ ppca_status ppca_variance_captured(ppca_handle* h, const float* E, int32_t k, do
     PPCA_TRY(ensure_workspace(h, std::max(k, h->ws_m)));
     const XView& xf = h->has_ref ? h->xref : h->x;
     PPCA_TRY(run_gram(h, xf, E, k, 0, xf.n, h->G, prec));                         // G = (X E)^T (X E)
+    PPCA_TRY(allreduce(h, h->G, (int64_t)k * k, 8));                               // over all ranks' rows
     CUDA_TRY(cudaMemcpy2DAsync(var, sizeof(double), h->G, (size_t)(k + 1) * sizeof(double), sizeof(double), (size_t)k,
                                cudaMemcpyDeviceToDevice, h->stream));              // its diagonal
     return PPCA_OK;
@@ -721,6 +778,27 @@ ppca_status ppca_set_schedule(ppca_handle* h, const ppca_schedule* s) {
     h->sched.kparts = s->kparts;
     h->sched.l2_keep = s->l2_keep;
     h->sched.fp8_mma = s->fp8_mma == 2 ? 0 : 1;
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_allreduce(ppca_handle* h, ppca_allreduce_fn fn, void* ctx, int64_t n_total, void* staging,
+                               int64_t staging_bytes) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    if (!fn) {
+        h->ar_fn = nullptr;
+        h->ar_ctx = h->ar_stage = nullptr;
+        h->ar_stage_bytes = h->n_total = 0;
+        return PPCA_OK;
+    }
+    if (n_total < h->x.n) return fail(PPCA_ERR_INVALID, "n_total = %lld < the local rows %lld", (long long)n_total,
+                                      (long long)h->x.n);
+    if ((staging == nullptr) != (staging_bytes == 0) || staging_bytes < 0)
+        return fail(PPCA_ERR_INVALID, "staging buffer and its size must be given together");
+    h->ar_fn = fn;
+    h->ar_ctx = ctx;
+    h->ar_stage = staging;
+    h->ar_stage_bytes = staging_bytes;
+    h->n_total = n_total;
     return PPCA_OK;
 }
 
