@@ -1309,9 +1309,13 @@ __device__ __forceinline__ void mma_3xtf32_stage(uint32_t d_tmem, uint32_t a_hi,
 }
 
 // Y = X V for FP32 X.  Stage: [A head 16 KB][A residual 16 KB][V head][V residual].
+// Split K: with ksplit > 1 a task is (tile t, K-range ks) and writes its FP32 partial Y rows to
+// Ypart[ks][row][m_pad] (summed and split by ypart_reduce_f32_kernel), so that a minibatch of few
+// row tiles still spreads over the SMs.
 __global__ void __launch_bounds__(kF32Threads, 1)
     xv_f32_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles, int nk,
-                  int m_pad, int stages, float* __restrict__ Yt, int64_t ldy, int* status) {
+                  int m_pad, int stages, float* __restrict__ Yt, int64_t ldy, int ksplit, float* __restrict__ Ypart,
+                  int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t a_bytes = 128u * 128u;
@@ -1328,8 +1332,10 @@ __global__ void __launch_bounds__(kF32Threads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int k = 0; k < nk; ++k, ++it) {
+            for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x) {
+                const int t = task / ksplit, ks = task % ksplit;
+                const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
+                for (int k = k0; k < k1; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
                         *abort_flag = 1;
@@ -1353,14 +1359,16 @@ __global__ void __launch_bounds__(kF32Threads, 1)
             const uint32_t idesc = tc::idesc_tf32(128, m_pad);
             uint32_t it = 0, tl = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tl) {
+            for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x, ++tl) {
+                const int ks = task % ksplit;
+                const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
                 const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
                     *abort_flag = 1;
                     break;
                 }
                 tc::fence_after_sync();
-                for (int k = 0; k < nk; ++k, ++it) {
+                for (int k = k0; k < k1; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->xform[s], ph, status) || *abort_flag) {
                         *abort_flag = 1;
@@ -1370,7 +1378,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                     tc::fence_after_sync();
                     const uint32_t a = tc::smem_u32(tiles + (size_t)s * stage_bytes);
                     mma_3xtf32_stage(tmem + b * (uint32_t)m_pad, a, a + a_bytes, a + 2 * a_bytes,
-                                     a + 2 * a_bytes + b_piece, idesc, k == 0);
+                                     a + 2 * a_bytes + b_piece, idesc, k == k0);
                     tc::mma_commit(&hd->empty[s]);
                 }
                 if (ok) tc::mma_commit(&hd->tfull[b]);
@@ -1379,7 +1387,8 @@ __global__ void __launch_bounds__(kF32Threads, 1)
     } else if (warp < 6) {
         const int q = warp & 3;
         uint32_t tl = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
+        for (int task = blockIdx.x; task < ntiles * ksplit; task += gridDim.x, ++tl) {
+            const int t = task / ksplit, ks = task % ksplit;
             const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
             if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
                 *abort_flag = 1;
@@ -1391,12 +1400,20 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                 uint32_t r[32];
                 tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)m_pad + (uint32_t)c0, r);
                 tc::tmem_ld_wait();
+                if (ksplit == 1) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float y = __uint_as_float(r[j]);
-                    const float hi = tc::tf32_rna(y);
-                    Yt[(int64_t)(c0 + j) * ldy + row] = hi;
-                    Yt[(int64_t)(m_pad + c0 + j) * ldy + row] = y - hi;
+                    for (int j = 0; j < 32; ++j) {
+                        const float y = __uint_as_float(r[j]);
+                        const float hi = tc::tf32_rna(y);
+                        Yt[(int64_t)(c0 + j) * ldy + row] = hi;
+                        Yt[(int64_t)(m_pad + c0 + j) * ldy + row] = y - hi;
+                    }
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(Ypart + ((int64_t)ks * ldy + row) * m_pad + c0);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                             __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
                 }
             }
             tc::fence_before_sync();
@@ -1406,9 +1423,11 @@ __global__ void __launch_bounds__(kF32Threads, 1)
         // transform: round the X tile to TF32 in place, residual into the next 16 KB
         const int tid = threadIdx.x - 192;
         uint32_t it = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int task = blockIdx.x; task < ntiles * ksplit; task += gridDim.x) {
+            const int ks = task % ksplit;
+            const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
             bool ok = true;
-            for (int k = 0; k < nk; ++k, ++it) {
+            for (int k = k0; k < k1; ++k, ++it) {
                 const uint32_t s = it % stages, ph = (it / stages) & 1u;
                 if (!tc::mbar_wait(&hd->full[s], ph, status) || *abort_flag) {
                     *abort_flag = 1;
@@ -1633,6 +1652,21 @@ __global__ void ypart_reduce_kernel(const float* __restrict__ Ypart, int ksplit,
         float acc = 0.f;
         for (int ks = 0; ks < ksplit; ++ks) acc += Ypart[(int64_t)ks * total + e];
         split_store<S>(acc, Yt + (int64_t)c * ldy + row, (int64_t)m_pad * ldy);
+    }
+}
+
+// FP32 data: Y = sum over the K-ranges of the split-K partials, then its TF32 head and FP32 residual.
+__global__ void ypart_reduce_f32_kernel(const float* __restrict__ Ypart, int ksplit, int64_t ldy, int m_pad,
+                                        float* __restrict__ Yt) {
+    const int64_t total = ldy * m_pad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / m_pad;
+        const int c = (int)(e % m_pad);
+        float acc = 0.f;
+        for (int ks = 0; ks < ksplit; ++ks) acc += Ypart[(int64_t)ks * total + e];
+        const float hi = tc::tf32_rna(acc);
+        Yt[(int64_t)c * ldy + row] = hi;
+        Yt[(int64_t)(m_pad + c) * ldy + row] = acc - hi;
     }
 }
 
@@ -2029,9 +2063,28 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(F32Header);
         e = cudaFuncSetAttribute(xv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        const int grid = ntiles < num_sms ? ntiles : num_sms;
+        // few row tiles (a minibatch) and a long K: split K so that every SM has work
+        int ksplit = 1;
+        if (ntiles * 2 <= num_sms && nk >= 8) {
+            ksplit = (2 * num_sms + ntiles - 1) / ntiles;
+            ksplit = std::min(ksplit, nk / 4);
+            const int64_t cap = (int64_t)(sc.z_bytes / ((size_t)ldy * m_pad * sizeof(float)));
+            ksplit = (int)std::min<int64_t>(ksplit, cap);
+            if (ksplit < 2) ksplit = 1;
+        }
+        const int ntask = ntiles * ksplit;
+        const int grid = ntask < num_sms ? ntask : num_sms;
+        float* Ypart = static_cast<float*>(sc.zacc);
         note_launch();
-        xv_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages, Yt, ldy, status);
+        xv_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages, Yt, ldy, ksplit, Ypart,
+                                                       status);
+        if (ksplit > 1) {
+            const int64_t total = ldy * m_pad;
+            int blocks = (int)((total + 255) / 256);
+            if (blocks > 4096) blocks = 4096;
+            note_launch();
+            ypart_reduce_f32_kernel<<<blocks, 256, 0, st>>>(Ypart, ksplit, ldy, m_pad, Yt);
+        }
     }
     int Sg;
     {

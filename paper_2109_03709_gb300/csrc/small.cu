@@ -986,96 +986,112 @@ __global__ void sign_kernel(float* __restrict__ E, int64_t d, const double* __re
 
 // ------------------------------------------------------------------ Oja / Sanger
 
-constexpr int kRowThreads = 64;
 
+// W[r][j] += c (Z[r][j] - sum_{l <= j} W[r][l] S[l][j]) with S = Y^T Y: one thread per
+// (row, column), kOjaRows rows of W and S (as FP32) staged in shared memory per CTA.
+constexpr int kOjaRows = 8;
 __global__ void oja_update_kernel(float* __restrict__ W, const float* __restrict__ Z, const double* __restrict__ S,
                                   int64_t d, int m, float c) {
     extern __shared__ float sm[];
     float* Ss = sm;                        // m x m (row-major)
-    float* w = sm + m * m;                 // m x kRowThreads
+    float* w = sm + m * m;                 // kOjaRows x m, the old rows of W
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ss[e] = (float)S[e];
+    const int64_t r0 = (int64_t)blockIdx.x * kOjaRows;
+    for (int e = threadIdx.x; e < kOjaRows * m; e += blockDim.x) {
+        const int i = e / m, j = e % m;
+        w[e] = r0 + i < d ? W[(int64_t)j * d + r0 + i] : 0.f;
+    }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= d) return;
-    const int t = threadIdx.x;
-    for (int j = 0; j < m; ++j) w[j * kRowThreads + t] = W[(int64_t)j * d + r];
-    for (int j = 0; j < m; ++j) {
+    for (int e = threadIdx.x; e < kOjaRows * m; e += blockDim.x) {
+        const int i = e % kOjaRows, j = e / kOjaRows;      // consecutive threads: consecutive rows (coalesced)
+        const int64_t r = r0 + i;
+        if (r >= d) continue;
+        const float* wr = w + i * m;
         float acc = 0.f;
-        for (int l = 0; l <= j; ++l) acc = __fmaf_rn(w[l * kRowThreads + t], Ss[l * m + j], acc);
-        const float z = Z[(int64_t)j * d + r];
-        W[(int64_t)j * d + r] = w[j * kRowThreads + t] + c * (z - acc);
+        for (int l = 0; l <= j; ++l) acc = __fmaf_rn(wr[l], Ss[l * m + j], acc);
+        W[(int64_t)j * d + r] = wr[j] + c * (Z[(int64_t)j * d + r] - acc);
     }
 }
 
 // ------------------------------------------------------------------ EigenGame
 
 // coef[i][j] = C_ij / C_ii (i < j), alpha_j = 2 C_jj - 2 sum_{i<j} C_ij^2 / C_ii, C scaled by 1/b.
+// One block per column j: thread i forms the term of player i, the block sums alpha_j (FP64).
+constexpr int kCoefThreads = 128;
 __global__ void eg_coef_kernel(const double* __restrict__ C, int m, double inv_b, float* __restrict__ coef,
                                float* __restrict__ alpha) {
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
+    __shared__ double red[kCoefThreads / 32];
+    const int j = blockIdx.x;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         const double cii = C[i * m + i] * inv_b;
         const double cij = 0.5 * (C[i * m + j] + C[j * m + i]) * inv_b;
-        coef[e] = (i < j && cii != 0.0) ? (float)(cij / cii) : 0.f;
+        const bool use = i < j && cii != 0.0;
+        const double q = use ? cij / cii : 0.0;
+        coef[i * m + j] = (float)q;
+        if (use) part += cij * q;
     }
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        double a = 2.0 * C[j * m + j] * inv_b;
-        for (int i = 0; i < j; ++i) {
-            const double cii = C[i * m + i] * inv_b;
-            const double cij = 0.5 * (C[i * m + j] + C[j * m + i]) * inv_b;
-            if (cii != 0.0) a -= 2.0 * cij * cij / cii;
-        }
-        alpha[j] = (float)a;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int w = 0; w < kCoefThreads / 32; ++w) sum += red[w];
+        alpha[j] = (float)(2.0 * C[j * m + j] * inv_b - 2.0 * sum);
     }
 }
 
-// Column norms: each block writes, per column, the double-float sum of its
-// rows' squares (exact FMA squares, a fixed shuffle tree per warp, the warps
-// in order); colnorm_reduce_kernel adds the blocks' sums.  All in FP32
-// arithmetic: GB300's FP64 rate is a small fraction of its FP32 rate.
+// One EigenGame step for `rows` rows of V per CTA, one thread per (row, player):
+// g_j = 2 (Z_j / b) - 2 sum_{i<j} coef_ij (Z_i / b) - alpha_j v_j (the utility gradient
+// with the Riemannian projection folded into alpha), Nesterov: buf <- mu buf + g,
+// v <- v + lr (mu buf + g); then each column's squared norm over the CTA's rows as a
+// double-float partial (colpart[block][j]).
+// (16 rows per CTA for short bases, 64 for tall ones, where the m x m coefficients
+// every CTA stages would otherwise dominate the traffic.)
+inline int eg_rows_per_block(int64_t d) { return d >= 65536 ? 64 : 16; }
+
 __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, const float* __restrict__ Z,
                                const float* __restrict__ coef_g, const float* __restrict__ alpha_g, int64_t d, int m,
-                               float inv_b, float lr, float mu, float2* __restrict__ colpart) {
+                               int rows, float inv_b, float lr, float mu, float2* __restrict__ colpart) {
     extern __shared__ float sm[];
     float* coef = sm;                      // m x m
     float* alpha = coef + m * m;           // m
-    float* mv = alpha + m;                 // m x kRowThreads
-    __shared__ float2 red[kRowThreads / 32][kMaxM];
+    float* mv = alpha + m;                 // rows x m: Z rows / b
+    float* vn = mv + rows * m;             // rows x m: the new rows of V
+    const int64_t r0 = (int64_t)blockIdx.x * rows;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) coef[e] = coef_g[e];
     for (int e = threadIdx.x; e < m; e += blockDim.x) alpha[e] = alpha_g[e];
+    for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+        const int i = e % rows, j = e / rows;      // consecutive threads: consecutive rows
+        mv[i * m + j] = r0 + i < d ? Z[(int64_t)j * d + r0 + i] * inv_b : 0.f;
+    }
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int t = threadIdx.x;
-    const bool live = r < d;
-    if (live)
-        for (int j = 0; j < m; ++j) mv[j * kRowThreads + t] = Z[(int64_t)j * d + r] * inv_b;
-    for (int j = 0; j < m; ++j) {
-        float vn = 0.f;
-        if (live) {
-            float g = 2.f * mv[j * kRowThreads + t];
-            for (int i = 0; i < j; ++i) g = __fmaf_rn(-2.f * coef[i * m + j], mv[i * kRowThreads + t], g);
+    for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+        const int i = e % rows, j = e / rows;
+        const int64_t r = r0 + i;
+        float out = 0.f;
+        if (r < d) {
+            const float* mr = mv + i * m;
+            float g = 2.f * mr[j];
+            for (int l = 0; l < j; ++l) g = __fmaf_rn(-2.f * coef[l * m + j], mr[l], g);
             const float v = V[(int64_t)j * d + r];
             g = __fmaf_rn(-alpha[j], v, g);                       // Riemannian projection
             const float b = __fmaf_rn(mu, buf[(int64_t)j * d + r], g);
             buf[(int64_t)j * d + r] = b;
-            vn = __fmaf_rn(lr, __fmaf_rn(mu, b, g), v);           // Nesterov step
-            V[(int64_t)j * d + r] = vn;
+            out = __fmaf_rn(lr, __fmaf_rn(mu, b, g), v);          // Nesterov step
+            V[(int64_t)j * d + r] = out;
         }
-        // this block's part of the column's squared norm
-        const float p = __fmul_rn(vn, vn);
-        dfloat q = df_norm(p, __fmaf_rn(vn, vn, -p));
-        for (int o = 16; o > 0; o >>= 1) {
-            dfloat r;
-            r.hi = __shfl_down_sync(0xffffffffu, q.hi, o);
-            r.lo = __shfl_down_sync(0xffffffffu, q.lo, o);
-            q = df_addx(q, r);
-        }
-        if ((t & 31) == 0) red[t >> 5][j] = make_float2(q.hi, q.lo);
+        vn[i * m + j] = out;
     }
     __syncthreads();
+    // this block's part of each column's squared norm (squares exact as hi + lo)
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
-        dfloat q = df_norm(red[0][j].x, red[0][j].y);
-        for (int w = 1; w < kRowThreads / 32; ++w) q = df_addx(q, df_norm(red[w][j].x, red[w][j].y));
+        dfloat q = {0.f, 0.f};
+        for (int i = 0; i < rows; ++i) {
+            const float x = vn[i * m + j];
+            const float p = __fmul_rn(x, x);
+            q = df_addx(q, df_norm(p, __fmaf_rn(x, x, -p)));
+        }
         colpart[(int64_t)blockIdx.x * m + j] = make_float2(q.hi, q.lo);
     }
 }
@@ -1485,18 +1501,19 @@ cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, c
 }
 
 cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c, cudaStream_t st) {
-    const size_t smem = (size_t)m * m * sizeof(float) + (size_t)m * kRowThreads * sizeof(float);
+    const size_t smem = ((size_t)m * m + (size_t)kOjaRows * m) * sizeof(float);
     cudaError_t e = allow_smem(oja_update_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    oja_update_kernel<<<ceil_div_i(d, kRowThreads), kRowThreads, smem, st>>>(W, Z, S, d, m, (float)c);
+    oja_update_kernel<<<ceil_div_i(d, kOjaRows), 256, smem, st>>>(W, Z, S, d, m, (float)c);
     return cudaGetLastError();
 }
 
 cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double* C, int64_t d, int m, double inv_b,
                              double lr, double mu, double* colnorm, cudaStream_t st) {
     // colnorm scratch layout: [coef m*m f32][alpha m f32][inv m float2][partials nblk*m float2]
-    const int nblk = ceil_div_i(d, kRowThreads);
+    const int rows = eg_rows_per_block(d);
+    const int nblk = ceil_div_i(d, rows);
     char* p = reinterpret_cast<char*>(colnorm);
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     float* coef = reinterpret_cast<float*>(p);
@@ -1507,12 +1524,12 @@ cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double*
     p += al((size_t)m * 8);
     float2* part = reinterpret_cast<float2*>(p);
     note_launch();
-    eg_coef_kernel<<<1, 256, 0, st>>>(C, m, inv_b, coef, alpha);
-    const size_t smem = (size_t)m * m * 4 + (size_t)m * 4 + (size_t)m * kRowThreads * 4;
+    eg_coef_kernel<<<m, kCoefThreads, 0, st>>>(C, m, inv_b, coef, alpha);
+    const size_t smem = ((size_t)m * m + (size_t)m + 2 * (size_t)rows * m) * 4;
     cudaError_t e = allow_smem(eg_step_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    eg_step_kernel<<<nblk, kRowThreads, smem, st>>>(V, buf, Z, coef, alpha, d, m, (float)inv_b, (float)lr,
+    eg_step_kernel<<<nblk, 256, smem, st>>>(V, buf, Z, coef, alpha, d, m, rows, (float)inv_b, (float)lr,
                                                      (float)mu, part);
     note_launch();
     colnorm_reduce_kernel<<<m, kNormThreads, 0, st>>>(part, nblk, m, inv);
@@ -1524,7 +1541,7 @@ cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double*
 size_t eigengame_scratch_bytes(int64_t d, int m) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     return al((size_t)m * m * 4) + al((size_t)m * 4) + al((size_t)m * 8) +
-           al((size_t)ceil_div_i(d, kRowThreads) * m * 8);
+           al((size_t)ceil_div_i(d, eg_rows_per_block(d)) * m * 8);
 }
 
 cudaError_t init_gaussian(float* V, int64_t d, int m, uint64_t seed, cudaStream_t st) {
