@@ -66,6 +66,9 @@ def parse_args(argv=None):
     ap.add_argument("--tune-eg-lr", action="store_true",
                     help="run the EigenGame learning-rate grid of the workload and print the choice")
     ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--batch-slots", type=int, default=16, help="batch workload: concurrent slots (streams)")
+    ap.add_argument("--batch-priming", choices=["bf16", "f32"], default="bf16",
+                    help="batch workload: data type of the priming passes over the FP32 instances")
     ap.add_argument("--runs", type=int, default=10, help="paper_synthetic: runs per method")
     ap.add_argument("--eg-steps", type=int, default=3000, help="paper_synthetic: EigenGame step budget")
     ap.add_argument("--oja-steps", type=int, default=500, help="paper_synthetic: Oja step budget")
@@ -908,9 +911,14 @@ def run_batch(args):
         inst.append({"X": X, "k": k, "m": m, "T": T, "V0": V0,
                      "E": torch.empty((k, d), dtype=torch.float32, device="cuda"),
                      "lam": torch.empty(k, dtype=torch.float64, device="cuda")})
-        total_bytes += (T + 1) * n * d * 4
+        # bytes of X each run reads: FP32 priming, T passes + the pPCA step over FP32 X; BF16
+        # priming, the rounding (FP32 read, BF16 written), T passes over BF16, the pPCA step over FP32
+        total_bytes += (T + 1) * n * d * 4 if args.batch_priming == "f32" else (4 + 2 + 2 * T + 4) * n * d
     stream = torch.cuda.current_stream()
-    b = P.ppca_batch_create(inst, slots=8, stream=stream)
+    b = P.ppca_batch_create(inst, slots=args.batch_slots, stream=stream)
+    bf16_priming = args.batch_priming == "bf16"
+    if bf16_priming:
+        P.ppca_batch_set_priming(b, P.PPCA_BF16)
     t_tune = time.perf_counter()
     groups = P.ppca_batch_autotune(b, 2)
     t_tune = time.perf_counter() - t_tune
@@ -937,7 +945,9 @@ def run_batch(args):
             "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": 8,
+            "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": args.batch_slots,
+                       "priming": ("FP32 X rounded to BF16 each run, BF16 fast passes; pPCA step on FP32 X"
+                                   if bf16_priming else "FP32 X, 3xTF32 fast passes; pPCA step on FP32 X"),
                        "autotune": {"groups": groups, "seconds": round(t_tune, 1)},
                        "bytes_per_step": total_bytes, "form": "one CUDA-graph launch per step",
                        "l2": f"inputs ({sum(i['X'].numel() * 4 for i in inst) / 1e9:.0f} GB) larger than L2, "

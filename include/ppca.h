@@ -435,6 +435,20 @@ PPCA_API ppca_status ppca_batch_run(ppca_batch *b);
  */
 PPCA_API ppca_status ppca_batch_autotune(ppca_batch *b, int32_t reps, int32_t *groups);
 
+/*
+ * Data type the batch's FP32 instances are primed in: PPCA_F32 (the default:
+ * the priming passes read X as given) or PPCA_BF16 (each run first rounds
+ * every FP32 instance's X to BF16, round to nearest even, into a buffer of its
+ * slot -- this call allocates them, for the largest FP32 instance of each slot
+ * -- primes on that rounding with the BF16 fast passes, and runs the pPCA step
+ * on the FP32 X at split precision).  The paper does not vary the precision;
+ * this is the library's use of Algorithm 1's structure: only span(V) carries
+ * from the priming to the pPCA step, which reads the data as stored.  Call
+ * before ppca_batch_autotune and the first ppca_batch_run (PPCA_ERR_STATE
+ * after them).
+ */
+PPCA_API ppca_status ppca_batch_set_priming(ppca_batch *b, int32_t dtype);
+
 /* Kernel launches one ppca_batch_run performs (the kernels captured in its graph;
  * 0 before the first run).  Measurement infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_batch_kernel_count(const ppca_batch *b, int64_t *count);

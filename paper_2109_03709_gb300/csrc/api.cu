@@ -1031,6 +1031,8 @@ struct ppca_batch {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;                  // kernel launches captured in the graph
     std::vector<TcSchedule> inst_sched;   // per instance, after ppca_batch_autotune
+    bool prime_bf16 = false;              // FP32 instances primed on a BF16 rounding of X
+    std::vector<void*> prime_buf;         // per slot: that rounding, for its largest FP32 instance
 };
 
 namespace {
@@ -1048,6 +1050,7 @@ void free_batch(ppca_batch* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto* h : b->slots) free_slot(h);
+    for (auto p : b->prime_buf) cudaFree(p);
     for (auto s : b->slot_streams) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -1066,6 +1069,26 @@ XView view_of(const ppca_instance_desc& ds) {
     x.dtype = (ppca_dtype)ds.dtype;
     x.scales = ds.row_scales;
     return x;
+}
+
+inline int64_t bf16_ld(int64_t d) { return (d + 7) / 8 * 8; }    // 16-byte row pitch
+
+// Point slot h at instance i: its priming data is X itself, or (BF16 priming of FP32
+// data) the BF16 rounding of X enqueued now into the slot's buffer, with X as the
+// pPCA step's refine copy.
+ppca_status bind_instance(ppca_batch* b, ppca_handle* h, int slot, const ppca_instance_desc& ds) {
+    h->x = view_of(ds);
+    h->has_ref = false;
+    if (!b->prime_bf16 || ds.dtype != PPCA_F32) return PPCA_OK;
+    const int64_t ldb = bf16_ld(ds.d);
+    CUDA_TRY(quantize_bf16(static_cast<const float*>(ds.X), ds.n, ds.d, ds.ld,
+                           static_cast<uint16_t*>(b->prime_buf[slot]), ldb, h->stream));
+    h->xref = h->x;
+    h->has_ref = true;
+    h->x.ptr = b->prime_buf[slot];
+    h->x.ld = ldb;
+    h->x.dtype = PPCA_BF16;
+    return PPCA_OK;
 }
 
 }  // namespace
@@ -1160,7 +1183,8 @@ ppca_status ppca_batch_run(ppca_batch* b) {
         for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK; ++i) {
             const ppca_instance_desc& ds = b->descs[i];
             ppca_handle* h = b->slots[i % nslots];
-            h->x = view_of(ds);
+            st = bind_instance(b, h, (int)(i % nslots), ds);
+            if (st != PPCA_OK) break;
             ppca_prime_params prm;
             ppca_prime_params_default(&prm, PPCA_POWER);
             prm.V0 = ds.V0;
@@ -1170,6 +1194,7 @@ ppca_status ppca_batch_run(ppca_batch* b) {
             st = ppca_prime(h, PPCA_POWER, ds.m, ds.T, &prm);
             if (st == PPCA_OK) st = ppca_finalize(h, ds.k, ds.E, ds.lambda, PPCA_PREC_ACCURATE);
             if (st == PPCA_OK && ds.V_out) st = ppca_get_basis(h, ds.V_out);
+            h->has_ref = false;
         }
         for (int s = 0; s < nslots && e == cudaSuccess; ++s) {
             e = cudaEventRecord(b->join[s], b->slot_streams[s]);
@@ -1222,12 +1247,43 @@ ppca_status ppca_batch_autotune(ppca_batch* b, int32_t reps, int32_t* groups) {
     for (size_t g = 0; g < keys.size(); ++g) {
         const int i = keys[g].second;
         ppca_handle* h = b->slots[i % nslots];
-        h->x = view_of(b->descs[i]);
+        PPCA_TRY(bind_instance(b, h, i % nslots, b->descs[i]));       // tune on the priming data
         PPCA_TRY(autotune_handle(h, b->descs[i].m, 0, reps, false, &best[g]));
+        h->has_ref = false;
     }
     b->inst_sched.resize(count);
     for (int i = 0; i < count; ++i) b->inst_sched[i] = best[group_of[i]];
     if (groups) *groups = (int32_t)keys.size();
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_set_priming(ppca_batch* b, int32_t dtype) {
+    if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
+    if (b->exec || !b->inst_sched.empty())
+        return fail(PPCA_ERR_STATE, "set the priming data type before ppca_batch_autotune and the first run");
+    if (dtype != PPCA_F32 && dtype != PPCA_BF16)
+        return fail(PPCA_ERR_INVALID, "priming data type %d: PPCA_F32 or PPCA_BF16", (int)dtype);
+    for (auto p : b->prime_buf) cudaFree(p);
+    b->prime_buf.clear();
+    b->prime_bf16 = dtype == PPCA_BF16;
+    if (!b->prime_bf16) return PPCA_OK;
+    const int nslots = (int)b->slots.size();
+    for (int s = 0; s < nslots; ++s) {
+        size_t bytes = 256;
+        for (size_t i = s; i < b->descs.size(); i += nslots)
+            if (b->descs[i].dtype == PPCA_F32)
+                bytes = std::max(bytes, (size_t)b->descs[i].n * (size_t)bf16_ld(b->descs[i].d) * 2);
+        void* p = nullptr;
+        const cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (auto q : b->prime_buf) cudaFree(q);
+            b->prime_buf.clear();
+            b->prime_bf16 = false;
+            return fail(PPCA_ERR_OOM, "cudaMalloc(%zu) for slot %d's BF16 priming copy failed", bytes, s);
+        }
+        b->prime_buf.push_back(p);
+    }
     return PPCA_OK;
 }
 

@@ -125,3 +125,33 @@ def test_batch_autotuned_matches_oracle(cuda_device):
     with pytest.raises(P.PPCAError) as ei:
         P.ppca_batch_autotune(b)                      # already captured
     assert ei.value.status_name == "PPCA_ERR_STATE"
+
+
+def test_batch_bf16_priming_matches_oracle(cuda_device):
+    """ppca_batch_set_priming(PPCA_BF16): each run rounds every FP32 instance to
+    BF16 (bit-exact round to nearest even), primes on that rounding with the
+    BF16 fast passes, and runs the pPCA step on the FP32 data.  The pPCA step
+    still equals the oracle's on the primed basis (FP32 tolerances), and the
+    primed subspace follows the oracle's FP64 block power on the BF16-rounded
+    data: each fast pass rounds V and Y to BF16 (2^-8 relative), which over
+    T = 10 unconverged iterations moves the subspace by a few 1e-3 rad (bound 3e-2)."""
+    import paper_2109_03709_gb300 as P
+    inst = make_batch(10, seed=505, T=10)
+    b = P.ppca_batch_create(inst, slots=3)
+    P.ppca_batch_set_priming(b, P.PPCA_BF16)
+    P.ppca_batch_run(b)
+    P.ppca_batch_sync(b)
+    worst = 0.0
+    for i, ins in enumerate(inst):
+        Xs = ins["X"].double().cpu().numpy()
+        Vg = host_basis(ins["V_out"])
+        Eo, lo = oracle.ppca_finalize(Xs, Vg, ins["k"])
+        np.testing.assert_allclose(ins["lam"].cpu().numpy(), lo, rtol=1e-5, err_msg=f"instance {i}")
+        assert oracle.angles(host_basis(ins["E"]), Eo).max() <= 1e-4, i
+        Vo = oracle.power_prime(oracle.bf16_round_rne(Xs), host_basis(ins["V0"]), ins["T"])
+        worst = max(worst, oracle.principal_angles(Vg, Vo).max())
+    print("bf16-primed batch: largest principal angle to the oracle's power iterate", worst)
+    assert worst <= 3e-2
+    with pytest.raises(P.PPCAError) as ei:
+        P.ppca_batch_set_priming(b, P.PPCA_F32)       # already captured
+    assert ei.value.status_name == "PPCA_ERR_STATE"
