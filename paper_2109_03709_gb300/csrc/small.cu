@@ -1194,6 +1194,26 @@ __global__ void quantize_bf16_kernel(const float* __restrict__ X, int64_t n, int
     }
 }
 
+// Eight values per thread (two 16-byte loads, one 16-byte store) over the whole
+// matrix as one flat index, for rows whose pitches keep every group of eight aligned.
+__global__ void quantize_bf16_vec8_kernel(const float* __restrict__ X, int64_t n, int64_t d, int64_t ld_in,
+                                          uint16_t* __restrict__ out, int64_t ld_out) {
+    const int64_t per_row = d / 8, total = n * per_row;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / per_row, j = (e - r * per_row) * 8;
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(X + r * ld_in + j));
+        const float4 b = __ldcs(reinterpret_cast<const float4*>(X + r * ld_in + j + 4));
+        __nv_bfloat162 p0 = __floats2bfloat162_rn(a.x, a.y), p1 = __floats2bfloat162_rn(a.z, a.w);
+        __nv_bfloat162 p2 = __floats2bfloat162_rn(b.x, b.y), p3 = __floats2bfloat162_rn(b.z, b.w);
+        uint4 o;
+        o.x = *reinterpret_cast<uint32_t*>(&p0);
+        o.y = *reinterpret_cast<uint32_t*>(&p1);
+        o.z = *reinterpret_cast<uint32_t*>(&p2);
+        o.w = *reinterpret_cast<uint32_t*>(&p3);
+        *reinterpret_cast<uint4*>(out + r * ld_out + j) = o;
+    }
+}
+
 __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t d, int64_t ld_in, uint8_t* __restrict__ out,
                                     int64_t ld_out, float* __restrict__ scales) {
     const int64_t r = blockIdx.x;
@@ -1216,6 +1236,46 @@ __global__ void quantize_fp8_kernel(const float* __restrict__ X, int64_t d, int6
     for (int64_t j = threadIdx.x; j < d; j += blockDim.x) {
         const float q = __fdiv_rn(x[j], s);
         out[r * ld_out + j] = (uint8_t)__nv_cvt_float_to_fp8(q, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+// One row per CTA of 256 threads held in registers (VPT float4 chunks a thread,
+// d % 4 == 0, 16-byte aligned rows): one read of the row for both its maximum and
+// its codes, four codes stored as one 32-bit word.
+template <int VPT>
+__global__ void __launch_bounds__(256) quantize_fp8_vec4_kernel(const float* __restrict__ X, int64_t d,
+                                                                int64_t ld_in, uint8_t* __restrict__ out,
+                                                                int64_t ld_out, float* __restrict__ scales) {
+    const int64_t r = blockIdx.x;
+    const float4* x = reinterpret_cast<const float4*>(X + r * ld_in);
+    const int64_t chunks = d / 4;
+    float4 v[VPT];
+    float amax = 0.f;
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+        const int64_t c = (int64_t)i * 256 + threadIdx.x;
+        v[i] = c < chunks ? __ldcs(x + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[i].x), fabsf(v[i].y)), fmaxf(fabsf(v[i].z), fabsf(v[i].w))));
+    }
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffff, amax, o));
+    __shared__ float wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x / 32] = amax;
+    __syncthreads();
+    amax = wm[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) amax = fmaxf(amax, wm[w]);
+    const float s = amax > 0.f ? __fdiv_rn(amax, 448.0f) : 1.0f;
+    if (threadIdx.x == 0) scales[r] = s;
+    uint32_t* o = reinterpret_cast<uint32_t*>(out + r * ld_out);
+#pragma unroll
+    for (int i = 0; i < VPT; ++i) {
+        const int64_t c = (int64_t)i * 256 + threadIdx.x;
+        if (c >= chunks) break;
+        const uint32_t q0 = __nv_cvt_float_to_fp8(__fdiv_rn(v[i].x, s), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t q1 = __nv_cvt_float_to_fp8(__fdiv_rn(v[i].y, s), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t q2 = __nv_cvt_float_to_fp8(__fdiv_rn(v[i].z, s), __NV_SATFINITE, __NV_E4M3);
+        const uint32_t q3 = __nv_cvt_float_to_fp8(__fdiv_rn(v[i].w, s), __NV_SATFINITE, __NV_E4M3);
+        o[c] = q0 | (q1 << 8) | (q2 << 16) | (q3 << 24);
     }
 }
 
@@ -1555,6 +1615,19 @@ cudaError_t init_gaussian(float* V, int64_t d, int m, uint64_t seed, cudaStream_
 cudaError_t quantize_bf16(const float* X, int64_t n, int64_t d, int64_t ld_in, uint16_t* out, int64_t ld_out,
                           cudaStream_t st) {
     if (n == 0 || d == 0) return cudaSuccess;
+    const bool vec = d % 8 == 0 && ld_in % 4 == 0 && ld_out % 8 == 0 && reinterpret_cast<uintptr_t>(X) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(out) % 16 == 0;
+    if (vec) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t groups = n * (d / 8);
+        const int64_t blocks = std::min<int64_t>((groups + 255) / 256, (int64_t)sms * 8);
+        note_launch();
+        quantize_bf16_vec8_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(X, n, d, ld_in, out,
+                                                                                        ld_out);
+        return cudaGetLastError();
+    }
     const int gx = ceil_div_i(d, 256) > 64 ? 64 : ceil_div_i(d, 256);
     for (int64_t r0 = 0; r0 < n; r0 += 65535) {
         const int64_t rows = (n - r0) < 65535 ? (n - r0) : 65535;
@@ -1568,6 +1641,24 @@ cudaError_t quantize_bf16(const float* X, int64_t n, int64_t d, int64_t ld_in, u
 cudaError_t quantize_fp8(const float* X, int64_t n, int64_t d, int64_t ld_in, uint8_t* out, int64_t ld_out,
                          float* scales, cudaStream_t st) {
     if (n == 0 || d == 0) return cudaSuccess;
+    const bool vec = d % 4 == 0 && d <= 8 * 1024 && ld_in % 4 == 0 && ld_out % 4 == 0 &&
+                     reinterpret_cast<uintptr_t>(X) % 16 == 0 && reinterpret_cast<uintptr_t>(out) % 4 == 0 &&
+                     n <= 2147483647LL;
+    if (vec) {
+        const int vpt = (int)((d / 4 + 255) / 256);
+        note_launch();
+        switch (vpt) {
+        case 1: quantize_fp8_vec4_kernel<1><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 2: quantize_fp8_vec4_kernel<2><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 3: quantize_fp8_vec4_kernel<3><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 4: quantize_fp8_vec4_kernel<4><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 5: quantize_fp8_vec4_kernel<5><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 6: quantize_fp8_vec4_kernel<6><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        case 7: quantize_fp8_vec4_kernel<7><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        default: quantize_fp8_vec4_kernel<8><<<(unsigned)n, 256, 0, st>>>(X, d, ld_in, out, ld_out, scales); break;
+        }
+        return cudaGetLastError();
+    }
     for (int64_t r0 = 0; r0 < n; r0 += 2147483647LL) {
         const int64_t rows = n - r0;
         note_launch();

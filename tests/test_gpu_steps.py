@@ -380,16 +380,21 @@ def test_eigh_small(P, m):
         assert oracle.angle(U[:, i], Uref[:, i]) <= 16 * u * wref[0] / gaps[i] + 1e-6
 
 
-def test_quantize_bf16_bit_exact(P):
+@pytest.mark.parametrize("n,d,ldo", [(257, 300, 304), (1000, 512, 512), (33, 1024, 1032)])
+def test_quantize_bf16_bit_exact(P, n, d, ldo):
+    """Round to nearest even, bit for bit: the oracle's codec and torch's conversion.
+    d % 8 == 0 with 16-byte pitches takes the eight-wide kernel, 300 the scalar one."""
     import torch
     rng = np.random.default_rng(0)
-    X = (rng.standard_normal((257, 300)) * 10.0 ** rng.uniform(-3, 3, (257, 300))).astype(np.float32)
+    X = (rng.standard_normal((n, d)) * 10.0 ** rng.uniform(-3, 3, (n, d))).astype(np.float32)
     Xd = torch.from_numpy(X).cuda()
-    out = torch.empty((257, 304), dtype=torch.int16, device="cuda")[:, :300]
+    out = torch.empty((n, ldo), dtype=torch.int16, device="cuda")[:, :d]
     P.ppca_quantize_bf16(Xd, out)
     torch.cuda.synchronize()
     lib = torch.from_numpy(X).to(torch.bfloat16).view(torch.int16).numpy()
     np.testing.assert_array_equal(out.cpu().numpy(), lib)
+    got = oracle.bf16_bits_to_f64(out.cpu().numpy().view(np.uint16))
+    np.testing.assert_array_equal(got, oracle.bf16_round_rne(X))
 
 
 FP8_CASES = [
@@ -447,14 +452,17 @@ def test_xpass_fp8_tensor_cores(P, n, d, m, r0, r1, prec, tol):
         assert split_ratio(host_basis(Zd), X8, host_basis(Vd), *tau_split(d), row_factor=s2) <= 1.0
 
 
-def test_quantize_fp8_bit_exact(P):
+@pytest.mark.parametrize("d,ldo", [(520, 528), (4096, 4096), (7, 16), (2050, 2064)])
+def test_quantize_fp8_bit_exact(P, d, ldo):
+    """Per-row scale and E4M3 codes bit for bit against the oracle's codec; d % 4 == 0
+    with aligned pitches takes the register-held row kernel, 7 the general one."""
     import torch
     rng = np.random.default_rng(1)
-    X = (rng.standard_normal((129, 520)) * 10.0 ** rng.uniform(-2, 2, (129, 1))).astype(np.float32)
+    X = (rng.standard_normal((129, d)) * 10.0 ** rng.uniform(-2, 2, (129, 1))).astype(np.float32)
     X[7] = 0.0
     X[8, 3] = 1e-30
     Xd = torch.from_numpy(X).cuda()
-    out = torch.empty((129, 528), dtype=torch.uint8, device="cuda")[:, :520]
+    out = torch.empty((129, ldo), dtype=torch.uint8, device="cuda")[:, :d]
     sc = torch.empty(129, dtype=torch.float32, device="cuda")
     P.ppca_quantize_fp8(Xd, out, sc)
     torch.cuda.synchronize()
