@@ -469,7 +469,9 @@ def measure_primers(cfg):
     Etrue, wtrue = lces_truth(X, k)
     out = {"n": n, "d": d, "k": k, "l": cfg.l, "tol_rad": cfg.angle_tol, "eig_rtol": cfg.eig_rtol,
            "truth": "FP64 eigh of X^T X (FP32 cuBLAS GEMMs over 1024-row chunks summed in FP64)",
-           "truth_s": round(time.perf_counter() - t0, 1)}
+           "truth_s": round(time.perf_counter() - t0, 1),
+           "parity": "each primer + pPCA step against the oracle's own run of it (same streak at 1e-4 rad and "
+                     "on the grid, largest angle within 10 %): tests/test_gpu_primers_compared.py"}
     V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, cfg.seed).T, dtype=np.float32)).cuda()
     E = torch.empty((k, d), dtype=torch.float32, device="cuda")
     lam = torch.empty(k, dtype=torch.float64, device="cuda")
@@ -501,7 +503,7 @@ def measure_primers(cfg):
         if method != P.PPCA_POWER:
             # the primer alone: its first k directions in order (Oja/Sanger and EigenGame order them)
             rec["primer_alone_lces_grid"] = {lab: int(lces_of(Vb[:k], Etrue, v)[0]) for lab, v in PAPER_GRID}
-        rec["within_tolerance"] = bool(streak == k and rec["eig_rel_err_max"] <= cfg.eig_rtol)
+        rec["meets_tolerance_vs_truth"] = bool(streak == k and rec["eig_rel_err_max"] <= cfg.eig_rtol)
         out[name] = rec
         del h
     del X
@@ -545,11 +547,10 @@ def measure_large_d_quality(cfg):
            "truth": "FP64 Rayleigh-Ritz of a 128-wide FP32 block subspace iteration (cuBLAS/cuSOLVER), "
                     "residual-certified", "truth_angle_bound_max": float(np.max(bound)),
            "truth_s": round(time.perf_counter() - t0, 1),
-           "within_tolerance": False,
            "method_limit": "the oracle's own FP64 EigenGame on the d = 4096 analogue (same spectrum formula, "
                            "generator and schedule) reaches the same streak as this path and stays short of k "
                            "(tests/test_gpu_eigengame_large_d.py)"}
-    out["within_tolerance"] = bool(streak == k and out["eig_rel_err_max"] <= cfg.eig_rtol)
+    out["meets_tolerance_vs_truth"] = bool(streak == k and out["eig_rel_err_max"] <= cfg.eig_rtol)
     del h, X
     torch.cuda.empty_cache()
     return out
@@ -888,20 +889,16 @@ def tune_eg_lr(args):
     print(json.dumps({"workload": cfg.name, "chosen_lr": best[0] if best else None}))
 
 
-def run_batch(args):
-    """The ragged batch workload: 512 independent problems, one graph launch per step."""
+def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup):
+    """The ragged batch: `count` independent problems (n ~ U[2000, 200000], d in {64, ..., 2048},
+    k ~ U[4, 32], l = k, lambda_i = rho^i), block power T + the pPCA step each, one CUDA-graph
+    launch per run.  Returns the run's device time and the bytes of X it reads."""
     import numpy as np
     import torch
 
     import paper_2109_03709_gb300 as P
     import synth
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    cfg = synth.CONFIGS[args.workload]
-    T = cfg.primers["power"]["T"]
-    shapes = synth.batch_instances(512, cfg.seed + 1000 * rank)
-    if args.rows:
-        shapes = shapes[:args.rows]
+    shapes = synth.batch_instances(512, seed)[:count]
     inst = []
     total_bytes = 0
     for s in shapes:
@@ -913,52 +910,108 @@ def run_batch(args):
                      "lam": torch.empty(k, dtype=torch.float64, device="cuda")})
         # bytes of X each run reads: FP32 priming, T passes + the pPCA step over FP32 X; BF16
         # priming, the rounding (FP32 read, BF16 written), T passes over BF16, the pPCA step over FP32
-        total_bytes += (T + 1) * n * d * 4 if args.batch_priming == "f32" else (4 + 2 + 2 * T + 4) * n * d
+        total_bytes += (T + 1) * n * d * 4 if not bf16_priming else (4 + 2 + 2 * T + 4) * n * d
     stream = torch.cuda.current_stream()
-    b = P.ppca_batch_create(inst, slots=args.batch_slots, stream=stream)
-    bf16_priming = args.batch_priming == "bf16"
+    b = P.ppca_batch_create(inst, slots=slots, stream=stream)
     if bf16_priming:
         P.ppca_batch_set_priming(b, P.PPCA_BF16)
     t_tune = time.perf_counter()
     groups = P.ppca_batch_autotune(b, 2)
     t_tune = time.perf_counter() - t_tune
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         P.ppca_batch_run(b)
     P.ppca_batch_sync(b)
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         P.ppca_batch_run(b)
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
     P.ppca_batch_sync(b)
-    kernels = P.ppca_batch_kernel_count(b)
-    ms = e0.elapsed_time(e1)
+    ms = e0.elapsed_time(e1) / steps
+    rec = {"instances": len(inst), "T": T, "slots": slots,
+           "priming": ("FP32 X rounded to BF16 each run, BF16 fast passes; pPCA step on FP32 X"
+                       if bf16_priming else "FP32 X, 3xTF32 fast passes; pPCA step on FP32 X"),
+           "autotune": {"groups": groups, "seconds": round(t_tune, 1)},
+           "bytes_per_step": total_bytes, "ms_per_step": round(ms, 3),
+           "gbs": round(total_bytes / (ms / 1e3) / 1e9, 1), "kernels_per_run": P.ppca_batch_kernel_count(b),
+           "data_gb": round(sum(i["X"].numel() * 4 for i in inst) / 1e9, 1)}
+    del b, inst
+    torch.cuda.empty_cache()
+    return rec
+
+
+def run_batch(args):
+    """The ragged batch workload: 512 independent problems, one graph launch per step."""
+    import torch
+
+    import synth
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    cfg = synth.CONFIGS[args.workload]
+    T = cfg.primers["power"]["T"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    rec = measure_batch(cfg, T, args.rows or 512, cfg.seed + 1000 * rank, args.batch_slots,
+                        args.batch_priming == "bf16", args.steps, args.warmup)
+    clk = clocks.stop()
     peaks, peak_kind = measured_peaks()
-    value = total_bytes * args.steps / (ms / 1e3) / 1e9
+    value = rec["gbs"] * ws
     line = {"metric": "X-pass HBM GB/s; time to LCES=k (BF16 vs FP32, same GPU, angle tol)",
             "value": round(value, 1), "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": cfg.name, "instances": len(inst), "T": T, "slots": args.batch_slots,
-                       "priming": ("FP32 X rounded to BF16 each run, BF16 fast passes; pPCA step on FP32 X"
-                                   if bf16_priming else "FP32 X, 3xTF32 fast passes; pPCA step on FP32 X"),
-                       "autotune": {"groups": groups, "seconds": round(t_tune, 1)},
-                       "bytes_per_step": total_bytes, "form": "one CUDA-graph launch per step",
-                       "l2": f"inputs ({sum(i['X'].numel() * 4 for i in inst) / 1e9:.0f} GB) larger than L2, "
-                             "no flush"},
+            "config": {"workload": cfg.name, "instances": rec["instances"], "T": T, "slots": rec["slots"],
+                       "priming": rec["priming"], "autotune": rec["autotune"],
+                       "bytes_per_step": rec["bytes_per_step"], "form": "one CUDA-graph launch per step",
+                       "l2": f"inputs ({rec['data_gb']:.0f} GB) larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": round(value, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(value / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": peak_kind,
-                         "kernel": "whole batch step: 3xTF32 priming passes, projected-Gram pPCA step, "
+                         "kernel": "whole batch step: priming passes, projected-Gram pPCA step, "
                                    "CholeskyQR2 and Jacobi per instance"},
-            "clocks": clk, "gpu_launches": kernels * args.steps}
+            "clocks": clk, "gpu_launches": rec["kernels_per_run"] * args.steps}
     if rank == 0:
         print(json.dumps(line))
+
+
+def measure_c1(cfg):
+    """Plain pPCA on the 4096 x 256 FP32 workload: block power (k = l = 8, T = 10) + the pPCA
+    step; streak and angles against the FP64 eigenvectors of X^T X (lces_truth)."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    n, d, k, m = cfg.n, cfg.d, cfg.k, cfg.m
+    X, _ = synth.gaussian_data_torch(n, d, cfg.lam(), cfg.seed, "cuda", torch.float32)
+    Et, wt = lces_truth(X, k)
+    V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, cfg.seed).T, dtype=np.float32)).cuda()
+    E = torch.empty((k, d), dtype=torch.float32, device="cuda")
+    lam = torch.empty(k, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = P.ppca_create(X, stream=stream)
+    prm = P.ppca_prime_params_default(P.PPCA_POWER)
+    prm.precision = P.PPCA_PREC_FAST
+    T = cfg.primers["power"]["T"]
+
+    def solve():
+        P.ppca_prime(h, P.PPCA_POWER, m, T, prm, V0=V0)
+        P.ppca_finalize(h, k, E, lam, P.PPCA_PREC_ACCURATE)
+
+    ms = _solve_ms(solve, stream, reps=5)
+    P.ppca_sync(h)
+    streak, ang = lces_of(E, Et, cfg.angle_tol)
+    rec = {"n": n, "d": d, "k": k, "l": cfg.l, "T": T, "tol_rad": cfg.angle_tol, "eig_rtol": cfg.eig_rtol,
+           "ms": round(ms, 3), "lces": int(streak), "max_angle_rad": float(np.max(ang)),
+           "eig_rel_err_max": float(((lam - wt).abs() / wt).max()),
+           "truth": "FP64 eigh of X^T X (FP32 cuBLAS GEMMs over 1024-row chunks summed in FP64)"}
+    rec["meets_tolerance_vs_truth"] = bool(streak == k and rec["eig_rel_err_max"] <= cfg.eig_rtol)
+    rec["parity"] = ("the pPCA step and the primed subspace against the oracle's own run, and the same streak as "
+                     "the oracle's pipeline: tests/test_gpu_ppca.py (T = 10 leaves direction 8 at ~1.2e-4 rad "
+                     "from the truth for both; T = 20 reaches the full streak)")
+    del h, X
+    return rec
 
 
 def run_ours(args):
@@ -1094,7 +1147,10 @@ def run_ours(args):
     # the other configurations' quality records (one solve each, not the timed headline)
     configs = None
     if rank == 0 and not args.no_configs:
-        configs = {"primers_fp32_100000x1024": measure_primers(synth.CONFIGS["primers_fp32_100000x1024"]),
+        bc = synth.CONFIGS["batch512_fp32"]
+        configs = {"power_fp32_4096x256": measure_c1(synth.CONFIGS["power_fp32_4096x256"]),
+                   "primers_fp32_100000x1024": measure_primers(synth.CONFIGS["primers_fp32_100000x1024"]),
+                   "batch512_fp32": measure_batch(bc, bc.primers["power"]["T"], 512, bc.seed, 16, True, 2, 1),
                    "largeD_bf16_50000x262144": measure_large_d_quality(synth.CONFIGS["largeD_bf16_50000x262144"])}
 
     cpu = None
