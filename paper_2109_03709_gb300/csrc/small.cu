@@ -26,7 +26,7 @@ namespace ppca {
 namespace {
 
 constexpr int kGramTile = 32;        // output tile of gram_df
-constexpr int kGramRows = 128;       // rows of A/B per slice
+constexpr int kGramRows = 32;        // rows of A/B per slice (one tile of 32 rows)
 
 // Row slices of gram_df: one per kGramRows rows, at most 1024 / T^2 (at least
 // 128) for T x T output tiles, so that a narrow basis over many rows still
