@@ -69,6 +69,8 @@ def parse_args(argv=None):
     ap.add_argument("--batch-slots", type=int, default=16, help="batch workload: concurrent slots (streams)")
     ap.add_argument("--batch-priming", choices=["bf16", "f32"], default="bf16",
                     help="batch workload: data type of the priming passes over the FP32 instances")
+    ap.add_argument("--batch-no-lockstep", action="store_true",
+                    help="batch workload: prime every instance on the slots, not in lockstep")
     ap.add_argument("--runs", type=int, default=10, help="paper_synthetic: runs per method")
     ap.add_argument("--eg-steps", type=int, default=3000, help="paper_synthetic: EigenGame step budget")
     ap.add_argument("--oja-steps", type=int, default=500, help="paper_synthetic: Oja step budget")
@@ -889,7 +891,7 @@ def tune_eg_lr(args):
     print(json.dumps({"workload": cfg.name, "chosen_lr": best[0] if best else None}))
 
 
-def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup):
+def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup, lockstep=True):
     """The ragged batch: `count` independent problems (n ~ U[2000, 200000], d in {64, ..., 2048},
     k ~ U[4, 32], l = k, lambda_i = rho^i), block power T + the pPCA step each, one CUDA-graph
     launch per run.  Returns the run's device time and the bytes of X it reads."""
@@ -915,6 +917,7 @@ def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup):
     b = P.ppca_batch_create(inst, slots=slots, stream=stream)
     if bf16_priming:
         P.ppca_batch_set_priming(b, P.PPCA_BF16)
+    P.ppca_batch_set_lockstep(b, lockstep)
     t_tune = time.perf_counter()
     groups = P.ppca_batch_autotune(b, 2)
     t_tune = time.perf_counter() - t_tune
@@ -930,7 +933,7 @@ def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup):
     torch.cuda.synchronize()
     P.ppca_batch_sync(b)
     ms = e0.elapsed_time(e1) / steps
-    rec = {"instances": len(inst), "T": T, "slots": slots,
+    rec = {"instances": len(inst), "T": T, "slots": slots, "lockstep": P.ppca_batch_lockstep(b),
            "priming": ("FP32 X rounded to BF16 each run, BF16 fast passes; pPCA step on FP32 X"
                        if bf16_priming else "FP32 X, 3xTF32 fast passes; pPCA step on FP32 X"),
            "autotune": {"groups": groups, "seconds": round(t_tune, 1)},
@@ -954,7 +957,7 @@ def run_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     rec = measure_batch(cfg, T, args.rows or 512, cfg.seed + 1000 * rank, args.batch_slots,
-                        args.batch_priming == "bf16", args.steps, args.warmup)
+                        args.batch_priming == "bf16", args.steps, args.warmup, not args.batch_no_lockstep)
     clk = clocks.stop()
     peaks, peak_kind = measured_peaks()
     value = rec["gbs"] * ws
@@ -963,7 +966,7 @@ def run_batch(args):
             "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": cfg.name, "instances": rec["instances"], "T": T, "slots": rec["slots"],
-                       "priming": rec["priming"], "autotune": rec["autotune"],
+                       "priming": rec["priming"], "lockstep": rec["lockstep"], "autotune": rec["autotune"],
                        "bytes_per_step": rec["bytes_per_step"], "form": "one CUDA-graph launch per step",
                        "l2": f"inputs ({rec['data_gb']:.0f} GB) larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": round(value, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",

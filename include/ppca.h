@@ -449,6 +449,27 @@ PPCA_API ppca_status ppca_batch_autotune(ppca_batch *b, int32_t reps, int32_t *g
  */
 PPCA_API ppca_status ppca_batch_set_priming(ppca_batch *b, int32_t dtype);
 
+/*
+ * Lockstep priming (enable != 0, the default): when every instance primes on
+ * BF16 data (BF16 X, or FP32 X with ppca_batch_set_priming(PPCA_BF16) and
+ * d % 8 == 0) and all share one T, the first ppca_batch_run captures step 1 of
+ * Algorithm 1 for all instances at once -- the BF16 rounding, V = orth(V0) and
+ * T times (Z = X^T X V on the BF16 tensor cores, V = orth(Z) by CholeskyQR2)
+ * -- one kernel launch per kernel kind and iteration for the whole batch, the
+ * work of the instances dealt out over the launch's blocks; the pPCA step
+ * (steps 2-5) of each instance then runs on the slots as before.  It keeps
+ * per-instance buffers for the whole batch (the BF16 copies of all FP32
+ * instances at once instead of one per slot); when they cannot be allocated,
+ * or the batch is not eligible, the batch primes on its slots.  enable == 0
+ * always primes on the slots.  The paper runs one problem at a time: the
+ * batching has no counterpart in it.  PPCA_ERR_STATE after the first run.
+ */
+PPCA_API ppca_status ppca_batch_set_lockstep(ppca_batch *b, int32_t enable);
+
+/* *active = 1 if the captured graph primes in lockstep, else 0 (also before the
+ * first run).  Infrastructure: no counterpart in the paper. */
+PPCA_API ppca_status ppca_batch_lockstep(const ppca_batch *b, int32_t *active);
+
 /* Kernel launches one ppca_batch_run performs (the kernels captured in its graph;
  * 0 before the first run).  Measurement infrastructure: no counterpart in the paper. */
 PPCA_API ppca_status ppca_batch_kernel_count(const ppca_batch *b, int64_t *count);

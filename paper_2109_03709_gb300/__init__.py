@@ -29,7 +29,8 @@ __all__ = [
     "ppca_timing", "ppca_eigh_noalloc", "ppca_schedule", "ppca_set_schedule", "ppca_instance_desc",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "ppca_set_wait_limit",
-    "ppca_set_allreduce", "TorchAllReduce", "ppca_batch_set_priming", "EXPORTED_SYMBOLS",
+    "ppca_set_allreduce", "TorchAllReduce", "ppca_batch_set_priming", "ppca_batch_set_lockstep",
+    "ppca_batch_lockstep", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -53,7 +54,8 @@ EXPORTED_SYMBOLS = [
     "ppca_eigh_noalloc", "ppca_set_schedule", "ppca_projected_gram", "ppca_autotune", "ppca_batch_autotune",
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured",
-    "ppca_set_wait_limit", "ppca_set_allreduce", "ppca_batch_set_priming",
+    "ppca_set_wait_limit", "ppca_set_allreduce", "ppca_batch_set_priming", "ppca_batch_set_lockstep",
+    "ppca_batch_lockstep",
 ]
 
 
@@ -159,6 +161,8 @@ _SIGS = {
     "ppca_set_wait_limit": (_c_status, [ctypes.c_uint64]),
     "ppca_set_allreduce": (_c_status, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "ppca_batch_set_priming": (_c_status, [_vp, _i32]),
+    "ppca_batch_set_lockstep": (_c_status, [_vp, _i32]),
+    "ppca_batch_lockstep": (_c_status, [_vp, ctypes.POINTER(_i32)]),
     "ppca_autotune": (_c_status, [_vp, _i32, _i64, _i32, ctypes.POINTER(ppca_schedule)]),
     "ppca_batch_autotune": (_c_status, [_vp, _i32, ctypes.POINTER(_i32)]),
     "ppca_batch_create": (_c_status, [ctypes.POINTER(_vp), ctypes.POINTER(ppca_instance_desc), _i32, _i32, _vp]),
@@ -463,6 +467,18 @@ def ppca_batch_run(b: Batch):
 def ppca_batch_set_priming(b: Batch, dtype: int):
     """PPCA_BF16: prime FP32 instances on their BF16 rounding (pPCA step on the FP32 data); PPCA_F32: as given."""
     _check(load_library().ppca_batch_set_priming(b.ptr, dtype), "ppca_batch_set_priming")
+
+
+def ppca_batch_set_lockstep(b: Batch, enable: bool):
+    """Allow (default) or forbid priming every instance in lockstep (grouped launches) at the first run."""
+    _check(load_library().ppca_batch_set_lockstep(b.ptr, 1 if enable else 0), "ppca_batch_set_lockstep")
+
+
+def ppca_batch_lockstep(b: Batch) -> bool:
+    """True if the captured graph primes the instances in lockstep."""
+    a = _i32(0)
+    _check(load_library().ppca_batch_lockstep(b.ptr, ctypes.byref(a)), "ppca_batch_lockstep")
+    return bool(a.value)
 
 
 def ppca_batch_autotune(b: Batch, reps: int = 2) -> int:

@@ -17,6 +17,7 @@
 #include <utility>
 #include <vector>
 
+#include "grouped.h"
 #include "kernels.h"
 #include "pass_tc.h"
 #include "tc_host.h"
@@ -62,6 +63,8 @@ size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
 int dtype_size(ppca_dtype t) { return t == PPCA_F32 ? 4 : (t == PPCA_BF16 ? 2 : 1); }
 
 }  // namespace
+
+ppca_status check_status_word(int* status);
 
 struct ppca_handle {
     XView x;                  // data used by the priming passes
@@ -692,10 +695,18 @@ ppca_status ppca_finalize_host(ppca_handle* h, int32_t k, float* E_host, double*
 ppca_status ppca_sync(ppca_handle* h) {
     if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return check_status_word(h->status);
+}
+
+}  // extern "C"
+
+// The device status word after the work that writes it has finished: an error
+// code is reported (and the word cleared for the next call).
+ppca_status check_status_word(int* status) {
     int st = 0;
-    CUDA_TRY(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&st, status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != kDevOk) {
-        CUDA_TRY(cudaMemset(h->status, 0, sizeof(int)));
+        CUDA_TRY(cudaMemset(status, 0, sizeof(int)));
         switch (st) {
         case kDevCholeskyBreakdown:
             return fail(PPCA_ERR_NUMERICAL, "CholeskyQR2: non-positive pivot (basis numerically rank-deficient)");
@@ -709,6 +720,8 @@ ppca_status ppca_sync(ppca_handle* h) {
     }
     return PPCA_OK;
 }
+
+extern "C" {
 
 ppca_status ppca_get_state(ppca_handle* h, void* buf, int64_t* bytes) {
     if (!h || !bytes) return fail(PPCA_ERR_INVALID, "NULL argument");
@@ -1033,6 +1046,24 @@ struct ppca_batch {
     std::vector<TcSchedule> inst_sched;   // per instance, after ppca_batch_autotune
     bool prime_bf16 = false;              // FP32 instances primed on a BF16 rounding of X
     std::vector<void*> prime_buf;         // per slot: that rounding, for its largest FP32 instance
+
+    // Lockstep priming: every instance's power iterations in grouped launches
+    // (grouped.h), one launch per kernel kind and iteration for the whole batch;
+    // the pPCA steps then run on the slots.
+    bool lockstep = true;                 // allowed (ppca_batch_set_lockstep)
+    bool grouped = false;                 // the captured graph primes in lockstep
+    void* g_mem = nullptr;                // per-instance buffers, tables, descriptors
+    GInst* g_inst = nullptr;              // device: one per instance
+    GMaps* g_maps = nullptr;              // device: one per instance
+    int* g_status = nullptr;              // device status word of the lockstep kernels
+    std::vector<GInst> g_host;
+    GTable t_quant{}, t_splitv{}, t_xv{}, t_xty{}, t_dm{}, t_gram{}, t_reduce{}, t_apply{};
+    const float* const* g_x32 = nullptr;  // device: FP32 X of each instance (quantize)
+    const int64_t* g_ld32 = nullptr;
+    bool any_f32 = false;
+    int g_max_m = 0;
+    int num_sms = 0;
+    cudaEvent_t g_done = nullptr;
 };
 
 namespace {
@@ -1051,6 +1082,9 @@ void free_batch(ppca_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto* h : b->slots) free_slot(h);
     for (auto p : b->prime_buf) cudaFree(p);
+    if (b->g_mem) cudaFree(b->g_mem);
+    if (b->g_status) cudaFree(b->g_status);
+    if (b->g_done) cudaEventDestroy(b->g_done);
     for (auto s : b->slot_streams) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
     if (b->fork) cudaEventDestroy(b->fork);
@@ -1091,6 +1125,229 @@ ppca_status bind_instance(ppca_batch* b, ppca_handle* h, int slot, const ppca_in
     return PPCA_OK;
 }
 
+// ---- lockstep priming
+
+inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Lockstep priming covers a batch whose instances all prime on BF16 data (BF16
+// X, or FP32 X with BF16 priming and d % 8 == 0), with one T for all, on the
+// tensor-core pass.
+bool lockstep_eligible(const ppca_batch* b) {
+    if (!b->lockstep) return false;
+    const int T = b->descs[0].T;
+    for (const auto& ds : b->descs) {
+        if (ds.T != T) return false;
+        const bool bf16 = ds.dtype == PPCA_BF16;
+        const bool f32 = ds.dtype == PPCA_F32 && b->prime_bf16 && ds.d % 8 == 0;
+        if (!bf16 && !f32) return false;
+        XView x = view_of(ds);
+        x.dtype = PPCA_BF16;
+        if (!tc_pass_supported(x, ds.m)) return false;
+    }
+    return true;
+}
+
+// Buffers, work tables and TMA descriptors of the lockstep priming (once, before
+// the capture).  Returns false, with nothing allocated, when the device memory
+// is not there (the batch then primes on its slots).
+bool prepare_lockstep(ppca_batch* b) {
+    const int count = (int)b->descs.size();
+    std::vector<GInst> gi(count);
+    std::vector<GShape> shp(count);
+    // sizes: one allocation, carved in order; offsets first
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
+    struct Off { size_t x, v, z, t, vp, yt, zacc, G, Gf, Rinv, part, flag; };
+    std::vector<Off> o(count);
+    int64_t n_quant = 0, n_splitv = 0, n_xv = 0, n_xty = 0, n_dm = 0, n_gram = 0, n_reduce = 0, n_apply = 0;
+    std::vector<int> c_quant(count), c_splitv(count), c_xv(count), c_xty(count), c_dm(count), c_gram(count),
+        c_reduce(count), c_apply(count);
+    b->any_f32 = false;
+    b->g_max_m = 0;
+    for (int i = 0; i < count; ++i) {
+        const ppca_instance_desc& ds = b->descs[i];
+        GInst& g = gi[i];
+        const int64_t n = ds.n, d = ds.d;
+        const int m = ds.m;
+        g.n = n;
+        g.d = d;
+        g.m = m;
+        g.m_pad = (int)rup(m, 32);
+        g.ldv = rup(d, 8);
+        g.ldy = rup(n, 128);
+        g.Dt = (int)cdiv(d, 128);
+        g.nk = (int)cdiv(d, 64);
+        g.ntiles = (int)(g.ldy / 128);
+        g.kst = (int)(g.ldy / 64);
+        g.Sg = (int)cdiv(g.kst, 128);        // Z = X^T Y row groups of at most 8192 rows
+        g.V0 = ds.V0;
+        const bool f32 = ds.dtype == PPCA_F32;
+        b->any_f32 |= f32;
+        b->g_max_m = std::max(b->g_max_m, m);
+        g.ld = f32 ? bf16_ld(d) : ds.ld;
+        shp[i] = grouped_shape(d, m);
+        g.gram_P = shp[i].gram_P;
+        g.gram_T = shp[i].gram_T;
+        g.gram_L = shp[i].gram_L;
+        o[i].x = f32 ? take((size_t)n * g.ld * 2) : 0;
+        o[i].v = take((size_t)d * m * 4);
+        o[i].z = take((size_t)d * m * 4);
+        o[i].t = take((size_t)d * m * 4);
+        o[i].vp = take((size_t)g.m_pad * g.ldv * 2);
+        o[i].yt = take((size_t)g.m_pad * g.ldy * 2);
+        o[i].zacc = take((size_t)g.Sg * g.m_pad * g.Dt * 128 * 8);
+        o[i].G = take((size_t)m * m * 8);
+        o[i].Gf = take((size_t)m * m * 4);
+        o[i].Rinv = take((size_t)m * m * 4);
+        o[i].part = take(gram_part_floats(d, m) * 4);
+        o[i].flag = take(4);
+        c_quant[i] = f32 ? (int)cdiv(n * (d / 8), 256) : 0;
+        c_splitv[i] = (int)cdiv((int64_t)g.m_pad * g.ldv, 256);
+        c_xv[i] = g.ntiles;
+        c_xty[i] = g.Dt * g.Sg;
+        c_dm[i] = (int)cdiv(d * m, 256);
+        c_gram[i] = shp[i].gram_blocks;
+        c_reduce[i] = shp[i].reduce_blocks;
+        c_apply[i] = shp[i].apply_blocks;
+        n_quant += c_quant[i];
+        n_splitv += c_splitv[i];
+        n_xv += c_xv[i];
+        n_xty += c_xty[i];
+        n_dm += c_dm[i];
+        n_gram += c_gram[i];
+        n_reduce += c_reduce[i];
+        n_apply += c_apply[i];
+    }
+    const int64_t most = std::max({n_quant, n_splitv, n_xv, n_xty, n_dm, n_gram, n_reduce, n_apply});
+    if (most >= (int64_t)1 << 31) return false;
+    const size_t tab_ints = (size_t)8 * (count + 1);
+    const size_t o_tabs = take(tab_ints * 4);
+    const size_t o_inst = take(sizeof(GInst) * count);
+    const size_t o_maps = take(sizeof(GMaps) * count);
+    const size_t o_x32 = take(sizeof(float*) * count);
+    const size_t o_ld32 = take(sizeof(int64_t) * count);
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, off) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int* st = nullptr;
+    if (cudaMalloc(reinterpret_cast<void**>(&st), 256) != cudaSuccess || cudaMemset(st, 0, 256) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(mem);
+        if (st) cudaFree(st);
+        return false;
+    }
+    char* base = static_cast<char*>(mem);
+    std::vector<GMaps> maps(count);
+    std::vector<const float*> x32(count);
+    std::vector<int64_t> ld32(count);
+    bool ok = true;
+    for (int i = 0; i < count && ok; ++i) {
+        const ppca_instance_desc& ds = b->descs[i];
+        GInst& g = gi[i];
+        g.X = ds.dtype == PPCA_F32 ? static_cast<const void*>(base + o[i].x) : ds.X;
+        g.V = reinterpret_cast<float*>(base + o[i].v);
+        g.Z = reinterpret_cast<float*>(base + o[i].z);
+        g.T = reinterpret_cast<float*>(base + o[i].t);
+        g.Vp = reinterpret_cast<__nv_bfloat16*>(base + o[i].vp);
+        g.Yt = reinterpret_cast<__nv_bfloat16*>(base + o[i].yt);
+        g.Zacc = reinterpret_cast<float*>(base + o[i].zacc);
+        g.G = reinterpret_cast<double*>(base + o[i].G);
+        g.Gf = reinterpret_cast<float*>(base + o[i].Gf);
+        g.Rinv = reinterpret_cast<float*>(base + o[i].Rinv);
+        g.gram_part = reinterpret_cast<float*>(base + o[i].part);
+        g.flag = reinterpret_cast<int*>(base + o[i].flag);
+        g.status = st;
+        x32[i] = ds.dtype == PPCA_F32 ? static_cast<const float*>(ds.X) : nullptr;
+        ld32[i] = ds.ld;
+        ok = grouped_encode_maps(g, maps[i]);
+    }
+    std::vector<int> tabs;
+    tabs.reserve(tab_ints);
+    int* dtabs = reinterpret_cast<int*>(base + o_tabs);
+    auto table = [&](const std::vector<int>& c) {
+        GTable t;
+        t.base = dtabs + tabs.size();
+        t.count = count;
+        int acc = 0;
+        for (int v : c) {
+            tabs.push_back(acc);
+            acc += v;
+        }
+        tabs.push_back(acc);
+        t.total = acc;
+        return t;
+    };
+    b->t_quant = table(c_quant);
+    b->t_splitv = table(c_splitv);
+    b->t_xv = table(c_xv);
+    b->t_xty = table(c_xty);
+    b->t_dm = table(c_dm);
+    b->t_gram = table(c_gram);
+    b->t_reduce = table(c_reduce);
+    b->t_apply = table(c_apply);
+    if (ok)
+        ok = cudaMemcpy(dtabs, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(base + o_inst, gi.data(), sizeof(GInst) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(base + o_maps, maps.data(), sizeof(GMaps) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(base + o_x32, x32.data(), sizeof(float*) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(base + o_ld32, ld32.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaEventCreateWithFlags(&b->g_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cudaFree(mem);
+        cudaFree(st);
+        return false;
+    }
+    b->g_mem = mem;
+    b->g_status = st;
+    b->g_inst = reinterpret_cast<GInst*>(base + o_inst);
+    b->g_maps = reinterpret_cast<GMaps*>(base + o_maps);
+    b->g_x32 = reinterpret_cast<const float* const*>(base + o_x32);
+    b->g_ld32 = reinterpret_cast<const int64_t*>(base + o_ld32);
+    b->g_host = std::move(gi);
+    // the slots' BF16 priming copies are not used by lockstep priming
+    for (auto p : b->prime_buf) cudaFree(p);
+    b->prime_buf.clear();
+    return true;
+}
+
+// CholeskyQR2 of every instance's src (V or Z) into V, through T (as run_orth).
+cudaError_t lockstep_orth(ppca_batch* b, int src) {
+    const int count = (int)b->descs.size();
+    cudaStream_t st = b->stream;
+    cudaError_t e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, src, b->g_max_m, false, st);
+    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, false, st);
+    if (e == cudaSuccess) e = grouped_chol_fallback(b->g_inst, count, b->g_max_m, st);
+    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, src, kGT, b->g_max_m, st);
+    if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, false, st);
+    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st);
+    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, kGV, b->g_max_m, st);
+    return e;
+}
+
+// Enqueue (inside the capture) Algorithm 1 step 1 for every instance in
+// lockstep on the batch stream: the BF16 rounding of FP32 X, V = orth(V0),
+// then T times Z = X^T X V (fast BF16 pass), V = orth(Z).
+ppca_status enqueue_lockstep(ppca_batch* b) {
+    cudaStream_t st = b->stream;
+    const int count = (int)b->descs.size();
+    if (b->any_f32) CUDA_TRY(grouped_quantize_bf16(b->g_x32, b->g_ld32, b->g_inst, b->t_quant, st));
+    CUDA_TRY(grouped_copy_v0(b->g_inst, b->t_dm, st));
+    for (int i = 0; i < count; ++i)
+        if (!b->descs[i].V0)
+            CUDA_TRY(init_gaussian(b->g_host[i].V, b->descs[i].d, b->descs[i].m, b->descs[i].seed, st));
+    CUDA_TRY(lockstep_orth(b, kGV));
+    for (int t = 0; t < b->descs[0].T; ++t) {
+        CUDA_TRY(grouped_split_v(b->g_inst, b->t_splitv, st));
+        CUDA_TRY(grouped_xpass(b->g_inst, b->g_maps, b->t_xv, b->t_xty, b->t_dm, b->g_status, b->num_sms, st));
+        CUDA_TRY(lockstep_orth(b, kGZ));
+    }
+    return PPCA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1119,6 +1376,7 @@ ppca_status ppca_batch_create(ppca_batch** out, const ppca_instance_desc* descs,
     int device = 0, num_sms = 0;
     cudaError_t e = cudaGetDevice(&device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device);
+    b->num_sms = num_sms;
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
@@ -1175,12 +1433,30 @@ ppca_status ppca_batch_run(ppca_batch* b) {
     if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
     if (!b->exec) {
         const int nslots = (int)b->slots.size();
+        b->grouped = lockstep_eligible(b) && prepare_lockstep(b);
         CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
         const int64_t launches0 = launches_so_far();
-        ppca_status st = PPCA_OK;
+        ppca_status st = b->grouped ? enqueue_lockstep(b) : PPCA_OK;
         cudaError_t e = cudaEventRecord(b->fork, b->stream);
         for (int s = 0; s < nslots && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->slot_streams[s], b->fork, 0);
-        for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK; ++i) {
+        for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK && b->grouped; ++i) {
+            // the pPCA step (steps 2-5) of a lockstep-primed instance on its slot
+            const ppca_instance_desc& ds = b->descs[i];
+            ppca_handle* h = b->slots[i % nslots];
+            h->x = view_of(ds);
+            h->has_ref = false;
+            h->method = PPCA_POWER;
+            h->m = ds.m;
+            h->iters = ds.T;
+            if (!b->inst_sched.empty()) h->sched = b->inst_sched[i];
+            const size_t bytes = (size_t)ds.d * ds.m * sizeof(float);
+            e = cudaMemcpyAsync(h->V, b->g_host[i].V, bytes, cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) break;
+            st = ppca_finalize(h, ds.k, ds.E, ds.lambda, PPCA_PREC_ACCURATE);
+            if (st == PPCA_OK && ds.V_out)
+                e = cudaMemcpyAsync(ds.V_out, b->g_host[i].V, bytes, cudaMemcpyDeviceToDevice, h->stream);
+        }
+        for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK && !b->grouped; ++i) {
             const ppca_instance_desc& ds = b->descs[i];
             ppca_handle* h = b->slots[i % nslots];
             st = bind_instance(b, h, (int)(i % nslots), ds);
@@ -1287,6 +1563,19 @@ ppca_status ppca_batch_set_priming(ppca_batch* b, int32_t dtype) {
     return PPCA_OK;
 }
 
+ppca_status ppca_batch_set_lockstep(ppca_batch* b, int32_t enable) {
+    if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
+    if (b->exec) return fail(PPCA_ERR_STATE, "the batch has already been captured");
+    b->lockstep = enable != 0;
+    return PPCA_OK;
+}
+
+ppca_status ppca_batch_lockstep(const ppca_batch* b, int32_t* active) {
+    if (!b || !active) return fail(PPCA_ERR_INVALID, "NULL argument");
+    *active = b->grouped ? 1 : 0;
+    return PPCA_OK;
+}
+
 ppca_status ppca_batch_kernel_count(const ppca_batch* b, int64_t* count) {
     if (!b || !count) return fail(PPCA_ERR_INVALID, "NULL argument");
     *count = b->kernels;
@@ -1296,6 +1585,7 @@ ppca_status ppca_batch_kernel_count(const ppca_batch* b, int64_t* count) {
 ppca_status ppca_batch_sync(ppca_batch* b) {
     if (!b) return fail(PPCA_ERR_INVALID, "batch is NULL");
     CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (b->g_status) PPCA_TRY(check_status_word(b->g_status));
     for (auto* h : b->slots) {
         ppca_status s = ppca_sync(h);
         if (s != PPCA_OK) return s;

@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "grouped.h"
 #include "pass_tc.h"
 #include "tc_host.h"
 #include "tc_ptx.cuh"
@@ -1686,6 +1687,264 @@ __global__ void zreduce_kernel(const float* __restrict__ Zacc, int Sg, int Dt, i
     }
 }
 
+// ---------------------------------------------------------------- grouped fast BF16 pass
+//
+// The two-kernel fast pass of many instances in one launch each (grouped.h):
+// work item w of Y = X V is tile w - base[i] of instance i, of Z = X^T Y task
+// w - base[i] (128-column slice s, row group g) of instance i.  Each item uses
+// its instance's TMA descriptors (device memory), basis width (the MMA's N)
+// and buffers; the shared-memory stages and TMEM are sized for the widest basis.
+
+__global__ void split_v_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)g.m_pad * g.ldv) return;
+    const int c = (int)(e / g.ldv);
+    const int64_t k = e % g.ldv;
+    const float v = (c < g.m && k < g.d) ? g.V[(int64_t)c * g.d + k] : 0.f;
+    g.Vp[e] = __float2bfloat16_rn(v);
+}
+
+__global__ void zreduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (e >= g.d * g.m) return;
+    const int c = (int)(e / g.d);
+    const int64_t j = e % g.d;
+    float hi = 0.f, lo = 0.f;
+    for (int q = 0; q < g.Sg; ++q) {
+        const float2 v = reinterpret_cast<const float2*>(g.Zacc)[((int64_t)q * g.m_pad + c) * (g.Dt * 128) + j];
+        df_add(hi, lo, v.x);
+        df_add(hi, lo, v.y);
+    }
+    g.Z[e] = hi + lo;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    xv_grouped_kernel(const GInst* __restrict__ gi, const GMaps* __restrict__ maps, GTable items, int stages,
+                      int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 128u * 128u, b_max = 128u * 128u;
+    const uint32_t stage_bytes = a_bytes + b_max;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = 256;
+    tc_prologue(hd, stages, tmem_cols, &maps[0].xa, &maps[0].v);
+    const uint32_t tmem = hd->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < items.total && ok; w += gridDim.x) {
+                const int i = group_find(items, w), t = w - items.base[i];
+                const GInst& g = gi[i];
+                const uint32_t bytes = a_bytes + (uint32_t)g.m_pad * 128u;
+                for (int k = 0; k < g.nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[s], bytes);
+                    uint8_t* st = tiles + (size_t)s * stage_bytes;
+                    tc::tma_load_2d(st, &maps[i].xa, &hd->full[s], k * kBK, t * 128);
+                    tc::tma_load_2d(st + a_bytes, &maps[i].v, &hd->full[s], k * kBK, 0);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, tl = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < items.total && ok; w += gridDim.x, ++tl) {
+                const GInst& g = gi[group_find(items, w)];
+                const uint32_t idesc = tc::idesc_bf16(128, g.m_pad, false, false);
+                const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t d_tmem = tmem + b * 128u;
+                for (int k = 0; k < g.nk; ++k, ++it) {
+                    const uint32_t s = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->full[s], ph, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t a_addr = tc::smem_u32(tiles + (size_t)s * stage_bytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 32, 16, 1024);
+                        const uint64_t bdesc = tc::smem_desc_sw128(a_addr + a_bytes + kk * 32, 16, 1024);
+                        tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k != 0 || kk != 0) ? 1u : 0u);
+                    }
+                    tc::mma_commit(&hd->empty[s]);
+                }
+                if (ok) tc::mma_commit(&hd->tfull[b]);
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t tl = 0;
+        for (int w = blockIdx.x; w < items.total; w += gridDim.x, ++tl) {
+            const int i = group_find(items, w), t = w - items.base[i];
+            const GInst& g = gi[i];
+            const uint32_t b = tl & 1u, tph = (tl >> 1) & 1u;
+            if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                hd->abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+            for (int c0 = 0; c0 < g.m_pad; c0 += 32) {
+                uint32_t r[32];
+                tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * 128u + (uint32_t)c0, r);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    g.Yt[(int64_t)(c0 + j) * g.ldy + row] = __float2bfloat16_rn(__uint_as_float(r[j]));
+            }
+            tc::fence_before_sync();
+            tc::mbar_arrive(&hd->tempty[b]);
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols, status);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    xty_grouped_kernel(const GInst* __restrict__ gi, const GMaps* __restrict__ maps, GTable items, int flush,
+                       int stages, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* tiles = align1024(smem_raw);
+    const uint32_t a_bytes = 2u * 64u * 128u, b_max = 128u * 128u;
+    const uint32_t stage_bytes = a_bytes + b_max;
+    SmemHeader* hd = reinterpret_cast<SmemHeader*>(tiles + (size_t)stages * stage_bytes);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t tmem_cols = 256;
+    tc_prologue(hd, stages, tmem_cols, &maps[0].xb, &maps[0].y);
+    const uint32_t tmem = hd->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < items.total && ok; w += gridDim.x) {
+                const int i = group_find(items, w), task = w - items.base[i];
+                const GInst& g = gi[i];
+                const int s = task % g.Dt, grp = task / g.Dt;
+                const int k0 = (int)((int64_t)grp * g.kst / g.Sg), k1 = (int)((int64_t)(grp + 1) * g.kst / g.Sg);
+                const uint32_t bytes = a_bytes + (uint32_t)g.m_pad * 128u;
+                for (int k = k0; k < k1; ++k, ++it) {
+                    const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                    if (!tc::mbar_wait(&hd->empty[st_i], ph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::mbar_expect_tx(&hd->full[st_i], bytes);
+                    uint8_t* st = tiles + (size_t)st_i * stage_bytes;
+                    tc::tma_load_2d(st, &maps[i].xb, &hd->full[st_i], s * 128, k * kBK);
+                    tc::tma_load_2d(st + 8192, &maps[i].xb, &hd->full[st_i], s * 128 + 64, k * kBK);
+                    tc::tma_load_2d(st + a_bytes, &maps[i].y, &hd->full[st_i], k * kBK, 0);
+                }
+            }
+            if (!ok) drain_copies(hd, it, stages, status);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            uint32_t it = 0, fb = 0;
+            bool ok = true;
+            for (int w = blockIdx.x; w < items.total && ok; w += gridDim.x) {
+                const int i = group_find(items, w), task = w - items.base[i];
+                const GInst& g = gi[i];
+                const uint32_t idesc = tc::idesc_bf16(128, g.m_pad, true, false);
+                const int grp = task / g.Dt;
+                const int k0 = (int)((int64_t)grp * g.kst / g.Sg), k1 = (int)((int64_t)(grp + 1) * g.kst / g.Sg);
+                for (int kb = k0; kb < k1 && ok; kb += flush, ++fb) {
+                    const int ke = kb + flush < k1 ? kb + flush : k1;
+                    const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                    if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *(volatile int*)&hd->abort) {
+                        hd->abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                    const uint32_t d_tmem = tmem + b * 128u;
+                    for (int k = kb; k < ke; ++k, ++it) {
+                        const uint32_t st_i = it % stages, ph = (it / stages) & 1u;
+                        if (!tc::mbar_wait(&hd->full[st_i], ph, status) || *(volatile int*)&hd->abort) {
+                            hd->abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint32_t a_addr = tc::smem_u32(tiles + (size_t)st_i * stage_bytes);
+#pragma unroll
+                        for (int kk = 0; kk < kBK / 16; ++kk) {
+                            const uint64_t adesc = tc::smem_desc_sw128(a_addr + kk * 2048, 8192, 1024);
+                            const uint64_t bdesc = tc::smem_desc_sw128(a_addr + a_bytes + kk * 32, 16, 1024);
+                            tc::mma_f16(d_tmem, adesc, bdesc, idesc, (k != kb) || kk != 0);
+                        }
+                        tc::mma_commit(&hd->empty[st_i]);
+                    }
+                    if (ok) tc::mma_commit(&hd->tfull[b]);
+                }
+            }
+        }
+    } else {
+        const int q = warp & 3;
+        uint32_t fb = 0;
+        bool ok = true;
+        for (int w = blockIdx.x; w < items.total && ok; w += gridDim.x) {
+            const int i = group_find(items, w), task = w - items.base[i];
+            const GInst& g = gi[i];
+            const int s = task % g.Dt, grp = task / g.Dt;
+            const int k0 = (int)((int64_t)grp * g.kst / g.Sg), k1 = (int)((int64_t)(grp + 1) * g.kst / g.Sg);
+            const int64_t j = (int64_t)s * 128 + q * 32 + lane;
+            const int64_t zs = (int64_t)g.Dt * 128;     // Z partials [g][column][row]
+            float2* z = reinterpret_cast<float2*>(g.Zacc) + (int64_t)grp * g.m_pad * zs + j;
+            for (int kb = k0; kb < k1; kb += flush, ++fb) {
+                const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
+                if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
+                    hd->abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                for (int c0 = 0; c0 < g.m_pad; c0 += 32) {
+                    uint32_t r[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * 128u + (uint32_t)c0, r);
+                    tc::tmem_ld_wait();
+                    float2* zz = z + (int64_t)c0 * zs;
+                    if (kb == k0) {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) zz[jj * zs] = make_float2(__uint_as_float(r[jj]), 0.f);
+                    } else {
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            float2 v = zz[jj * zs];
+                            df_add(v.x, v.y, __uint_as_float(r[jj]));
+                            zz[jj * zs] = v;
+                        }
+                    }
+                }
+                tc::fence_before_sync();
+                tc::mbar_arrive(&hd->tempty[b]);
+            }
+        }
+    }
+    tc_epilogue_teardown(hd, tmem_cols, status);
+}
+
 // ---------------------------------------------------------------- host side
 
 }  // namespace
@@ -2151,6 +2410,43 @@ cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t 
     const bool fuse = sched.fused != 0 && can_fuse;
     if (fuse) return run_fused(x, V, m, r0, r1, Z, s, sched, status, num_sms, st);
     return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
+}
+
+bool grouped_encode_maps(const GInst& g, GMaps& out) {
+    const void* X = g.X;
+    return encode_bf16_2d(&out.xa, X, g.d, g.n, g.ld * 2, 64, 128) &&
+           encode_bf16_2d(&out.v, g.Vp, g.d, (uint64_t)g.m_pad, g.ldv * 2, 64, g.m_pad) &&
+           encode_bf16_2d(&out.xb, X, g.d, g.n, g.ld * 2, 64, 64) &&
+           encode_bf16_2d(&out.y, g.Yt, g.ldy, (uint64_t)g.m_pad, g.ldy * 2, 64, g.m_pad);
+}
+
+cudaError_t grouped_split_v(const GInst* gi, GTable blocks, cudaStream_t st) {
+    note_launch();
+    split_v_grouped_kernel<<<blocks.total, 256, 0, st>>>(gi, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_xpass(const GInst* gi, const GMaps* maps, GTable xv_items, GTable xty_items, GTable zred_blocks,
+                          int* status, int num_sms, cudaStream_t st) {
+    const uint32_t xv_stage = 128u * 128u + 128u * 128u;
+    const int xv_stages = stages_for(xv_stage);
+    const size_t xv_smem = smem_bytes(xv_stages, xv_stage);
+    cudaError_t e = cudaFuncSetAttribute(xv_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xv_smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    xv_grouped_kernel<<<std::min(xv_items.total, num_sms), kThreads, xv_smem, st>>>(gi, maps, xv_items, xv_stages,
+                                                                                   status);
+    const uint32_t xty_stage = 2u * 64u * 128u + 128u * 128u;
+    const int xty_stages = stages_for(xty_stage);
+    const size_t xty_smem = smem_bytes(xty_stages, xty_stage);
+    e = cudaFuncSetAttribute(xty_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xty_smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    xty_grouped_kernel<<<std::min(xty_items.total, num_sms), kThreads, xty_smem, st>>>(gi, maps, xty_items, 256,
+                                                                                      xty_stages, status);
+    note_launch();
+    zreduce_grouped_kernel<<<zred_blocks.total, 256, 0, st>>>(gi, zred_blocks);
+    return cudaGetLastError();
 }
 
 cudaError_t pass_tc_set_wait_limit(uint64_t ns) { return tc::set_wait_limit(ns); }

@@ -15,6 +15,7 @@
 //   init_gaussian    Philox4x32-10 + Box-Muller starting basis
 //   quantize_*       BF16 / FP8 E4M3 data formats
 #include "kernels.h"
+#include "grouped.h"
 
 #include <cuda_fp8.h>
 #include <math.h>
@@ -52,12 +53,11 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     e = __fmaf_rn(a, b, -p);
 }
 
-__global__ void gram_df_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t d, int m,
-                               float* __restrict__ part, int64_t slice_rows, const int* run_if) {
-    if (run_if && *run_if == 0) return;       // only needed when the FP32 factorisation was rejected
+__device__ __forceinline__ void gram_df_body(const float* __restrict__ A, const float* __restrict__ B, int64_t d,
+                                             int m, float* __restrict__ part, int64_t slice_rows, int ti, int tj,
+                                             int p) {
     __shared__ float As[32][kGramTile + 1];
     __shared__ float Bs[32][kGramTile + 1];
-    const int ti = blockIdx.x, tj = blockIdx.y, p = blockIdx.z;
     if (A == B && ti > tj) return;          // symmetric: the reduction mirrors the upper tiles
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const int i0 = ti * kGramTile, j0 = tj * kGramTile;
@@ -115,13 +115,18 @@ __global__ void gram_df_kernel(const float* __restrict__ A, const float* __restr
         }
 }
 
+__global__ void gram_df_kernel(const float* __restrict__ A, const float* __restrict__ B, int64_t d, int m,
+                               float* __restrict__ part, int64_t slice_rows, const int* run_if) {
+    if (run_if && *run_if == 0) return;       // only needed when the FP32 factorisation was rejected
+    gram_df_body(A, B, d, m, part, slice_rows, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // L consecutive threads (L a power of two dividing 32) reduce one output: lane
 // l sums slices l, l + L, ... in order, then the lanes are combined by a fixed
 // shuffle tree, all in double-float.
-__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, int L, bool sym,
-                                   double* __restrict__ G, float* __restrict__ Gf, const int* run_if) {
-    if (run_if && *run_if == 0) return;
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void gram_reduce_body(const float* __restrict__ part, int P, int m, int L, bool sym,
+                                                 double* __restrict__ G, float* __restrict__ Gf, int block) {
+    const int64_t g = (int64_t)block * blockDim.x + threadIdx.x;
     const int idx = (int)(g / L), lane = (int)(g % L);
     const bool live = idx < m * m;               // whole groups are live or not: shuffles stay uniform
     dfloat q = {0.f, 0.f};
@@ -145,6 +150,12 @@ __global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m,
     }
 }
 
+__global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m, int L, bool sym,
+                                   double* __restrict__ G, float* __restrict__ Gf, const int* run_if) {
+    if (run_if && *run_if == 0) return;
+    gram_reduce_body(part, P, m, L, sym, G, Gf, blockIdx.x);
+}
+
 // ------------------------------------------------------------------ Cholesky
 
 // Right-looking Cholesky G = R^T R (R upper) in one CTA, then the triangular
@@ -160,10 +171,8 @@ __global__ void gram_reduce_kernel(const float* __restrict__ part, int P, int m,
 constexpr int kCholThreads = 512;
 
 template <bool DF>
-__global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ G, int m,
-                                                               float* __restrict__ Rinv, const int* run_if,
-                                                               int* status) {
-    if (run_if && *run_if == 0) return;      // the FP32 attempt was accepted
+__device__ __forceinline__ void cholesky_body(const double* __restrict__ G, int m, float* __restrict__ Rinv,
+                                              int* status) {
     extern __shared__ float csm[];
     float* ah = csm;                       // m x m, hi parts (the FP32 value when !DF)
     float* al = ah + m * m;                // m x m, lo parts (DF only)
@@ -252,6 +261,14 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
     }
     for (int e = threadIdx.x; e < m * m; e += kCholThreads) Rinv[e] = X[e];
     if (threadIdx.x == 0 && broke) set_status(status, kDevCholeskyBreakdown);
+}
+
+template <bool DF>
+__global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __restrict__ G, int m,
+                                                               float* __restrict__ Rinv, const int* run_if,
+                                                               int* status) {
+    if (run_if && *run_if == 0) return;      // the FP32 attempt was accepted
+    cholesky_body<DF>(G, m, Rinv, status);
 }
 
 // Blocked Cholesky in FP32 of the diagonally scaled Gram matrix G' = D G D
@@ -404,9 +421,8 @@ __device__ bool chol_series(float* A, float* W, const float* dsc, int m, int lda
     return true;
 }
 
-__global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float* __restrict__ Gf, int m,
-                                                                   float* __restrict__ Rinv, int* fallback,
-                                                                   int* status, int near_identity) {
+__device__ __forceinline__ void chol_blocked_body(const float* __restrict__ Gf, int m, float* __restrict__ Rinv,
+                                                  int* fallback, int* status, int near_identity) {
     extern __shared__ __align__(16) float cbs[];
     const int lda = (m + 3) & ~3;           // shared-memory row stride: rows start 16-byte aligned
     float* A = cbs;                         // m x lda; upper triangle, rows of R' overwrite it panel by panel
@@ -659,6 +675,12 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float
     }
 }
 
+__global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float* __restrict__ Gf, int m,
+                                                                   float* __restrict__ Rinv, int* fallback,
+                                                                   int* status, int near_identity) {
+    chol_blocked_body(Gf, m, Rinv, fallback, status, near_identity);
+}
+
 // Q = V X with X = R^-1 upper triangular (row-major).  A block stages X and
 // 32 rows of V in shared memory; thread (c, h) computes output column c for
 // the 16 rows of half h: Q[r, c] = sum_{l <= c} V[r, l] X[l, c], V's rows
@@ -669,12 +691,12 @@ constexpr int kApplyHalf = kApplyRows / 2;
 
 __host__ __device__ inline int apply_xs_floats(int m) { return (m * m + 3) & ~3; }
 
-__global__ void __launch_bounds__(256) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
-                                                         int64_t d, int m, float* __restrict__ Q) {
+__device__ __forceinline__ void apply_rinv_body(const float* __restrict__ V, const float* __restrict__ Rinv,
+                                                int64_t d, int m, float* __restrict__ Q, int block) {
     extern __shared__ __align__(16) float ars[];
     float* xs = ars;                          // m x m, X row-major
     float* vs = ars + apply_xs_floats(m);     // m x kApplyRows, vs[l][r] = V[r0 + r, l]
-    const int64_t r0 = (int64_t)blockIdx.x * kApplyRows;
+    const int64_t r0 = (int64_t)block * kApplyRows;
     const int mm = m * m, mm4 = mm / 4;
     if ((reinterpret_cast<uintptr_t>(Rinv) & 15) == 0) {
         const float4* x4 = reinterpret_cast<const float4*>(Rinv);
@@ -711,6 +733,11 @@ __global__ void __launch_bounds__(256) apply_rinv_kernel(const float* __restrict
 #pragma unroll
     for (int r = 0; r < kApplyHalf; ++r)
         if (rb + r < d) out[r] = acc[r];
+}
+
+__global__ void __launch_bounds__(256) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
+                                                         int64_t d, int m, float* __restrict__ Q) {
+    apply_rinv_body(V, Rinv, d, m, Q, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ Jacobi
@@ -1290,6 +1317,77 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// ------------------------------------------------------------------ grouped launches
+//
+// The same bodies over many instances at once (grouped.h): block b of the grid
+// belongs to instance group_find(tab, b) and is its block b - tab.base[i].
+
+__global__ void gram_df_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int src, int gated) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    if (gated && *g.flag == 0) return;                 // the FP32 factor was accepted
+    const int local = blockIdx.x - tab.base[i], T = g.gram_T;
+    const int ti = local % T, tj = (local / T) % T, p = local / (T * T);
+    const float* A = garray(g, src);
+    gram_df_body(A, A, g.d, g.m, g.gram_part, (g.d + g.gram_P - 1) / g.gram_P, ti, tj, p);
+}
+
+__global__ void gram_reduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int gated) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    if (gated && *g.flag == 0) return;
+    gram_reduce_body(g.gram_part, g.gram_P, g.m, g.gram_L, true, g.G, g.Gf, blockIdx.x - tab.base[i]);
+}
+
+__global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_grouped_kernel(const GInst* __restrict__ gi,
+                                                                           int near_identity) {
+    const GInst& g = gi[blockIdx.x];
+    chol_blocked_body(g.Gf, g.m, g.Rinv, near_identity ? nullptr : g.flag, g.status, near_identity);
+}
+
+__global__ void __launch_bounds__(kCholThreads) cholesky_grouped_kernel(const GInst* __restrict__ gi) {
+    const GInst& g = gi[blockIdx.x];
+    if (*g.flag == 0) return;                           // the FP32 factor was accepted
+    cholesky_body<true>(g.G, g.m, g.Rinv, g.status);
+}
+
+__global__ void __launch_bounds__(256) apply_rinv_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int src,
+                                                                 int dst) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    apply_rinv_body(garray(g, src), g.Rinv, g.d, g.m, garray(g, dst), blockIdx.x - tab.base[i]);
+}
+
+// BF16 rounding of every instance's FP32 X (d % 8 == 0, 16-byte aligned rows), eight values a thread.
+__global__ void quantize_bf16_grouped_kernel(const float* const* __restrict__ X32, const int64_t* __restrict__ ld32,
+                                             const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t per_row = g.d / 8;
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (e >= g.n * per_row) return;
+    const int64_t r = e / per_row, j = (e - r * per_row) * 8;
+    const float* x = X32[i] + r * ld32[i] + j;
+    const float4 a = __ldcs(reinterpret_cast<const float4*>(x));
+    const float4 b = __ldcs(reinterpret_cast<const float4*>(x + 4));
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(a.x, a.y), p1 = __floats2bfloat162_rn(a.z, a.w);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(b.x, b.y), p3 = __floats2bfloat162_rn(b.z, b.w);
+    uint4 o;
+    o.x = *reinterpret_cast<uint32_t*>(&p0);
+    o.y = *reinterpret_cast<uint32_t*>(&p1);
+    o.z = *reinterpret_cast<uint32_t*>(&p2);
+    o.w = *reinterpret_cast<uint32_t*>(&p3);
+    *reinterpret_cast<uint4*>(const_cast<__nv_bfloat16*>(static_cast<const __nv_bfloat16*>(g.X)) + r * g.ld + j) = o;
+}
+
+// Starting bases: V0 of every instance that has one, copied into its V.
+__global__ void copy_v0_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (g.V0 && e < g.d * g.m) g.V[e] = g.V0[e];
+}
+
 }  // namespace
 
 // ============================================================================ launchers
@@ -1674,6 +1772,73 @@ cudaError_t copy_f32(const float* src, float* dst, int64_t count, cudaStream_t s
     if (blocks > 4096) blocks = 4096;
     note_launch();
     copy_kernel<<<blocks, 256, 0, st>>>(src, dst, count);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ grouped launchers
+
+cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_blocks, int src, int max_m, bool gated,
+                         cudaStream_t st) {
+    (void)max_m;
+    note_launch();
+    gram_df_grouped_kernel<<<gram_blocks.total, 256, 0, st>>>(gi, gram_blocks, src, gated ? 1 : 0);
+    note_launch();
+    gram_reduce_grouped_kernel<<<reduce_blocks.total, 256, 0, st>>>(gi, reduce_blocks, gated ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st) {
+    const size_t lda = (size_t)((max_m + 3) & ~3);
+    const size_t smem = ((size_t)2 * max_m * lda + (size_t)((max_m + kCB - 1) / kCB) * kCB * kCB + max_m) *
+                        sizeof(float);
+    cudaError_t e = allow_smem(chol_blocked_grouped_kernel, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    chol_blocked_grouped_kernel<<<count, kCBThreads, smem, st>>>(gi, near_identity ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_chol_fallback(const GInst* gi, int count, int max_m, cudaStream_t st) {
+    const size_t smem = (size_t)3 * max_m * max_m * sizeof(float);
+    cudaError_t e = allow_smem(cholesky_grouped_kernel, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    cholesky_grouped_kernel<<<count, kCholThreads, smem, st>>>(gi);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st) {
+    if (max_m > 128) return cudaErrorInvalidValue;
+    const int threads = 2 * ((max_m + 31) / 32 * 32);
+    const size_t smem = ((size_t)apply_xs_floats(max_m) + (size_t)max_m * kApplyRows) * sizeof(float);
+    cudaError_t e = allow_smem(apply_rinv_grouped_kernel, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    apply_rinv_grouped_kernel<<<blocks.total, threads, smem, st>>>(gi, blocks, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_copy_v0(const GInst* gi, GTable dm_blocks, cudaStream_t st) {
+    note_launch();
+    copy_v0_grouped_kernel<<<dm_blocks.total, 256, 0, st>>>(gi, dm_blocks);
+    return cudaGetLastError();
+}
+
+GShape grouped_shape(int64_t d, int m) {
+    GShape s;
+    s.gram_P = gram_nslices(d, m);
+    s.gram_T = (m + kGramTile - 1) / kGramTile;
+    s.gram_L = gram_reduce_lanes(s.gram_P);
+    s.gram_blocks = s.gram_T * s.gram_T * s.gram_P;
+    s.reduce_blocks = ceil_div_i((int64_t)m * m * s.gram_L, 256);
+    s.apply_blocks = ceil_div_i(d, kApplyRows);
+    return s;
+}
+
+cudaError_t grouped_quantize_bf16(const float* const* X32, const int64_t* ld32, const GInst* gi, GTable blocks,
+                                  cudaStream_t st) {
+    note_launch();
+    quantize_bf16_grouped_kernel<<<blocks.total, 256, 0, st>>>(X32, ld32, gi, blocks);
     return cudaGetLastError();
 }
 

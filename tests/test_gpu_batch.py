@@ -23,15 +23,16 @@ from gpu_util import host_basis
 pytestmark = pytest.mark.gpu
 
 
-def make_batch(count, seed, T, nmax=20000):
+def make_batch(count, seed, T, nmax=20000, dtypes=None):
     import torch
     shapes = synth.batch_instances(count, seed)
     inst = []
-    for s in shapes:
+    for i, s in enumerate(shapes):
         n = min(s["n"], nmax)
         d, k, m = s["d"], s["k"], s["m"]
         lam = s["rho"] ** np.arange(1, d + 1)
-        X = synth.instance_data_torch(n, d, lam, s["seed"], "cuda", torch.float32)
+        dt = dtypes[i % len(dtypes)] if dtypes else torch.float32
+        X = synth.instance_data_torch(n, d, lam, s["seed"], "cuda", dt)
         V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, s["seed"]).T,
                                                    dtype=np.float32)).cuda()
         inst.append({"X": X, "k": k, "m": m, "T": T, "V0": V0,
@@ -141,6 +142,7 @@ def test_batch_bf16_priming_matches_oracle(cuda_device):
     P.ppca_batch_set_priming(b, P.PPCA_BF16)
     P.ppca_batch_run(b)
     P.ppca_batch_sync(b)
+    assert P.ppca_batch_lockstep(b)                   # all FP32, d % 8 == 0, one T: primed in lockstep
     worst = 0.0
     for i, ins in enumerate(inst):
         Xs = ins["X"].double().cpu().numpy()
@@ -155,3 +157,45 @@ def test_batch_bf16_priming_matches_oracle(cuda_device):
     with pytest.raises(P.PPCAError) as ei:
         P.ppca_batch_set_priming(b, P.PPCA_F32)       # already captured
     assert ei.value.status_name == "PPCA_ERR_STATE"
+
+
+def test_lockstep_priming_against_slots_and_oracle(cuda_device):
+    """Lockstep priming (every instance's power iterations in grouped launches)
+    on a mixed batch: FP32 instances primed on their BF16 rounding, BF16
+    instances primed as stored, ragged n (not multiples of 128) and m (not
+    multiples of 32), one instance drawing its V0 from its seed.  Against the
+    same batch primed on its slots (the per-instance path): the same pPCA-step
+    parity with the oracle on each primed basis, primed subspaces within
+    3e-2 rad of the oracle's FP64 block power on the stored (BF16 or
+    BF16-rounded) values, and far fewer kernel launches."""
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    T = 6
+    runs = {}
+    for lockstep in (True, False):
+        inst = make_batch(9, seed=611, T=T, nmax=9000, dtypes=[torch.float32, torch.bfloat16, torch.float32])
+        inst[4]["V0"] = None
+        inst[4]["seed"] = 99
+        b = P.ppca_batch_create(inst, slots=3)
+        P.ppca_batch_set_priming(b, P.PPCA_BF16)
+        P.ppca_batch_set_lockstep(b, lockstep)
+        P.ppca_batch_run(b)
+        P.ppca_batch_sync(b)
+        assert P.ppca_batch_lockstep(b) == lockstep
+        runs[lockstep] = (inst, P.ppca_batch_kernel_count(b))
+    (inst_l, k_l), (inst_s, k_s) = runs[True], runs[False]
+    print("kernels per run: lockstep", k_l, "slots", k_s)
+    assert k_l < k_s
+    for i, (a, c) in enumerate(zip(inst_l, inst_s)):
+        Xs = a["X"].double().cpu().numpy()            # stored values (BF16 instances exactly)
+        Xp = oracle.bf16_round_rne(Xs)                # the priming data of both paths
+        Va, Vc = host_basis(a["V_out"]), host_basis(c["V_out"])
+        Eo, lo = oracle.ppca_finalize(Xs, Va, a["k"])
+        np.testing.assert_allclose(a["lam"].cpu().numpy(), lo, rtol=1e-5, err_msg=f"instance {i}")
+        assert oracle.angles(host_basis(a["E"]), Eo).max() <= 1e-4, i
+        if a["V0"] is not None:
+            Vo = oracle.power_prime(Xp, host_basis(a["V0"]), T)
+            assert oracle.principal_angles(Va, Vo).max() <= 3e-2, i
+        # the slot path from the same start (the seeded instance: the same Philox draw)
+        assert oracle.principal_angles(Va, Vc).max() <= 3e-2, i
