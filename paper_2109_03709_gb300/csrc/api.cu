@@ -1058,6 +1058,8 @@ struct ppca_batch {
     int* g_status = nullptr;              // device status word of the lockstep kernels
     std::vector<GInst> g_host;
     GTable t_quant{}, t_splitv{}, t_xv{}, t_xty{}, t_dm{}, t_gram{}, t_reduce{}, t_apply{};
+    GTable t_ygen32{}, t_ygen16{}, t_ychunks{}, t_gred{}, t_rayleigh{}, t_rotate{}, t_sign{};
+    bool any_vout = false;
     const float* const* g_x32 = nullptr;  // device: FP32 X of each instance (quantize)
     const int64_t* g_ld32 = nullptr;
     bool any_f32 = false;
@@ -1158,12 +1160,19 @@ bool prepare_lockstep(ppca_batch* b) {
     // sizes: one allocation, carved in order; offsets first
     size_t off = 0;
     auto take = [&](size_t bytes) { const size_t o = off; off += al256(bytes); return o; };
-    struct Off { size_t x, v, z, t, vp, yt, zacc, G, Gf, Rinv, part, flag; };
+    struct Off {
+        size_t x, v, z, t, vp, yt, zacc, G, Gf, Rinv, part, flag;
+        size_t q3, y3, gpart, gp, evals, uf, u64, lam, sweeps, w, U;
+    };
     std::vector<Off> o(count);
     int64_t n_quant = 0, n_splitv = 0, n_xv = 0, n_xty = 0, n_dm = 0, n_gram = 0, n_reduce = 0, n_apply = 0;
     std::vector<int> c_quant(count), c_splitv(count), c_xv(count), c_xty(count), c_dm(count), c_gram(count),
         c_reduce(count), c_apply(count);
+    std::vector<int> c_ygen32(count), c_ygen16(count), c_ychunks(count), c_gred(count), c_rayleigh(count),
+        c_rotate(count), c_sign(count);
+    int64_t n_pp = 0;
     b->any_f32 = false;
+    b->any_vout = false;
     b->g_max_m = 0;
     for (int i = 0; i < count; ++i) {
         const ppca_instance_desc& ds = b->descs[i];
@@ -1190,7 +1199,38 @@ bool prepare_lockstep(ppca_batch* b) {
         g.gram_P = shp[i].gram_P;
         g.gram_T = shp[i].gram_T;
         g.gram_L = shp[i].gram_L;
-        o[i].x = f32 ? take((size_t)n * g.ld * 2) : 0;
+        g.k = ds.k;
+        g.xf32 = f32 ? 1 : 0;
+        g.XP = ds.X;
+        g.ldp = ds.ld;
+        g.nparts = (int)cdiv(g.kst, kGramChunk);
+        g.E = ds.E;
+        g.lambda = ds.lambda;
+        g.V_out = ds.V_out;
+        b->any_vout |= ds.V_out != nullptr;
+        // the BF16 copy of FP32 X serves the priming only: the pPCA step's Y pieces reuse it
+        const size_t y3_bytes = (size_t)3 * g.m_pad * g.ldy * 2;
+        const size_t xcopy = f32 ? (size_t)n * g.ld * 2 : 0;
+        o[i].x = f32 ? take(std::max(xcopy, y3_bytes)) : 0;
+        o[i].y3 = f32 ? o[i].x : take(y3_bytes);
+        o[i].q3 = take((size_t)3 * g.m_pad * g.ldv * 2);
+        o[i].gpart = take((size_t)g.nparts * g.m_pad * g.m_pad * 8);
+        o[i].gp = take((size_t)m * m * 8);
+        o[i].evals = take((size_t)m * 4);
+        o[i].uf = take((size_t)m * m * 4);
+        o[i].u64 = take((size_t)m * m * 8);
+        o[i].lam = take((size_t)m * 8);
+        o[i].sweeps = take(4);
+        o[i].w = take((size_t)m * 8);
+        o[i].U = take((size_t)m * m * 8);
+        c_ygen32[i] = f32 ? g.ntiles : 0;
+        c_ygen16[i] = f32 ? 0 : g.ntiles;
+        c_ychunks[i] = g.nparts;
+        c_gred[i] = (int)cdiv((int64_t)m * m, 256);
+        c_rayleigh[i] = m;
+        c_rotate[i] = (int)cdiv(d, 256) * ds.k;
+        c_sign[i] = ds.k;
+        for (int v : {c_ygen32[i], c_ygen16[i], c_ychunks[i], c_rotate[i]}) n_pp = std::max<int64_t>(n_pp, v);
         o[i].v = take((size_t)d * m * 4);
         o[i].z = take((size_t)d * m * 4);
         o[i].t = take((size_t)d * m * 4);
@@ -1220,8 +1260,8 @@ bool prepare_lockstep(ppca_batch* b) {
         n_apply += c_apply[i];
     }
     const int64_t most = std::max({n_quant, n_splitv, n_xv, n_xty, n_dm, n_gram, n_reduce, n_apply});
-    if (most >= (int64_t)1 << 31) return false;
-    const size_t tab_ints = (size_t)8 * (count + 1);
+    if (most >= (int64_t)1 << 31 || n_pp * count >= (int64_t)1 << 31) return false;
+    const size_t tab_ints = (size_t)15 * (count + 1);
     const size_t o_tabs = take(tab_ints * 4);
     const size_t o_inst = take(sizeof(GInst) * count);
     const size_t o_maps = take(sizeof(GMaps) * count);
@@ -1260,9 +1300,20 @@ bool prepare_lockstep(ppca_batch* b) {
         g.gram_part = reinterpret_cast<float*>(base + o[i].part);
         g.flag = reinterpret_cast<int*>(base + o[i].flag);
         g.status = st;
+        g.Q3 = reinterpret_cast<__nv_bfloat16*>(base + o[i].q3);
+        g.Y3 = reinterpret_cast<__nv_bfloat16*>(base + o[i].y3);
+        g.Gpart = reinterpret_cast<float2*>(base + o[i].gpart);
+        g.Gp = reinterpret_cast<double*>(base + o[i].gp);
+        g.evals = reinterpret_cast<float*>(base + o[i].evals);
+        g.Uf = reinterpret_cast<float*>(base + o[i].uf);
+        g.U64 = reinterpret_cast<double*>(base + o[i].u64);
+        g.lam = reinterpret_cast<double*>(base + o[i].lam);
+        g.sweeps = reinterpret_cast<int*>(base + o[i].sweeps);
+        g.w = reinterpret_cast<double*>(base + o[i].w);
+        g.U = reinterpret_cast<double*>(base + o[i].U);
         x32[i] = ds.dtype == PPCA_F32 ? static_cast<const float*>(ds.X) : nullptr;
         ld32[i] = ds.ld;
-        ok = grouped_encode_maps(g, maps[i]);
+        ok = grouped_encode_maps(g, maps[i]) && grouped_encode_gram_maps(g, maps[i]);
     }
     std::vector<int> tabs;
     tabs.reserve(tab_ints);
@@ -1288,6 +1339,13 @@ bool prepare_lockstep(ppca_batch* b) {
     b->t_gram = table(c_gram);
     b->t_reduce = table(c_reduce);
     b->t_apply = table(c_apply);
+    b->t_ygen32 = table(c_ygen32);
+    b->t_ygen16 = table(c_ygen16);
+    b->t_ychunks = table(c_ychunks);
+    b->t_gred = table(c_gred);
+    b->t_rayleigh = table(c_rayleigh);
+    b->t_rotate = table(c_rotate);
+    b->t_sign = table(c_sign);
     if (ok)
         ok = cudaMemcpy(dtabs, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(base + o_inst, gi.data(), sizeof(GInst) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1308,14 +1366,19 @@ bool prepare_lockstep(ppca_batch* b) {
     b->g_x32 = reinterpret_cast<const float* const*>(base + o_x32);
     b->g_ld32 = reinterpret_cast<const int64_t*>(base + o_ld32);
     b->g_host = std::move(gi);
-    // the slots' BF16 priming copies are not used by lockstep priming
+    // the whole run is grouped: the slots' workspaces and BF16 priming copies go unused
     for (auto p : b->prime_buf) cudaFree(p);
     b->prime_buf.clear();
+    for (auto* h : b->slots) {
+        if (h->ws) cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_m = 0;
+    }
     return true;
 }
 
-// CholeskyQR2 of every instance's src (V or Z) into V, through T (as run_orth).
-cudaError_t lockstep_orth(ppca_batch* b, int src) {
+// CholeskyQR2 of every instance's src (V or Z) into dst (V or Z), through T (as run_orth).
+cudaError_t lockstep_orth(ppca_batch* b, int src, int dst) {
     const int count = (int)b->descs.size();
     cudaStream_t st = b->stream;
     cudaError_t e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, src, b->g_max_m, false, st);
@@ -1324,13 +1387,13 @@ cudaError_t lockstep_orth(ppca_batch* b, int src) {
     if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, src, kGT, b->g_max_m, st);
     if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, false, st);
     if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st);
-    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, kGV, b->g_max_m, st);
+    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, dst, b->g_max_m, st);
     return e;
 }
 
-// Enqueue (inside the capture) Algorithm 1 step 1 for every instance in
-// lockstep on the batch stream: the BF16 rounding of FP32 X, V = orth(V0),
-// then T times Z = X^T X V (fast BF16 pass), V = orth(Z).
+// Enqueue (inside the capture) Algorithm 1 for every instance in lockstep on
+// the batch stream: step 1 -- the BF16 rounding of FP32 X, V = orth(V0), then
+// T times Z = X^T X V (fast BF16 pass), V = orth(Z) -- and steps 2-5.
 ppca_status enqueue_lockstep(ppca_batch* b) {
     cudaStream_t st = b->stream;
     const int count = (int)b->descs.size();
@@ -1339,12 +1402,21 @@ ppca_status enqueue_lockstep(ppca_batch* b) {
     for (int i = 0; i < count; ++i)
         if (!b->descs[i].V0)
             CUDA_TRY(init_gaussian(b->g_host[i].V, b->descs[i].d, b->descs[i].m, b->descs[i].seed, st));
-    CUDA_TRY(lockstep_orth(b, kGV));
+    CUDA_TRY(lockstep_orth(b, kGV, kGV));
     for (int t = 0; t < b->descs[0].T; ++t) {
         CUDA_TRY(grouped_split_v(b->g_inst, b->t_splitv, st));
         CUDA_TRY(grouped_xpass(b->g_inst, b->g_maps, b->t_xv, b->t_xty, b->t_dm, b->g_status, b->num_sms, st));
-        CUDA_TRY(lockstep_orth(b, kGZ));
+        CUDA_TRY(lockstep_orth(b, kGZ, kGV));
     }
+    // steps 2-5 for every instance: Q = orth(V) (into Z), G = (X Q)^T (X Q) at
+    // split precision on the data as given, the eigensolve, E = Q U[:, :k]
+    if (b->any_vout) CUDA_TRY(grouped_copy_vout(b->g_inst, b->t_dm, st));
+    CUDA_TRY(lockstep_orth(b, kGV, kGZ));
+    CUDA_TRY(grouped_split_q(b->g_inst, b->t_splitv, st));
+    CUDA_TRY(grouped_projected_gram(b->g_inst, b->g_maps, b->t_ygen32, b->t_ygen16, b->t_ychunks, b->t_gred,
+                                    b->g_max_m, b->g_status, b->num_sms, st));
+    CUDA_TRY(grouped_eigh(b->g_inst, count, b->t_rayleigh, b->g_max_m, st));
+    CUDA_TRY(grouped_rotate(b->g_inst, b->t_rotate, b->t_sign, st));
     return PPCA_OK;
 }
 
@@ -1439,23 +1511,6 @@ ppca_status ppca_batch_run(ppca_batch* b) {
         ppca_status st = b->grouped ? enqueue_lockstep(b) : PPCA_OK;
         cudaError_t e = cudaEventRecord(b->fork, b->stream);
         for (int s = 0; s < nslots && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->slot_streams[s], b->fork, 0);
-        for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK && b->grouped; ++i) {
-            // the pPCA step (steps 2-5) of a lockstep-primed instance on its slot
-            const ppca_instance_desc& ds = b->descs[i];
-            ppca_handle* h = b->slots[i % nslots];
-            h->x = view_of(ds);
-            h->has_ref = false;
-            h->method = PPCA_POWER;
-            h->m = ds.m;
-            h->iters = ds.T;
-            if (!b->inst_sched.empty()) h->sched = b->inst_sched[i];
-            const size_t bytes = (size_t)ds.d * ds.m * sizeof(float);
-            e = cudaMemcpyAsync(h->V, b->g_host[i].V, bytes, cudaMemcpyDeviceToDevice, h->stream);
-            if (e != cudaSuccess) break;
-            st = ppca_finalize(h, ds.k, ds.E, ds.lambda, PPCA_PREC_ACCURATE);
-            if (st == PPCA_OK && ds.V_out)
-                e = cudaMemcpyAsync(ds.V_out, b->g_host[i].V, bytes, cudaMemcpyDeviceToDevice, h->stream);
-        }
         for (size_t i = 0; i < b->descs.size() && e == cudaSuccess && st == PPCA_OK && !b->grouped; ++i) {
             const ppca_instance_desc& ds = b->descs[i];
             ppca_handle* h = b->slots[i % nslots];

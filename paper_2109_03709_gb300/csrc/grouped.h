@@ -37,7 +37,31 @@ struct GInst {
     int gram_P, gram_T, gram_L;
     int* flag;                // CholeskyQR: the FP32 factor was rejected
     int* status;              // device status word of the batch
+
+    // the pPCA step (Algorithm 1, steps 2-5), Q = orth(V) held in Z
+    int k;                    // components returned
+    int xf32;                 // the step's data (XP) is FP32 (else BF16)
+    const void* XP;           // the step's data: X as given, leading dimension ldp
+    int64_t ldp;
+    __nv_bfloat16* Q3;        // [3][m_pad][ldv]: Q as three BF16 pieces
+    __nv_bfloat16* Y3;        // [3][m_pad][ldy]: Y = X Q as three BF16 pieces (transposed)
+    float2* Gpart;            // [nparts][m_pad][m_pad]: double-float partials of Y^T Y
+    int nparts;               // row chunks of Y^T Y (kGramChunk K-stages each)
+    double* Gp;               // m x m: the projected Gram matrix
+    float* evals;             // m: Jacobi eigenvalues (FP32)
+    float* Uf;                // m x m: Jacobi eigenvectors (FP32)
+    double* U64;              // m x m: FP64-polished eigenvectors
+    double* lam;              // m: Rayleigh quotients
+    int* sweeps;
+    double* w;                // m: eigenvalues, descending
+    double* U;                // m x m: eigenvectors, columns in the order of w
+    float* E;                 // d x k output
+    double* lambda;           // k output: w / n
+    float* V_out;             // d x m output (NULL: none)
 };
+
+// K-stages (64 rows) of Y per partial of the grouped Y^T Y.
+constexpr int kGramChunk = 64;
 
 // TMA descriptors of one instance's X-pass (64-byte aligned in device memory).
 struct alignas(64) GMaps {
@@ -45,6 +69,9 @@ struct alignas(64) GMaps {
     CUtensorMap v;            // V pieces, box 64 x m_pad
     CUtensorMap xb;           // X, box 64 x 64 (Z = X^T Y)
     CUtensorMap y;            // Y^T, box 64 x m_pad
+    CUtensorMap xp;           // the pPCA step's X: FP32 box 32 x 128, BF16 box 64 x 128
+    CUtensorMap q3;           // Q pieces, box 64 x m_pad
+    CUtensorMap y3;           // Y pieces, box 64 x m_pad
 };
 
 // A grouped launch's block (or work item) table.
@@ -89,8 +116,22 @@ struct GShape {
 };
 GShape grouped_shape(int64_t d, int m);
 
+// ---- launchers (small.cu): the pPCA step's small kernels of every instance
+cudaError_t grouped_eigh(const GInst* gi, int count, GTable rayleigh_blocks, int max_m, cudaStream_t st);
+cudaError_t grouped_rotate(const GInst* gi, GTable rotate_blocks, GTable sign_blocks, cudaStream_t st);
+cudaError_t grouped_copy_vout(const GInst* gi, GTable dm_blocks, cudaStream_t st);
+
+// ---- launchers (pass_gram.cu): G = (X Q)^T (X Q) of every instance (split
+// precision), over the instances with FP32 data (ygen32 items) and with BF16
+// data (ygen16 items); gram items are (instance, chunk of kGramChunk K-stages)
+cudaError_t grouped_projected_gram(const GInst* gi, const GMaps* maps, GTable ygen32, GTable ygen16, GTable gram_items,
+                                   GTable reduce_blocks, int max_m, int* status, int num_sms, cudaStream_t st);
+bool grouped_encode_gram_maps(const GInst& g, GMaps& out);
+
 // ---- launchers (pass_tc.cu): the fast BF16 X-pass of every instance
 cudaError_t grouped_split_v(const GInst* gi, GTable blocks, cudaStream_t st);
+// Q (held in Z) as three BF16 pieces Q3 (the pPCA step's split precision).
+cudaError_t grouped_split_q(const GInst* gi, GTable blocks, cudaStream_t st);
 cudaError_t grouped_xpass(const GInst* gi, const GMaps* maps, GTable xv_items, GTable xty_items,
                           GTable zred_blocks, int* status, int num_sms, cudaStream_t st);
 bool grouped_encode_maps(const GInst& g, GMaps& out);

@@ -29,6 +29,7 @@
 // and returns.
 #include <cudaTypedefs.h>
 
+#include "grouped.h"
 #include "pass_tc.h"
 #include "tc_host.h"
 #include "tc_ptx.cuh"
@@ -42,7 +43,7 @@ constexpr int kGThreadsF32 = 320;
 constexpr int kGMaxStages = 6;
 constexpr int kGBK = 64;                    // K extent of one stage (64 BF16 = 128 B)
 constexpr uint32_t kPiece = 128u * 128u;    // one 128-row x 128-byte operand tile
-constexpr int kGSmemBudget = 200 * 1024;
+constexpr int kGSmemBudget = 227 * 1024;       // the opt-in maximum per block
 
 struct GHeader {
     uint64_t full[kGMaxStages], xform[kGMaxStages], empty[kGMaxStages];
@@ -119,8 +120,9 @@ __device__ __forceinline__ void split3_df(float hi, float lo, __nv_bfloat16* dst
 // One flush group's epilogue step for a 32-column chunk of this thread's TMEM
 // lane: fold the accumulator chunk `a` into the running sum (R, L) at column
 // offset `run`; returns the updated sum in (rh, rl).  g = group index.
-__device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col, uint32_t run_col, int m_pad, int g,
-                                           bool keep, uint32_t (&a)[32], uint32_t (&rh)[32], uint32_t (&rl)[32]) {
+__device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col, uint32_t run_col, uint32_t lo_off,
+                                           int g, bool keep, uint32_t (&a)[32], uint32_t (&rh)[32],
+                                           uint32_t (&rl)[32]) {
     tc::tmem_ld32(lane_base + acc_col, a);
     if (g == 0) {
         tc::tmem_ld_wait();
@@ -131,7 +133,7 @@ __device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col,
         }
     } else {
         tc::tmem_ld32(lane_base + run_col, rh);
-        tc::tmem_ld32(lane_base + run_col + (uint32_t)m_pad, rl);
+        tc::tmem_ld32(lane_base + run_col + lo_off, rl);
         tc::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -143,70 +145,113 @@ __device__ __forceinline__ void fold_chunk(uint32_t lane_base, uint32_t acc_col,
     }
     if (keep) {
         tc::tmem_st32(lane_base + run_col, rh);
-        tc::tmem_st32(lane_base + run_col + (uint32_t)m_pad, rl);
+        tc::tmem_st32(lane_base + run_col + lo_off, rl);
         tc::tmem_st_wait();
     }
 }
 
 // ---------------------------------------------------------------- Y = X Q
 
-// Stage: [X area][Q piece 0 .. NV-1].  X area: BF16 X -> one 16 KB tile; FP32 X
-// -> two raw 32-column boxes (32 KB), overwritten in place by the NX pieces.
-template <int NX, int NV, bool F32X>
+// One 128-row tile of Y = X Q: the descriptors of X and of the Q pieces, the
+// first X row, the K-stages, the basis width (the MMA's N) and where its rows
+// of the Y pieces go (piece p at Yt + p m_pad ldy, transposed).
+struct YItem {
+    const CUtensorMap* mx;
+    const CUtensorMap* mq;
+    int xr;
+    int nk;
+    int m_pad;
+    __nv_bfloat16* Yt;
+    int64_t ldy;
+    int64_t row;
+};
+
+// One problem: tile t of rows [r0, r1), or the t-th listed 128-row block.
+struct YgenOne {
+    CUtensorMap tmX, tmQ;
+    int ntiles, nk, m_pad;
+    __nv_bfloat16* Yt;
+    int64_t ldy;
+    const int* tile_row;
+    __device__ int count() const { return ntiles; }
+    __device__ YItem item(int t) const {
+        return YItem{&tmX, &tmQ, tile_row ? tile_row[t] : t * 128, nk, m_pad, Yt, ldy, (int64_t)t * 128};
+    }
+};
+
+// Many problems (grouped.h): item w is tile w - base[i] of instance i.
+struct YgenGroup {
+    const GInst* gi;
+    const GMaps* maps;
+    GTable items;
+    __device__ int count() const { return items.total; }
+    __device__ YItem item(int w) const {
+        const int i = group_find(items, w), t = w - items.base[i];
+        const GInst& g = gi[i];
+        return YItem{&maps[i].xp, &maps[i].q3, t * 128, g.nk, g.m_pad, g.Y3, g.ldy, (int64_t)t * 128};
+    }
+};
+
+// Stage: [X area][Q piece 0 .. NV-1], pieces q_piece bytes apart.  X area: BF16
+// X -> one 16 KB tile; FP32 X -> two raw 32-column boxes (32 KB), overwritten in
+// place by the NX pieces.  TMEM: accumulator b at column b * acc_stride, the
+// double-float running sum at [2, 4) * acc_stride.
+template <int NX, int NV, bool F32X, class Work>
 __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
-    ygen_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int ntiles, int nk,
-                int flush, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy,
-                const int* __restrict__ tile_row, int* status) {
+    ygen_kernel(const __grid_constant__ Work work, int flush, int stages, uint32_t q_piece, uint32_t acc_stride,
+                uint32_t tmem_cols, int* status) {
     constexpr int ORD = (NX > NV ? NX : NV) - 1;
     constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
-    const uint32_t q_piece = (uint32_t)m_pad * 128u;
     const uint32_t stage_bytes = x_bytes + NV * q_piece;
     GHeader* hd = reinterpret_cast<GHeader*>(tiles + (size_t)stages * stage_bytes);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int ngroups = (nk + flush - 1) / flush;
-    const uint32_t tmem_cols = pow2_cols((ngroups > 1 ? 4u : 2u) * (uint32_t)m_pad);
-    g_prologue(hd, stages, tmem_cols, &tmX, &tmQ);
+    {
+        const YItem first = work.item(0);
+        g_prologue(hd, stages, tmem_cols, first.mx, first.mq);
+    }
     const uint32_t tmem = hd->tmem_base;
     volatile int* abort_flag = &hd->abort;
+    const int count = work.count();
 
     if (warp == 0) {
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                // Y tile t comes from X rows [xr, xr + 128): consecutive tiles, or
-                // the listed 128-row blocks of a row sample
-                const int xr = tile_row ? tile_row[t] : t * 128;
-                for (int k = 0; k < nk; ++k, ++it) {
+            for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
+                const YItem y = work.item(w);
+                const uint32_t q_bytes = (uint32_t)y.m_pad * 128u;
+                for (int k = 0; k < y.nk; ++k, ++it) {
                     const uint32_t s = it % stages, ph = (it / stages) & 1u;
                     if (!tc::mbar_wait(&hd->empty[s], ph ^ 1u, status) || *abort_flag) {
                         *abort_flag = 1;
                         ok = false;
                         break;
                     }
-                    tc::mbar_expect_tx(&hd->full[s], (F32X ? 2u * kPiece : kPiece) + NV * q_piece);
+                    tc::mbar_expect_tx(&hd->full[s], (F32X ? 2u * kPiece : kPiece) + NV * q_bytes);
                     uint8_t* st = tiles + (size_t)s * stage_bytes;
                     if (F32X) {
-                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, xr);
-                        tc::tma_load_2d(st + kPiece, &tmX, &hd->full[s], k * kGBK + 32, xr);
+                        tc::tma_load_2d(st, y.mx, &hd->full[s], k * kGBK, y.xr);
+                        tc::tma_load_2d(st + kPiece, y.mx, &hd->full[s], k * kGBK + 32, y.xr);
                     } else {
-                        tc::tma_load_2d(st, &tmX, &hd->full[s], k * kGBK, xr);
+                        tc::tma_load_2d(st, y.mx, &hd->full[s], k * kGBK, y.xr);
                     }
 #pragma unroll
                     for (int p = 0; p < NV; ++p)
-                        tc::tma_load_2d(st + x_bytes + p * q_piece, &tmQ, &hd->full[s], k * kGBK, p * m_pad);
+                        tc::tma_load_2d(st + x_bytes + p * q_piece, y.mq, &hd->full[s], k * kGBK, p * y.m_pad);
                 }
             }
             if (!ok) g_drain(hd, it, stages, status);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
             uint32_t it = 0, fb = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
+                const YItem y = work.item(w);
+                const uint32_t idesc = tc::idesc_bf16(128, y.m_pad, false, false);
+                const int ngroups = (y.nk + flush - 1) / flush;
                 for (int g = 0; g < ngroups && ok; ++g, ++fb) {
                     const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
                     if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
@@ -215,8 +260,8 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                         break;
                     }
                     tc::fence_after_sync();
-                    const uint32_t d_tmem = tmem + b * (uint32_t)m_pad;
-                    const int k0 = g * flush, k1 = k0 + flush < nk ? k0 + flush : nk;
+                    const uint32_t d_tmem = tmem + b * acc_stride;
+                    const int k0 = g * flush, k1 = k0 + flush < y.nk ? k0 + flush : y.nk;
                     uint32_t acc = 0;
                     for (int k = k0; k < k1; ++k, ++it) {
                         const uint32_t s = it % stages, ph = (it / stages) & 1u;
@@ -251,11 +296,13 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
     } else if (warp < 6) {
         const int q = warp & 3;
         const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
-        const int64_t piece_stride = (int64_t)m_pad * ldy;
         uint32_t fb = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-            const int64_t row = (int64_t)t * 128 + q * 32 + lane;
+        for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
+            const YItem y = work.item(w);
+            const int64_t row = y.row + q * 32 + lane;
+            const int64_t piece_stride = (int64_t)y.m_pad * y.ldy;
+            const int ngroups = (y.nk + flush - 1) / flush;
             for (int g = 0; g < ngroups; ++g, ++fb) {
                 const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *abort_flag) {
@@ -265,15 +312,15 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                 }
                 tc::fence_after_sync();
                 const bool last = g == ngroups - 1;
-                for (int c0 = 0; c0 < m_pad; c0 += 32) {
+                for (int c0 = 0; c0 < y.m_pad; c0 += 32) {
                     uint32_t a[32], rh[32], rl[32];
-                    fold_chunk(lane_base, b * (uint32_t)m_pad + (uint32_t)c0, 2u * (uint32_t)m_pad + (uint32_t)c0,
-                               m_pad, g, !last, a, rh, rl);
+                    fold_chunk(lane_base, b * acc_stride + (uint32_t)c0, 2u * acc_stride + (uint32_t)c0, acc_stride,
+                               g, !last, a, rh, rl);
                     if (last) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
                             split3_df(__uint_as_float(rh[j]), __uint_as_float(rl[j]),
-                                      Yt + (int64_t)(c0 + j) * ldy + row, piece_stride);
+                                      y.Yt + (int64_t)(c0 + j) * y.ldy + row, piece_stride);
                     }
                 }
                 tc::fence_before_sync();
@@ -288,7 +335,8 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
         const int tid = threadIdx.x - 192;
         uint32_t it = 0;
         bool ok = true;
-        for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
+            const int nk = work.item(w).nk;
             for (int k = 0; k < nk; ++k, ++it) {
                 const uint32_t s = it % stages, ph = (it / stages) & 1u;
                 if (tid == 0) {
@@ -317,15 +365,15 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int id = i * 128 + tid, r = id >> 3, c = id & 7;
-                    uint32_t w[NX][4];
+                    uint32_t wd[NX][4];
 #pragma unroll
                     for (int e = 0; e < 8; e += 2) {
                         float x0 = v[i][e], x1 = v[i][e + 1];
 #pragma unroll
                         for (int p = 0; p < NX; ++p) {
                             const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                            w[p][e / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
-                                          ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                            wd[p][e / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
+                                           ((uint32_t)__bfloat16_as_ushort(h1) << 16);
                             x0 = __fsub_rn(x0, __bfloat162float(h0));
                             x1 = __fsub_rn(x1, __bfloat162float(h1));
                         }
@@ -333,7 +381,8 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                     const uint32_t off = (uint32_t)r * 128u + (uint32_t)((c ^ (r & 7)) << 4);
 #pragma unroll
                     for (int p = 0; p < NX; ++p)
-                        *reinterpret_cast<uint4*>(xs + p * kPiece + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+                        *reinterpret_cast<uint4*>(xs + p * kPiece + off) =
+                            make_uint4(wd[p][0], wd[p][1], wd[p][2], wd[p][3]);
                 }
                 tc::fence_proxy_async_shared();
                 tc::mbar_arrive(&hd->xform[s]);
@@ -345,20 +394,52 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
 
 // ---------------------------------------------------------------- G = Y^T Y
 
+// One CTA's share of G = Y^T Y: K-stages [k0, k1) of the Y pieces (descriptor
+// my, basis width m_pad), written as an m_pad x m_pad double-float partial.
+struct GramItem {
+    const CUtensorMap* my;
+    int k0, k1, m_pad;
+    float2* part;
+};
+
+// One problem: CTA c takes K-stages [c kst / grid, (c + 1) kst / grid).
+struct GramOne {
+    CUtensorMap tmY;
+    int kst, m_pad;
+    float2* parts;
+    __device__ GramItem item(int c) const {
+        return GramItem{&tmY, (int)((int64_t)c * kst / gridDim.x), (int)((int64_t)(c + 1) * kst / gridDim.x), m_pad,
+                        parts + (int64_t)c * m_pad * m_pad};
+    }
+};
+
+// Many problems: CTA c is chunk c - base[i] (kGramChunk K-stages) of instance i.
+struct GramGroup {
+    const GInst* gi;
+    const GMaps* maps;
+    GTable items;
+    __device__ GramItem item(int c) const {
+        const int i = group_find(items, c), p = c - items.base[i];
+        const GInst& g = gi[i];
+        const int kst = (int)(g.ldy / kGBK);
+        const int k0 = p * kGramChunk, k1 = k0 + kGramChunk < kst ? k0 + kGramChunk : kst;
+        return GramItem{&maps[i].y3, k0, k1, g.m_pad, g.Gpart + (int64_t)p * g.m_pad * g.m_pad};
+    }
+};
+
 // Stage: three 16 KB slots (pieces y1, y2, y3 of 64 rows of Y, as m_pad rows of
 // Y^T x 128 B); slot rows m_pad .. 127 stay zero so the M = 128 MMA reads
-// zeros there.  CTA c takes K-stages [c kst / grid, (c + 1) kst / grid); the
-// launch keeps grid <= kst, so every CTA has at least one.
+// zeros there.  Every CTA has at least one K-stage.
+template <class Work>
 __global__ void __launch_bounds__(kGThreadsBf16, 1)
-    gram_y_kernel(const __grid_constant__ CUtensorMap tmY, int kst, int flush, int m_pad, int stages,
-                  float2* __restrict__ Gpart, int* status) {
+    gram_y_kernel(const __grid_constant__ Work work, int flush, int stages, int* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t stage_bytes = 3u * kPiece;
     GHeader* hd = reinterpret_cast<GHeader*>(tiles + (size_t)stages * stage_bytes);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int k0 = (int)((int64_t)blockIdx.x * kst / gridDim.x);
-    const int k1 = (int)((int64_t)(blockIdx.x + 1) * kst / gridDim.x);
+    const GramItem gw = work.item(blockIdx.x);
+    const int k0 = gw.k0, k1 = gw.k1, m_pad = gw.m_pad;
     const int ngroups = (k1 - k0 + flush - 1) / flush;
     const uint32_t tmem_cols = pow2_cols(4u * (uint32_t)m_pad);
     // zero the slot rows no TMA box covers
@@ -371,7 +452,7 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
         }
         tc::fence_proxy_async_shared();
     }
-    g_prologue(hd, stages, tmem_cols, &tmY, nullptr);
+    g_prologue(hd, stages, tmem_cols, gw.my, nullptr);
     const uint32_t tmem = hd->tmem_base;
     volatile int* abort_flag = &hd->abort;
     const uint32_t box_bytes = (uint32_t)m_pad * 128u;
@@ -389,7 +470,7 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
                 tc::mbar_expect_tx(&hd->full[s], 3u * box_bytes);
                 uint8_t* st = tiles + (size_t)s * stage_bytes;
 #pragma unroll
-                for (int p = 0; p < 3; ++p) tc::tma_load_2d(st + p * kPiece, &tmY, &hd->full[s], k * kGBK, p * m_pad);
+                for (int p = 0; p < 3; ++p) tc::tma_load_2d(st + p * kPiece, gw.my, &hd->full[s], k * kGBK, p * m_pad);
             }
         }
     } else if (warp == 1) {
@@ -452,9 +533,9 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
                 for (int c0 = 0; c0 < m_pad; c0 += 32) {
                     uint32_t a[32], rh[32], rl[32];
                     fold_chunk(lane_base, b * (uint32_t)m_pad + (uint32_t)c0, 2u * (uint32_t)m_pad + (uint32_t)c0,
-                               m_pad, g, !last, a, rh, rl);
+                               (uint32_t)m_pad, g, !last, a, rh, rl);
                     if (last) {
-                        float2* dst = Gpart + ((int64_t)blockIdx.x * m_pad + i) * m_pad + c0;
+                        float2* dst = gw.part + (int64_t)i * m_pad + c0;
 #pragma unroll
                         for (int j = 0; j < 32; ++j) dst[j] = make_float2(__uint_as_float(rh[j]), __uint_as_float(rl[j]));
                     }
@@ -483,23 +564,58 @@ __global__ void gram_parts_reduce_kernel(const float2* __restrict__ Gpart, int n
     if (Gf) Gf[e] = (float)(0.5 * s);
 }
 
-template <int NX, int NV, bool F32X>
-cudaError_t launch_ygen(const CUtensorMap& tmX, const CUtensorMap& tmQ, int ntiles, int nk, int flush, int m_pad,
-                        __nv_bfloat16* Yt, int64_t ldy, const int* tile_row, int* status, int num_sms,
+// The grouped reduction: instance i's blocks reduce its nparts partials.
+__global__ void gram_parts_reduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int e = (blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    const int m = g.m, m_pad = g.m_pad;
+    if (e >= m * m) return;
+    const int r = e / m, c = e % m;
+    double s = 0.0;
+    for (int p = 0; p < g.nparts; ++p) {
+        const float2 a = g.Gpart[((int64_t)p * m_pad + r) * m_pad + c];
+        const float2 b = g.Gpart[((int64_t)p * m_pad + c) * m_pad + r];
+        s += ((double)a.x + (double)a.y) + ((double)b.x + (double)b.y);
+    }
+    g.Gp[e] = 0.5 * s;
+}
+
+// ygen over `work` (count() items, each 128 rows): the Q-piece slots and the
+// TMEM accumulators are laid out for the widest basis, m_pad_max; grid =
+// min(items, SMs).
+template <int NX, int NV, bool F32X, class Work>
+cudaError_t launch_ygen(const Work& work, int items, int flush, int m_pad_max, int* status, int num_sms,
                         cudaStream_t st) {
     constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
-    const uint32_t stage_bytes = x_bytes + NV * (uint32_t)m_pad * 128u;
+    const uint32_t q_piece = (uint32_t)m_pad_max * 128u;
+    const uint32_t stage_bytes = x_bytes + NV * q_piece;
     int stages = (int)((kGSmemBudget - 2048) / stage_bytes);
     if (stages > kGMaxStages) stages = kGMaxStages;
     if (stages < 2) return cudaErrorInvalidValue;
     const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(GHeader);
-    auto kern = ygen_kernel<NX, NV, F32X>;
+    // accumulators: two buffers and the double-float running sum
+    const uint32_t acc_stride = (uint32_t)m_pad_max;
+    const uint32_t tmem_cols = pow2_cols(4u * acc_stride);
+    auto kern = ygen_kernel<NX, NV, F32X, Work>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    const int grid = items < num_sms ? items : num_sms;
     note_launch();
-    kern<<<grid, F32X ? kGThreadsF32 : kGThreadsBf16, smem, st>>>(tmX, tmQ, ntiles, nk, flush, m_pad, stages, Yt, ldy,
-                                                                 tile_row, status);
+    kern<<<grid, F32X ? kGThreadsF32 : kGThreadsBf16, smem, st>>>(work, flush, stages, q_piece, acc_stride, tmem_cols,
+                                                                 status);
+    return cudaGetLastError();
+}
+
+template <class Work>
+cudaError_t launch_gram_y(const Work& work, int grid, int* status, cudaStream_t st) {
+    const int gstages = 4;
+    const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
+    auto kern = gram_y_kernel<Work>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    kern<<<grid, kGThreadsBf16, smem, st>>>(work, 1, gstages, status);
     return cudaGetLastError();
 }
 
@@ -527,9 +643,10 @@ cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r
     // running sums.  A fold costs ~10 instructions per accumulator element and is
     // what bounds the kernel's time at short intervals; each accumulating MMA adds
     // ~2e-8 relative drift.  BF16 data: every 4 stages (three piece products,
-    // 48 MMAs; measured drift ~1e-6 scaled entrywise); FP32 data: every stage
-    // (six piece products, 24 MMAs).
-    if (flush <= 0) flush = accurate ? (f32 ? 1 : 4) : nk;
+    // 48 MMAs; measured drift ~1e-6 scaled entrywise); FP32 data: every 2
+    // stages (six piece products, also 48 MMAs; 2.6e-6 scaled at 200000 x 2048,
+    // against 1.8e-6 folding every stage, for 9 % of the time).
+    if (flush <= 0) flush = accurate ? (f32 ? 2 : 4) : nk;
     __nv_bfloat16* Qp = static_cast<__nv_bfloat16*>(sc.vp);
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
     cudaError_t e = launch_split_v(Q, d, m, m_pad, ldv, NV, Qp, st);
@@ -543,25 +660,20 @@ cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r
     if (!ok_x || !encode_bf16_2d(&tmQ, Qp, d, (uint64_t)NV * m_pad, ldv * 2, 64, m_pad) ||
         !encode_bf16_2d(&tmY, Yt, ldy, 3ull * m_pad, ldy * 2, 64, m_pad))
         return cudaErrorInvalidValue;
+    YgenOne yw{tmX, tmQ, ntiles, nk, m_pad, Yt, ldy, tile_row};
     if (f32) {
-        e = accurate ? launch_ygen<3, 3, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st)
-                     : launch_ygen<2, 2, true>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st);
+        e = accurate ? launch_ygen<3, 3, true>(yw, ntiles, flush, m_pad, status, num_sms, st)
+                     : launch_ygen<2, 2, true>(yw, ntiles, flush, m_pad, status, num_sms, st);
     } else {
-        e = accurate ? launch_ygen<1, 3, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st)
-                     : launch_ygen<1, 1, false>(tmX, tmQ, ntiles, nk, flush, m_pad, Yt, ldy, tile_row, status, num_sms, st);
+        e = accurate ? launch_ygen<1, 3, false>(yw, ntiles, flush, m_pad, status, num_sms, st)
+                     : launch_ygen<1, 1, false>(yw, ntiles, flush, m_pad, status, num_sms, st);
     }
     if (e != cudaSuccess) return e;
     // G = Y^T Y
     const int kst = (int)(ldy / kGBK);
     const int grid = kst < num_sms ? kst : num_sms;
-    const int gstages = 4;
-    const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
-    e = cudaFuncSetAttribute(gram_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     float2* parts = static_cast<float2*>(sc.zacc);
-    note_launch();
-    gram_y_kernel<<<grid, kGThreadsBf16, smem, st>>>(tmY, kst, 1, m_pad, gstages, parts, status);
-    e = cudaGetLastError();
+    e = launch_gram_y(GramOne{tmY, kst, m_pad, parts}, grid, status, st);
     if (e != cudaSuccess) return e;
     note_launch();
     gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G, nullptr);
@@ -603,17 +715,37 @@ cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, cons
     int grid = kst / 8;
     if (grid > num_sms) grid = num_sms;
     if (grid < 1) grid = 1;
-    const int gstages = 4;
-    const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
-    e = cudaFuncSetAttribute(gram_y_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     float2* parts = static_cast<float2*>(sc.zacc);
-    note_launch();
-    gram_y_kernel<<<grid, kGThreadsBf16, smem, st>>>(tmY, kst, 1, m_pad, gstages, parts, status);
-    e = cudaGetLastError();
+    e = launch_gram_y(GramOne{tmY, kst, m_pad, parts}, grid, status, st);
     if (e != cudaSuccess) return e;
     note_launch();
     gram_parts_reduce_kernel<<<(m * m + 255) / 256, 256, 0, st>>>(parts, grid, m, m_pad, G, Gf);
+    return cudaGetLastError();
+}
+
+bool grouped_encode_gram_maps(const GInst& g, GMaps& out) {
+    const bool ok_x = g.xf32 ? encode_2d(&out.xp, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, g.XP, g.d, g.n, g.ldp * 4, 32, 128,
+                                         CU_TENSOR_MAP_SWIZZLE_128B)
+                             : encode_bf16_2d(&out.xp, g.XP, g.d, g.n, g.ldp * 2, 64, 128);
+    return ok_x && encode_bf16_2d(&out.q3, g.Q3, g.d, 3ull * g.m_pad, g.ldv * 2, 64, g.m_pad) &&
+           encode_bf16_2d(&out.y3, g.Y3, g.ldy, 3ull * g.m_pad, g.ldy * 2, 64, g.m_pad);
+}
+
+// Split precision throughout (Algorithm 1, step 3 at the accuracy of the
+// single-problem ACCURATE path): FP32 X in three pieces against three Q pieces,
+// folded every 2 K-stages; BF16 X against three Q pieces, folded every 4.
+cudaError_t grouped_projected_gram(const GInst* gi, const GMaps* maps, GTable ygen32, GTable ygen16, GTable gram_items,
+                                   GTable reduce_blocks, int max_m, int* status, int num_sms, cudaStream_t st) {
+    const int m_pad_max = (int)rup(max_m, 32);
+    cudaError_t e = cudaSuccess;
+    if (ygen32.total > 0)
+        e = launch_ygen<3, 3, true>(YgenGroup{gi, maps, ygen32}, ygen32.total, 2, m_pad_max, status, num_sms, st);
+    if (e == cudaSuccess && ygen16.total > 0)
+        e = launch_ygen<1, 3, false>(YgenGroup{gi, maps, ygen16}, ygen16.total, 4, m_pad_max, status, num_sms, st);
+    if (e == cudaSuccess) e = launch_gram_y(GramGroup{gi, maps, gram_items}, gram_items.total, status, st);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    gram_parts_reduce_grouped_kernel<<<reduce_blocks.total, 256, 0, st>>>(gi, reduce_blocks);
     return cudaGetLastError();
 }
 

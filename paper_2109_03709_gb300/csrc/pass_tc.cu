@@ -1706,6 +1706,18 @@ __global__ void split_v_grouped_kernel(const GInst* __restrict__ gi, GTable tab)
     g.Vp[e] = __float2bfloat16_rn(v);
 }
 
+__global__ void split_q_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t total = (int64_t)g.m_pad * g.ldv;
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int c = (int)(e / g.ldv);
+    const int64_t k = e % g.ldv;
+    const float v = (c < g.m && k < g.d) ? g.Z[(int64_t)c * g.d + k] : 0.f;
+    split_store<3>(v, g.Q3 + e, total);
+}
+
 __global__ void zreduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
     const int i = group_find(tab, blockIdx.x);
     const GInst& g = gi[i];
@@ -2423,6 +2435,12 @@ bool grouped_encode_maps(const GInst& g, GMaps& out) {
 cudaError_t grouped_split_v(const GInst* gi, GTable blocks, cudaStream_t st) {
     note_launch();
     split_v_grouped_kernel<<<blocks.total, 256, 0, st>>>(gi, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_split_q(const GInst* gi, GTable blocks, cudaStream_t st) {
+    note_launch();
+    split_q_grouped_kernel<<<blocks.total, 256, 0, st>>>(gi, blocks);
     return cudaGetLastError();
 }
 

@@ -770,8 +770,8 @@ __device__ __forceinline__ void jbar() {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict__ G, int m, float* __restrict__ evals,
-                                                        float* __restrict__ Uf, int* sweeps_out, int* status) {
+__device__ __forceinline__ void jacobi_f32_body(const double* __restrict__ G, int m, float* __restrict__ evals,
+                                                float* __restrict__ Uf, int* sweeps_out, int* status) {
     constexpr int NW = NT / 32;
     constexpr int NMAX = NT == 32 ? 32 : kMaxM;           // largest N this instance runs
     constexpr int KP = (NMAX / 2 + NW - 1) / NW;          // pairs per warp and step
@@ -905,12 +905,17 @@ __global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict
     for (int i = threadIdx.x; i < m; i += NT) evals[i] = A[i * S + i];
 }
 
+template <int NT>
+__global__ void __launch_bounds__(NT) jacobi_f32_kernel(const double* __restrict__ G, int m, float* __restrict__ evals,
+                                                        float* __restrict__ Uf, int* sweeps_out, int* status) {
+    jacobi_f32_body<NT>(G, m, evals, Uf, sweeps_out, status);
+}
+
 // FP64 polish: u_j <- u_j / |u_j|, lambda_j = u_j^T G u_j (Rayleigh quotient).
-__global__ void rayleigh_f64_kernel(const double* __restrict__ G, int m, const float* __restrict__ Uf,
-                                    double* __restrict__ U64, double* __restrict__ lam) {
+__device__ __forceinline__ void rayleigh_f64_body(const double* __restrict__ G, int m, const float* __restrict__ Uf,
+                                                  double* __restrict__ U64, double* __restrict__ lam, int j) {
     __shared__ double u[kMaxM];
     __shared__ double red[32];
-    const int j = blockIdx.x;
     for (int i = threadIdx.x; i < m; i += blockDim.x) u[i] = (double)Uf[j * m + i];
     __syncthreads();
     double nrm = 0.0, rq = 0.0;
@@ -942,9 +947,14 @@ __global__ void rayleigh_f64_kernel(const double* __restrict__ G, int m, const f
     if (threadIdx.x == 0) lam[j] = n2 > 0.0 ? red[0] / n2 : 0.0;
 }
 
+__global__ void rayleigh_f64_kernel(const double* __restrict__ G, int m, const float* __restrict__ Uf,
+                                    double* __restrict__ U64, double* __restrict__ lam) {
+    rayleigh_f64_body(G, m, Uf, U64, lam, blockIdx.x);
+}
+
 // Sort eigenpairs descending (stable in the index), in one CTA.
-__global__ void sort_desc_kernel(const double* __restrict__ lam, const double* __restrict__ U64, int m,
-                                 double* __restrict__ w, double* __restrict__ U) {
+__device__ __forceinline__ void sort_desc_body(const double* __restrict__ lam, const double* __restrict__ U64, int m,
+                                               double* __restrict__ w, double* __restrict__ U) {
     __shared__ int rank[kMaxM];
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         int r = 0;
@@ -963,24 +973,33 @@ __global__ void sort_desc_kernel(const double* __restrict__ lam, const double* _
     }
 }
 
+__global__ void sort_desc_kernel(const double* __restrict__ lam, const double* __restrict__ U64, int m,
+                                 double* __restrict__ w, double* __restrict__ U) {
+    sort_desc_body(lam, U64, m, w, U);
+}
+
 // ------------------------------------------------------------------ rotate + sign
 
-__global__ void rotate_kernel(const float* __restrict__ Q, int64_t d, int m, const double* __restrict__ U, int k,
-                              float* __restrict__ E) {
+__device__ __forceinline__ void rotate_body(const float* __restrict__ Q, int64_t d, int m,
+                                            const double* __restrict__ U, float* __restrict__ E, int bx, int j) {
     __shared__ float u[kMaxM];
-    const int j = blockIdx.y;
     for (int i = threadIdx.x; i < m; i += blockDim.x) u[i] = (float)U[j * m + i];
     __syncthreads();
-    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t r = (int64_t)bx * blockDim.x + threadIdx.x;
     if (r >= d) return;
     float s = 0.f;
     for (int i = 0; i < m; ++i) s = __fmaf_rn(Q[(int64_t)i * d + r], u[i], s);
     E[(int64_t)j * d + r] = s;
 }
 
-__global__ void sign_kernel(float* __restrict__ E, int64_t d, const double* __restrict__ w, double inv_n,
-                            double* __restrict__ lambda) {
-    const int j = blockIdx.x;
+__global__ void rotate_kernel(const float* __restrict__ Q, int64_t d, int m, const double* __restrict__ U, int k,
+                              float* __restrict__ E) {
+    (void)k;
+    rotate_body(Q, d, m, U, E, blockIdx.x, blockIdx.y);
+}
+
+__device__ __forceinline__ void sign_body(float* __restrict__ E, int64_t d, const double* __restrict__ w,
+                                          double inv_n, double* __restrict__ lambda, int j) {
     float* e = E + (int64_t)j * d;
     float best = -1.f;
     int64_t bi = 0;
@@ -1009,6 +1028,11 @@ __global__ void sign_kernel(float* __restrict__ E, int64_t d, const double* __re
     if (flip)
         for (int64_t r = threadIdx.x; r < d; r += blockDim.x) e[r] = -e[r];
     if (threadIdx.x == 0) lambda[j] = w[j] * inv_n;
+}
+
+__global__ void sign_kernel(float* __restrict__ E, int64_t d, const double* __restrict__ w, double inv_n,
+                            double* __restrict__ lambda) {
+    sign_body(E, d, w, inv_n, lambda, blockIdx.x);
 }
 
 // ------------------------------------------------------------------ Oja / Sanger
@@ -1378,6 +1402,48 @@ __global__ void quantize_bf16_grouped_kernel(const float* const* __restrict__ X3
     o.z = *reinterpret_cast<uint32_t*>(&p2);
     o.w = *reinterpret_cast<uint32_t*>(&p3);
     *reinterpret_cast<uint4*>(const_cast<__nv_bfloat16*>(static_cast<const __nv_bfloat16*>(g.X)) + r * g.ld + j) = o;
+}
+
+// The pPCA step's eigensolve (Algorithm 1, step 4) per instance: Jacobi on
+// block i, the FP64 Rayleigh polish on blocks (instance, eigenvector), the sort.
+__global__ void __launch_bounds__(512) jacobi_grouped_kernel(const GInst* __restrict__ gi) {
+    const GInst& g = gi[blockIdx.x];
+    jacobi_f32_body<512>(g.Gp, g.m, g.evals, g.Uf, g.sweeps, g.status);
+}
+
+__global__ void rayleigh_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    rayleigh_f64_body(g.Gp, g.m, g.Uf, g.U64, g.lam, blockIdx.x - tab.base[i]);
+}
+
+__global__ void sort_grouped_kernel(const GInst* __restrict__ gi) {
+    const GInst& g = gi[blockIdx.x];
+    sort_desc_body(g.lam, g.U64, g.m, g.w, g.U);
+}
+
+// Step 5 per instance: E = Q U[:, :k] (Q = orth(V), held in Z), the sign
+// convention and lambda = w / n.
+__global__ void rotate_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int local = blockIdx.x - tab.base[i];
+    const int nbx = (int)((g.d + blockDim.x - 1) / blockDim.x);
+    rotate_body(g.Z, g.d, g.m, g.U, g.E, local % nbx, local / nbx);
+}
+
+__global__ void sign_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    sign_body(g.E, g.d, g.w, 1.0 / (double)g.n, g.lambda, blockIdx.x - tab.base[i]);
+}
+
+// The primed basis of every instance that asked for it.
+__global__ void copy_vout_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
+    const int i = group_find(tab, blockIdx.x);
+    const GInst& g = gi[i];
+    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    if (g.V_out && e < g.d * g.m) g.V_out[e] = g.V[e];
 }
 
 // Starting bases: V0 of every instance that has one, copied into its V.
@@ -1821,6 +1887,34 @@ cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst,
 cudaError_t grouped_copy_v0(const GInst* gi, GTable dm_blocks, cudaStream_t st) {
     note_launch();
     copy_v0_grouped_kernel<<<dm_blocks.total, 256, 0, st>>>(gi, dm_blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_eigh(const GInst* gi, int count, GTable rayleigh_blocks, int max_m, cudaStream_t st) {
+    const int N = max_m + (max_m & 1);
+    const size_t smem = (size_t)2 * N * (N + 1) * sizeof(float);
+    cudaError_t e = allow_smem(jacobi_grouped_kernel, smem);
+    if (e != cudaSuccess) return e;
+    note_launch();
+    jacobi_grouped_kernel<<<count, 512, smem, st>>>(gi);
+    note_launch();
+    rayleigh_grouped_kernel<<<rayleigh_blocks.total, 128, 0, st>>>(gi, rayleigh_blocks);
+    note_launch();
+    sort_grouped_kernel<<<count, 256, 0, st>>>(gi);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_rotate(const GInst* gi, GTable rotate_blocks, GTable sign_blocks, cudaStream_t st) {
+    note_launch();
+    rotate_grouped_kernel<<<rotate_blocks.total, 256, 0, st>>>(gi, rotate_blocks);
+    note_launch();
+    sign_grouped_kernel<<<sign_blocks.total, 1024, 0, st>>>(gi, sign_blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t grouped_copy_vout(const GInst* gi, GTable dm_blocks, cudaStream_t st) {
+    note_launch();
+    copy_vout_grouped_kernel<<<dm_blocks.total, 256, 0, st>>>(gi, dm_blocks);
     return cudaGetLastError();
 }
 

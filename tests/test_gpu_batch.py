@@ -160,8 +160,8 @@ def test_batch_bf16_priming_matches_oracle(cuda_device):
 
 
 def test_lockstep_priming_against_slots_and_oracle(cuda_device):
-    """Lockstep priming (every instance's power iterations in grouped launches)
-    on a mixed batch: FP32 instances primed on their BF16 rounding, BF16
+    """Lockstep batch (every instance's power iterations and pPCA step in
+    grouped launches: one launch per kernel kind and iteration) on a mixed batch: FP32 instances primed on their BF16 rounding, BF16
     instances primed as stored, ragged n (not multiples of 128) and m (not
     multiples of 32), one instance drawing its V0 from its seed.  Against the
     same batch primed on its slots (the per-instance path): the same pPCA-step
@@ -186,7 +186,7 @@ def test_lockstep_priming_against_slots_and_oracle(cuda_device):
         runs[lockstep] = (inst, P.ppca_batch_kernel_count(b))
     (inst_l, k_l), (inst_s, k_s) = runs[True], runs[False]
     print("kernels per run: lockstep", k_l, "slots", k_s)
-    assert k_l < k_s
+    assert k_l <= 40 + 13 * T < k_s                   # independent of the instance count
     for i, (a, c) in enumerate(zip(inst_l, inst_s)):
         Xs = a["X"].double().cpu().numpy()            # stored values (BF16 instances exactly)
         Xp = oracle.bf16_round_rne(Xs)                # the priming data of both paths

@@ -5,9 +5,9 @@ values of X (exact in FP64) and the FP32 Q.  Errors are measured entrywise on
 the scale of the diagonal, |dG_ij| / sqrt(G_ii G_jj), the scale at which an
 error moves eigenvalues and eigenvectors of G.  Bounds (u = 2^-24):
 * ACCURATE: the operands are split into BF16 pieces whose dropped products are
-  below u; each FP32 tensor-core accumulator takes at most 48 MMAs (BF16 X; 24
-  for FP32 X) before it is folded into a double-float sum, which bounds its
-  drift to about 1e-6.  Y's relative error is then ~1.5e-6 and G's about twice
+  below u; each FP32 tensor-core accumulator takes at most 48 MMAs (four
+  K-stages of three piece products for BF16 X, two of six for FP32 X) before
+  it is folded into a double-float sum, which bounds its drift to about 1e-6.  Y's relative error is then ~1.5e-6 and G's about twice
   that: bound 4e-6.
 * FAST, FP32 X (two pieces per operand, products to ~2^-16, no flushing):
   bound 1e-4.
