@@ -39,7 +39,7 @@ namespace ppca {
 namespace {
 
 constexpr int kGThreadsBf16 = 192;
-constexpr int kGThreadsF32 = 320;
+constexpr int kGThreadsF32 = 448;             // + two groups of four transform warps
 constexpr int kGMaxStages = 6;
 constexpr int kGBK = 64;                    // K extent of one stage (64 BF16 = 128 B)
 constexpr uint32_t kPiece = 128u * 128u;    // one 128-row x 128-byte operand tile
@@ -51,7 +51,7 @@ struct GHeader {
     uint64_t drain;                 // the MMA thread's completion barrier after an abort
     uint32_t tmem_base;
     int abort;
-    int xform_go;
+    int xform_go[2];
 };
 
 __host__ __device__ inline uint32_t pow2_cols(uint32_t need) {
@@ -78,7 +78,7 @@ __device__ inline void g_prologue(GHeader* hd, int stages, uint32_t tmem_cols, c
         }
         tc::mbar_init(&hd->drain, 1);
         hd->abort = 0;
-        hd->xform_go = 0;
+        hd->xform_go[0] = hd->xform_go[1] = 0;
         tc::mbar_init_fence();
         tc::tma_prefetch(m0);
         if (m1) tc::tma_prefetch(m1);
@@ -331,21 +331,24 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
         // Raw FP32 (two boxes of 128 rows x 32 columns, 128-byte swizzle) ->
         // NX BF16 pieces (128 rows x 64 columns, 128-byte swizzle), in place.
         // Task (r, c): row r, piece chunk c = columns 8c .. 8c+7 = raw box c / 4,
-        // raw chunks 2 (c % 4) and 2 (c % 4) + 1.
-        const int tid = threadIdx.x - 192;
+        // raw chunks 2 (c % 4) and 2 (c % 4) + 1.  Two groups of four warps take
+        // the even and the odd stages, so two stages are split at once.
+        const int grp = (warp - 6) / 4;
+        const int tid = threadIdx.x - 192 - grp * 128;
         uint32_t it = 0;
         bool ok = true;
         for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
             const int nk = work.item(w).nk;
             for (int k = 0; k < nk; ++k, ++it) {
+                if ((int)(it & 1u) != grp) continue;
                 const uint32_t s = it % stages, ph = (it / stages) & 1u;
                 if (tid == 0) {
                     const bool go = tc::mbar_wait(&hd->full[s], ph, status) && !*abort_flag;
                     if (!go) *abort_flag = 1;
-                    *(volatile int*)&hd->xform_go = go ? 1 : 0;
+                    *(volatile int*)&hd->xform_go[grp] = go ? 1 : 0;
                 }
-                tc::named_barrier(1, 128);
-                if (!*(volatile int*)&hd->xform_go) {
+                tc::named_barrier(1 + grp, 128);
+                if (!*(volatile int*)&hd->xform_go[grp]) {
                     ok = false;
                     break;
                 }
@@ -361,7 +364,7 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                     v[i][0] = u0.x; v[i][1] = u0.y; v[i][2] = u0.z; v[i][3] = u0.w;
                     v[i][4] = u1.x; v[i][5] = u1.y; v[i][6] = u1.z; v[i][7] = u1.w;
                 }
-                tc::named_barrier(1, 128);
+                tc::named_barrier(1 + grp, 128);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int id = i * 128 + tid, r = id >> 3, c = id & 7;
