@@ -918,8 +918,9 @@ def measure_batch(cfg, T, count, seed, slots, bf16_priming, steps, warmup, locks
     if bf16_priming:
         P.ppca_batch_set_priming(b, P.PPCA_BF16)
     P.ppca_batch_set_lockstep(b, lockstep)
+    # the slots' per-group schedules: only the slot path runs per-instance passes
     t_tune = time.perf_counter()
-    groups = P.ppca_batch_autotune(b, 2)
+    groups = P.ppca_batch_autotune(b, 2) if not lockstep else 0
     t_tune = time.perf_counter() - t_tune
     for _ in range(max(warmup, 1)):
         P.ppca_batch_run(b)
@@ -971,8 +972,11 @@ def run_batch(args):
                        "l2": f"inputs ({rec['data_gb']:.0f} GB) larger than L2, no flush"},
             "roofline": {"bound": "hbm", "achieved": round(value, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": round(value / peaks["hbm_gbs"], 4), "traffic": None, "peak_source": peak_kind,
-                         "kernel": "whole batch step: priming passes, projected-Gram pPCA step, "
-                                   "CholeskyQR2 and Jacobi per instance"},
+                         "kernel": ("whole batch step, every instance in lockstep: BF16 rounding, T two-kernel "
+                                    "BF16 passes and CholeskyQR2s, split-precision projected Gram, Jacobi, "
+                                    "one grouped launch per kernel kind" if rec["lockstep"] else
+                                    "whole batch step on the slots: priming passes, projected-Gram pPCA step, "
+                                    "CholeskyQR2 and Jacobi per instance")},
             "clocks": clk, "gpu_launches": rec["kernels_per_run"] * args.steps}
     if rank == 0:
         print(json.dumps(line))
