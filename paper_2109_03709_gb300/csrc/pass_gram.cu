@@ -48,6 +48,7 @@ constexpr int kGSmemBudget = 227 * 1024;       // the opt-in maximum per block
 struct GHeader {
     uint64_t full[kGMaxStages], xform[kGMaxStages], empty[kGMaxStages];
     uint64_t tfull[2], tempty[2];
+    uint64_t bempty;                // split accumulation: the tile's small-piece sum has been read
     uint64_t drain;                 // the MMA thread's completion barrier after an abort
     uint32_t tmem_base;
     int abort;
@@ -76,6 +77,7 @@ __device__ inline void g_prologue(GHeader* hd, int stages, uint32_t tmem_cols, c
             tc::mbar_init(&hd->tfull[i], 1);
             tc::mbar_init(&hd->tempty[i], 128);
         }
+        tc::mbar_init(&hd->bempty, 128);
         tc::mbar_init(&hd->drain, 1);
         hd->abort = 0;
         hd->xform_go[0] = hd->xform_go[1] = 0;
@@ -194,13 +196,22 @@ struct YgenGroup {
 
 // Stage: [X area][Q piece 0 .. NV-1], pieces q_piece bytes apart.  X area: BF16
 // X -> one 16 KB tile; FP32 X -> two raw 32-column boxes (32 KB), overwritten in
-// place by the NX pieces.  TMEM: accumulator b at column b * acc_stride, the
-// double-float running sum at [2, 4) * acc_stride.
+// place by the NX pieces.
+//
+// Accumulation.  FAST (one or three products, no fold): accumulator b at TMEM
+// column b * acc_stride, the double-float running sum at [2, 4) * acc_stride.
+// Split precision (NV = 3): the leading product x_0 q_0 goes to accumulator b,
+// emptied every `flush` K-stages into an FP32 running sum R (column 2
+// acc_stride); the other products, at most 2^-8 of Y, go to one accumulator S
+// (column 3 acc_stride) for the whole tile: an accumulator drifts relative to
+// its own size, so S needs no fold, and a fold of the leading product alone is
+// a load, an add and a store.  Y = (R + acc_last) + S.
 template <int NX, int NV, bool F32X, class Work>
 __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
     ygen_kernel(const __grid_constant__ Work work, int flush, int stages, uint32_t q_piece, uint32_t acc_stride,
                 uint32_t tmem_cols, int* status) {
     constexpr int ORD = (NX > NV ? NX : NV) - 1;
+    constexpr bool SPLIT = NV == 3;
     constexpr uint32_t x_bytes = F32X ? (NX > 2 ? NX : 2) * kPiece : kPiece;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
@@ -246,12 +257,22 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            uint32_t it = 0, fb = 0;
+            uint32_t it = 0, fb = 0, tl = 0;
             bool ok = true;
-            for (int w = blockIdx.x; w < count && ok; w += gridDim.x) {
+            for (int w = blockIdx.x; w < count && ok; w += gridDim.x, ++tl) {
                 const YItem y = work.item(w);
                 const uint32_t idesc = tc::idesc_bf16(128, y.m_pad, false, false);
                 const int ngroups = (y.nk + flush - 1) / flush;
+                const uint32_t s_tmem = tmem + 3u * acc_stride;
+                uint32_t acc_s = 0;
+                if (SPLIT) {
+                    // the previous tile's small-piece sum must have been read
+                    if (!tc::mbar_wait(&hd->bempty, (tl & 1u) ^ 1u, status) || *abort_flag) {
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                }
                 for (int g = 0; g < ngroups && ok; ++g, ++fb) {
                     const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
                     if (!tc::mbar_wait(&hd->tempty[b], tph ^ 1u, status) || *abort_flag) {
@@ -282,8 +303,13 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                                     const uint64_t ad = tc::smem_desc_sw128(a0 + pa * kPiece + kk * 32, 16, 1024);
                                     const uint64_t bd =
                                         tc::smem_desc_sw128(a0 + x_bytes + pb * q_piece + kk * 32, 16, 1024);
-                                    tc::mma_f16(d_tmem, ad, bd, idesc, acc);
-                                    acc = 1;
+                                    if (SPLIT && (pa | pb) != 0) {
+                                        tc::mma_f16(s_tmem, ad, bd, idesc, acc_s);
+                                        acc_s = 1;
+                                    } else {
+                                        tc::mma_f16(d_tmem, ad, bd, idesc, acc);
+                                        acc = 1;
+                                    }
                                 }
                             }
                         }
@@ -313,18 +339,42 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                 tc::fence_after_sync();
                 const bool last = g == ngroups - 1;
                 for (int c0 = 0; c0 < y.m_pad; c0 += 32) {
-                    uint32_t a[32], rh[32], rl[32];
-                    fold_chunk(lane_base, b * acc_stride + (uint32_t)c0, 2u * acc_stride + (uint32_t)c0, acc_stride,
-                               g, !last, a, rh, rl);
-                    if (last) {
+                    if (SPLIT) {
+                        const uint32_t a_col = b * acc_stride + (uint32_t)c0, r_col = 2u * acc_stride + (uint32_t)c0;
+                        uint32_t a[32], r[32];
+                        tc::tmem_ld32(lane_base + a_col, a);
+                        if (g > 0) tc::tmem_ld32(lane_base + r_col, r);
+                        tc::tmem_ld_wait();
+                        if (g > 0) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            split3_df(__uint_as_float(rh[j]), __uint_as_float(rl[j]),
-                                      y.Yt + (int64_t)(c0 + j) * y.ldy + row, piece_stride);
+                            for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(a[j]));
+                        }
+                        if (!last) {
+                            tc::tmem_st32(lane_base + r_col, a);
+                            tc::tmem_st_wait();
+                        } else {
+                            tc::tmem_ld32(lane_base + 3u * acc_stride + (uint32_t)c0, r);
+                            tc::tmem_ld_wait();
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                split3_df(__uint_as_float(a[j]) + __uint_as_float(r[j]), 0.f,
+                                          y.Yt + (int64_t)(c0 + j) * y.ldy + row, piece_stride);
+                        }
+                    } else {
+                        uint32_t a[32], rh[32], rl[32];
+                        fold_chunk(lane_base, b * acc_stride + (uint32_t)c0, 2u * acc_stride + (uint32_t)c0,
+                                   acc_stride, g, !last, a, rh, rl);
+                        if (last) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                split3_df(__uint_as_float(rh[j]), __uint_as_float(rl[j]),
+                                          y.Yt + (int64_t)(c0 + j) * y.ldy + row, piece_stride);
+                        }
                     }
                 }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&hd->tempty[b]);
+                if (SPLIT && last) tc::mbar_arrive(&hd->bempty);
             }
         }
     } else if (F32X) {
@@ -642,14 +692,12 @@ cudaError_t projected_gram_impl(const XView& x, const float* Q, int m, int64_t r
     const int64_t ldv = rup(d, 8), ldy = tile_row ? (int64_t)nsel * 128 : rup(rows, 128);
     const int ntiles = (int)(ldy / 128), nk = (int)((d + kGBK - 1) / kGBK);
     const int NV = accurate ? 3 : (f32 ? 2 : 1);
-    // K-stages per fold of the FP32 tensor-core accumulator into the double-float
-    // running sums.  A fold costs ~10 instructions per accumulator element and is
-    // what bounds the kernel's time at short intervals; each accumulating MMA adds
-    // ~2e-8 relative drift.  BF16 data: every 4 stages (three piece products,
-    // 48 MMAs; measured drift ~1e-6 scaled entrywise); FP32 data: every 2
-    // stages (six piece products, also 48 MMAs; 2.6e-6 scaled at 200000 x 2048,
-    // against 1.8e-6 folding every stage, for 9 % of the time).
-    if (flush <= 0) flush = accurate ? (f32 ? 2 : 4) : nk;
+    // K-stages per fold of the leading product's FP32 tensor-core accumulator
+    // into the running sum.  Each accumulating MMA adds ~2e-8 drift relative to
+    // the accumulator: a fold every 12 stages lets it take 48 MMAs (4 per
+    // stage), the drift the earlier all-products accumulator had at a fold every
+    // 4 (BF16 X) or 2 (FP32 X) stages, at a twelfth of the folds.
+    if (flush <= 0) flush = accurate ? 12 : nk;
     __nv_bfloat16* Qp = static_cast<__nv_bfloat16*>(sc.vp);
     __nv_bfloat16* Yt = static_cast<__nv_bfloat16*>(sc.yt);
     cudaError_t e = launch_split_v(Q, d, m, m_pad, ldv, NV, Qp, st);
@@ -735,16 +783,16 @@ bool grouped_encode_gram_maps(const GInst& g, GMaps& out) {
 }
 
 // Split precision throughout (Algorithm 1, step 3 at the accuracy of the
-// single-problem ACCURATE path): FP32 X in three pieces against three Q pieces,
-// folded every 2 K-stages; BF16 X against three Q pieces, folded every 4.
+// single-problem ACCURATE path): FP32 X in three pieces or BF16 X against three
+// Q pieces, the leading product folded every 12 K-stages.
 cudaError_t grouped_projected_gram(const GInst* gi, const GMaps* maps, GTable ygen32, GTable ygen16, GTable gram_items,
                                    GTable reduce_blocks, int max_m, int* status, int num_sms, cudaStream_t st) {
     const int m_pad_max = (int)rup(max_m, 32);
     cudaError_t e = cudaSuccess;
     if (ygen32.total > 0)
-        e = launch_ygen<3, 3, true>(YgenGroup{gi, maps, ygen32}, ygen32.total, 2, m_pad_max, status, num_sms, st);
+        e = launch_ygen<3, 3, true>(YgenGroup{gi, maps, ygen32}, ygen32.total, 12, m_pad_max, status, num_sms, st);
     if (e == cudaSuccess && ygen16.total > 0)
-        e = launch_ygen<1, 3, false>(YgenGroup{gi, maps, ygen16}, ygen16.total, 4, m_pad_max, status, num_sms, st);
+        e = launch_ygen<1, 3, false>(YgenGroup{gi, maps, ygen16}, ygen16.total, 12, m_pad_max, status, num_sms, st);
     if (e == cudaSuccess) e = launch_gram_y(GramGroup{gi, maps, gram_items}, gram_items.total, status, st);
     if (e != cudaSuccess) return e;
     note_launch();
