@@ -359,6 +359,21 @@ typedef struct ppca_timing {
     int64_t launches;         /* kernels the library launched (all handles) since the reset */
 } ppca_timing;
 
+/*
+ * Graph-replayed minibatch steps (enable != 0, the default).  Oja (Section 2.2)
+ * and EigenGame (Section 2.3) take one minibatch per step; the steps of full
+ * minibatches differ only in the batch's first row and, for Oja, in the step
+ * size lr / (t + lr_offset).  With this on, ppca_prime / ppca_prime_continue
+ * read both from device memory and run blocks of 16 such steps from a CUDA graph
+ * captured once (per handle, shape and parameters) on a private stream joined
+ * to the handle's stream by events; steps that hold an epoch's partial batch,
+ * FP8 data, minibatches that are not whole 128-row tiles, row sharding, pass
+ * timing and the CUDA-core engine run step by step.  The results are the same
+ * bits either way (the same kernels and arithmetic).  enable == 0: always step
+ * by step.  Infrastructure: no counterpart in the paper.
+ */
+PPCA_API ppca_status ppca_set_step_graphs(ppca_handle *h, int32_t enable);
+
 /* enable != 0: record a CUDA event pair around every X-pass of this handle,
  * on its stream, and reset the counters; enable == 0: stop recording.
  * Measurement infrastructure: no counterpart in the paper. */

@@ -30,7 +30,7 @@ __all__ = [
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured", "ppca_set_wait_limit",
     "ppca_set_allreduce", "TorchAllReduce", "ppca_batch_set_priming", "ppca_batch_set_lockstep",
-    "ppca_batch_lockstep", "EXPORTED_SYMBOLS",
+    "ppca_batch_lockstep", "ppca_set_step_graphs", "EXPORTED_SYMBOLS",
 ]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -55,7 +55,7 @@ EXPORTED_SYMBOLS = [
     "ppca_batch_create", "ppca_batch_run", "ppca_batch_sync", "ppca_batch_destroy", "ppca_batch_kernel_count",
     "ppca_upload", "ppca_finalize_host", "ppca_finalize_sampled", "ppca_variance_captured",
     "ppca_set_wait_limit", "ppca_set_allreduce", "ppca_batch_set_priming", "ppca_batch_set_lockstep",
-    "ppca_batch_lockstep",
+    "ppca_batch_lockstep", "ppca_set_step_graphs",
 ]
 
 
@@ -162,6 +162,7 @@ _SIGS = {
     "ppca_set_allreduce": (_c_status, [_vp, _vp, _vp, _i64, _vp, _i64]),
     "ppca_batch_set_priming": (_c_status, [_vp, _i32]),
     "ppca_batch_set_lockstep": (_c_status, [_vp, _i32]),
+    "ppca_set_step_graphs": (_c_status, [_vp, _i32]),
     "ppca_batch_lockstep": (_c_status, [_vp, ctypes.POINTER(_i32)]),
     "ppca_autotune": (_c_status, [_vp, _i32, _i64, _i32, ctypes.POINTER(ppca_schedule)]),
     "ppca_batch_autotune": (_c_status, [_vp, _i32, ctypes.POINTER(_i32)]),
@@ -509,6 +510,11 @@ def ppca_set_schedule(h: Handle, fused: int = -1, producers: int = 0, window: in
                       engine: int = 0, kparts: int = 0, l2_keep: int = 0, fp8_mma: int = 0):
     s = ppca_schedule(fused, producers, window, flush, engine, kparts, l2_keep, fp8_mma)
     _check(load_library().ppca_set_schedule(h.ptr, ctypes.byref(s)), "ppca_set_schedule")
+
+
+def ppca_set_step_graphs(h: Handle, enable: bool):
+    """Run full-minibatch Oja / EigenGame steps from a captured CUDA graph (default) or step by step."""
+    _check(load_library().ppca_set_step_graphs(h.ptr, 1 if enable else 0), "ppca_set_step_graphs")
 
 
 def ppca_set_wait_limit(ns: int = 0):

@@ -118,6 +118,15 @@ struct ppca_handle {
     int64_t ar_stage_bytes = 0;
     int64_t n_total = 0;
 
+    // minibatch steps (Oja, EigenGame) replayed from a CUDA graph of kStepGraph
+    // steps, captured once per shape and parameters (step_graphs)
+    bool step_graphs = true;
+    PrimerStep* pstep = nullptr;
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    unsigned char gkey[160] = {};
+
     // measurement
     bool timing = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
@@ -137,6 +146,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     size_t need = 5 * dm + al256((size_t)m * m * 8) + 2 * al256((size_t)m * m * 4) + al256((size_t)m * 8) +
                   al256((size_t)m * m * 8) + al256(gram_part_floats(d, m) * 4) + al256(jacobi_scratch_bytes(m)) +
                   dm + al256((size_t)m * 8) + al256((size_t)((n + 127) / 128) * 4) + al256(8) +
+                  al256(sizeof(PrimerStep)) +
                   al256(eigengame_scratch_bytes(d, m)) + al256(simt_pass_scratch_floats(n, d, m, nsplit) * 4) +
                   al256(tc_pass_scratch_bytes(n, d, m, h->num_sms));
     if (h->ws_limit > 0 && (int64_t)need > h->ws_limit)
@@ -172,6 +182,7 @@ ppca_status ensure_workspace_dims(ppca_handle* h, int64_t n, int64_t d, int m) {
     h->lam_res = reinterpret_cast<double*>(take((size_t)m * 8));
     h->tile_rows = reinterpret_cast<int*>(take((size_t)((n + 127) / 128) * 4));
     h->seq_diff = reinterpret_cast<double*>(take(8));
+    h->pstep = reinterpret_cast<PrimerStep*>(take(sizeof(PrimerStep)));
     h->gram_part = reinterpret_cast<float*>(take(gram_part_floats(d, m) * 4));
     h->jac = take(jacobi_scratch_bytes(m));
     h->eg = reinterpret_cast<double*>(take(eigengame_scratch_bytes(d, m)));
@@ -365,10 +376,159 @@ ppca_status run_power_seq(ppca_handle* h, int64_t T) {
     return PPCA_OK;
 }
 
+// One minibatch step of Oja or EigenGame with host-side parameters.
+ppca_status minibatch_step(ppca_handle* h) {
+    const int m = h->m;
+    const int64_t n = h->x.n, d = h->x.d;
+    int64_t r0, r1;
+    minibatch(h->t, n, h->params.batch, r0, r1);
+    PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
+    PPCA_TRY(allreduce(h, h->Z, d * m, 4));                                       // the batch of all ranks
+    int64_t b = 0;
+    PPCA_TRY(global_rows(h, r1 - r0, &b));
+    if (h->method == PPCA_OJA) {
+        CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));       // S = Y^T Y = W^T Z
+        const double lr = h->params.lr / ((double)h->t + h->params.lr_offset);
+        CUDA_TRY(oja_update(h->V, h->Z, h->G, d, m, lr / (double)b, h->stream));
+    } else {
+        CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));       // C = V^T Z
+        CUDA_TRY(eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)b, h->params.lr,
+                                  h->params.momentum, h->eg, h->stream));
+    }
+    ++h->t;
+    return PPCA_OK;
+}
+
+// Graph-replayed steps.  Full minibatches of one epoch differ only in their
+// first row (and Oja in its step size), so a step whose kernels read those
+// from the device state (primer_step_begin) is the same for every t: a CUDA
+// graph of kStepGraph such steps is captured once and replayed, saving the
+// launch gaps of its ~10 small kernels per step.  The kernels and their
+// arithmetic are those of minibatch_step: the results are the same bits.
+constexpr int kStepGraph = 16;
+
+struct StepGraphKey {
+    int method, m, dtype, prec;
+    int64_t n, d, ld, batch;
+    const void* x;
+    const void* ws;
+    double lr, lr_offset, momentum;
+    TcSchedule sched;
+};
+
+bool step_graph_eligible(const ppca_handle* h) {
+    if (!h->step_graphs || h->ar_fn || h->timing) return false;
+    if (h->method != PPCA_OJA && h->method != PPCA_EIGENGAME) return false;
+    const ppca_precision prec = prime_prec(h);
+    const bool supported = tc_pass_supported(h->x, h->m);
+    const bool tc = h->sched.engine == 2 ? false
+                    : h->sched.engine == 1 ? supported
+                                           : supported && !(h->x.dtype == PPCA_F32 && prec == PPCA_PREC_ACCURATE);
+    const int64_t b = h->params.batch;
+    return tc && b <= h->x.n && xpass_tc_row0_same(h->x, b, prec, h->sched, h->num_sms);
+}
+
+ppca_status build_step_graph(ppca_handle* h, const StepGraphKey& key) {
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    if (!h->gstream) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&h->gev_in, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventCreateWithFlags(&h->gev_out, cudaEventDisableTiming));
+    }
+    const int m = h->m;
+    const int64_t n = h->x.n, d = h->x.d, b = h->params.batch, per_epoch = (n + b - 1) / b;
+    const bool oja = h->method == PPCA_OJA;
+    cudaStream_t st = h->gstream;
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < kStepGraph && e == cudaSuccess; ++i) {
+        e = primer_step_begin(h->pstep, per_epoch, b, oja ? h->params.lr : 0.0, oja ? h->params.lr_offset : 1.0, st);
+        if (e == cudaSuccess)
+            e = xpass_tc(h->x, h->V, m, 0, b, h->Z, prime_prec(h), h->tc, h->sched, h->status, h->num_sms, st,
+                         &h->pstep->row0);
+        if (e == cudaSuccess) e = gram_df(h->V, h->Z, d, m, h->G, h->gram_part, st);
+        if (e == cudaSuccess)
+            e = oja ? oja_update(h->V, h->Z, h->G, d, m, 0.0, st, &h->pstep->c)
+                    : eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)b, h->params.lr,
+                                       h->params.momentum, h->eg, st);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (e == cudaSuccess) e = ee;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->gexec = nullptr;
+        return fail(PPCA_ERR_CUDA, "capturing the minibatch steps failed: %s", cudaGetErrorString(e));
+    }
+    static_assert(sizeof(StepGraphKey) <= sizeof(h->gkey), "step graph key");
+    std::memcpy(h->gkey, &key, sizeof key);
+    return PPCA_OK;
+}
+
+// Runs as many whole graphs of full-minibatch steps as fit in `remaining` from
+// step h->t on (none if the next kStepGraph steps hold the epoch's partial
+// batch); *done = the steps run.
+ppca_status step_graphs(ppca_handle* h, int64_t remaining, int64_t* done) {
+    *done = 0;
+    if (remaining < kStepGraph || !step_graph_eligible(h)) return PPCA_OK;
+    const int64_t n = h->x.n, b = h->params.batch, per_epoch = (n + b - 1) / b;
+    const int64_t full = n % b == 0 ? per_epoch : per_epoch - 1;     // full batches per epoch
+    int64_t blocks = 0;
+    for (int64_t t = h->t; remaining - blocks * kStepGraph >= kStepGraph; t += kStepGraph) {
+        if (n % b != 0 && (t % per_epoch) + kStepGraph > full) break;
+        ++blocks;
+    }
+    if (blocks == 0) return PPCA_OK;
+    StepGraphKey key;
+    std::memset(&key, 0, sizeof key);
+    key.method = h->method;
+    key.m = h->m;
+    key.dtype = h->x.dtype;
+    key.prec = prime_prec(h);
+    key.n = n;
+    key.d = h->x.d;
+    key.ld = h->x.ld;
+    key.batch = b;
+    key.x = h->x.ptr;
+    key.ws = h->ws;
+    key.lr = h->params.lr;
+    key.lr_offset = h->params.lr_offset;
+    key.momentum = h->params.momentum;
+    key.sched = h->sched;
+    if (!h->gexec || std::memcmp(h->gkey, &key, sizeof key) != 0) PPCA_TRY(build_step_graph(h, key));
+    CUDA_TRY(cudaEventRecord(h->gev_in, h->stream));
+    CUDA_TRY(cudaStreamWaitEvent(h->gstream, h->gev_in, 0));
+    CUDA_TRY(primer_step_set(h->pstep, h->t, h->gstream));
+    for (int64_t i = 0; i < blocks; ++i) CUDA_TRY(cudaGraphLaunch(h->gexec, h->gstream));
+    CUDA_TRY(cudaEventRecord(h->gev_out, h->gstream));
+    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->gev_out, 0));
+    h->t += blocks * kStepGraph;
+    *done = blocks * kStepGraph;
+    return PPCA_OK;
+}
+
 ppca_status run_steps(ppca_handle* h, int64_t T) {
     const int m = h->m;
     const int64_t n = h->x.n, d = h->x.d;
     if (h->method == PPCA_POWER_SEQ) return run_power_seq(h, T);
+    if (h->method == PPCA_OJA || h->method == PPCA_EIGENGAME) {
+        int64_t i = 0;
+        while (i < T) {
+            int64_t g = 0;
+            PPCA_TRY(step_graphs(h, T - i, &g));
+            i += g;
+            if (i < T) {
+                PPCA_TRY(minibatch_step(h));
+                ++i;
+            }
+        }
+        return PPCA_OK;
+    }
     for (int64_t i = 0; i < T; ++i) {
         switch (h->method) {
         case PPCA_POWER:
@@ -377,32 +537,6 @@ ppca_status run_steps(ppca_handle* h, int64_t T) {
             PPCA_TRY(run_orth(h, h->Z, h->V, m));
             ++h->iters;
             break;
-        case PPCA_OJA: {
-            int64_t r0, r1;
-            minibatch(h->t, n, h->params.batch, r0, r1);
-            PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
-            PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // the batch of all ranks
-            int64_t b = 0;
-            PPCA_TRY(global_rows(h, r1 - r0, &b));
-            CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // S = Y^T Y = W^T Z
-            const double lr = h->params.lr / ((double)h->t + h->params.lr_offset);
-            CUDA_TRY(oja_update(h->V, h->Z, h->G, d, m, lr / (double)b, h->stream));
-            ++h->t;
-            break;
-        }
-        case PPCA_EIGENGAME: {
-            int64_t r0, r1;
-            minibatch(h->t, n, h->params.batch, r0, r1);
-            PPCA_TRY(run_xpass(h, h->x, h->V, m, r0, r1, h->Z, prime_prec(h)));
-            PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // the batch of all ranks
-            int64_t b = 0;
-            PPCA_TRY(global_rows(h, r1 - r0, &b));
-            CUDA_TRY(gram_df(h->V, h->Z, d, m, h->G, h->gram_part, h->stream));   // C = V^T Z
-            CUDA_TRY(eigengame_update(h->V, h->buf, h->Z, h->G, d, m, 1.0 / (double)b, h->params.lr,
-                                      h->params.momentum, h->eg, h->stream));
-            ++h->t;
-            break;
-        }
         default:
             return fail(PPCA_ERR_STATE, "no priming method set");
         }
@@ -953,9 +1087,22 @@ ppca_status ppca_destroy(ppca_handle* h) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gstream) {
+        cudaStreamSynchronize(h->gstream);
+        cudaStreamDestroy(h->gstream);
+    }
+    if (h->gev_in) cudaEventDestroy(h->gev_in);
+    if (h->gev_out) cudaEventDestroy(h->gev_out);
     if (h->ws) cudaFree(h->ws);
     if (h->status) cudaFree(h->status);
     delete h;
+    return PPCA_OK;
+}
+
+ppca_status ppca_set_step_graphs(ppca_handle* h, int32_t enable) {
+    if (!h) return fail(PPCA_ERR_INVALID, "handle is NULL");
+    h->step_graphs = enable != 0;
     return PPCA_OK;
 }
 

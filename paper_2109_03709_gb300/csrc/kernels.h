@@ -75,7 +75,19 @@ cudaError_t sample_blocks(int64_t n, double fraction, uint64_t seed, int64_t for
 
 // Oja/Sanger update: W += c (Z - W triu(S)), S = W^T Z (m x m FP64 row-major), c = lr / b.
 cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c,
-                       cudaStream_t st);
+                       cudaStream_t st, const float* c_dev = nullptr);
+
+// Device state of graph-replayed minibatch steps (Oja, EigenGame): the step
+// index, the first row of its minibatch, Oja's coefficient lr / (t + lr_offset) / b.
+struct PrimerStep {
+    int64_t t;
+    int64_t row0;
+    float c;
+};
+// One step's state from t (then t advances); setting t before a replay.
+cudaError_t primer_step_begin(PrimerStep* ps, int64_t per_epoch, int64_t b, double lr, double lr_offset,
+                              cudaStream_t st);
+cudaError_t primer_step_set(PrimerStep* ps, int64_t t, cudaStream_t st);
 
 // EigenGame update from Z = X_b^T X_b V and C = V^T Z (both unnormalised by b):
 // MV = Z / b, Riemannian gradient, Nesterov momentum (buf), step lr, renormalise.

@@ -171,7 +171,8 @@ template <int S, bool FP8X>
 __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
     xv_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles,
                  int nk, int m_pad, int stages, __nv_bfloat16* __restrict__ Yt, int64_t ldy, int ksplit,
-                 float* __restrict__ Ypart, const float* __restrict__ scales, int64_t rows, int* status) {
+                 float* __restrict__ Ypart, const float* __restrict__ scales, int64_t rows, int* status,
+                 const int64_t* __restrict__ row0) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     constexpr uint32_t raw_bytes = FP8X ? 128u * 64u : 0u;
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            const int xr0 = row0 ? (int)*row0 : 0;     // device-side first row of X (graph-replayed steps)
             for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x) {
                 const int t = task / ksplit, ks = task % ksplit;
                 const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
                     }
                     tc::mbar_expect_tx(&hd->full[s], FP8X ? raw_bytes + S * b_piece : stage_bytes);
                     uint8_t* st = tiles + (size_t)s * stage_bytes;
-                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK, t * 128);
+                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK, xr0 + t * 128);
 #pragma unroll
                     for (int p = 0; p < S; ++p)
                         tc::tma_load_2d(st + raw_bytes + a_bytes + p * b_piece, &tmV, &hd->full[s], k * kBK,
@@ -331,7 +333,8 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
 template <int S, bool FP8X>
 __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
     xty_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
-                  int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
+                  int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status,
+                  const int64_t* __restrict__ row0) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     constexpr uint32_t raw_bytes = FP8X ? 64u * 128u : 0u;
@@ -349,6 +352,7 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            const int xr0 = row0 ? (int)*row0 : 0;     // device-side first row of X (graph-replayed steps)
             for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
                 const int s = task % Dt, g = task / Dt;
                 const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
@@ -361,8 +365,8 @@ __global__ void __launch_bounds__(FP8X ? kThreadsFp8 : kThreads, 1)
                     }
                     tc::mbar_expect_tx(&hd->full[st_i], FP8X ? raw_bytes + S * b_piece : stage_bytes);
                     uint8_t* st = tiles + (size_t)st_i * stage_bytes;
-                    tc::tma_load_2d(st, &tmX, &hd->full[st_i], s * 128, k * kBK);
-                    if (!FP8X) tc::tma_load_2d(st + 8192, &tmX, &hd->full[st_i], s * 128 + 64, k * kBK);
+                    tc::tma_load_2d(st, &tmX, &hd->full[st_i], s * 128, xr0 + k * kBK);
+                    if (!FP8X) tc::tma_load_2d(st + 8192, &tmX, &hd->full[st_i], s * 128 + 64, xr0 + k * kBK);
 #pragma unroll
                     for (int p = 0; p < S; ++p)
                         tc::tma_load_2d(st + raw_bytes + a_bytes + p * b_piece, &tmY, &hd->full[st_i], k * kBK,
@@ -1316,7 +1320,7 @@ __device__ __forceinline__ void mma_3xtf32_stage(uint32_t d_tmem, uint32_t a_hi,
 __global__ void __launch_bounds__(kF32Threads, 1)
     xv_f32_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int ntiles, int nk,
                   int m_pad, int stages, float* __restrict__ Yt, int64_t ldy, int ksplit, float* __restrict__ Ypart,
-                  int* status) {
+                  int* status, const int64_t* __restrict__ row0) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t a_bytes = 128u * 128u;
@@ -1333,6 +1337,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            const int xr0 = row0 ? (int)*row0 : 0;     // device-side first row of X (graph-replayed steps)
             for (int task = blockIdx.x; task < ntiles * ksplit && ok; task += gridDim.x) {
                 const int t = task / ksplit, ks = task % ksplit;
                 const int k0 = (int)((int64_t)ks * nk / ksplit), k1 = (int)((int64_t)(ks + 1) * nk / ksplit);
@@ -1345,7 +1350,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                     }
                     tc::mbar_expect_tx(&hd->full[s], a_bytes + 2u * b_piece);
                     uint8_t* st = tiles + (size_t)s * stage_bytes;
-                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK32, t * 128);
+                    tc::tma_load_2d(st, &tmX, &hd->full[s], k * kBK32, xr0 + t * 128);
                     tc::tma_load_2d(st + 2 * a_bytes, &tmV, &hd->full[s], k * kBK32, 0);
                     tc::tma_load_2d(st + 2 * a_bytes + b_piece, &tmV, &hd->full[s], k * kBK32, m_pad);
                 }
@@ -1457,7 +1462,8 @@ __global__ void __launch_bounds__(kF32Threads, 1)
 // Z = X^T Y for FP32 X.  Stage: [raw X 4 x (32 x 32) 16 KB][A head 16 KB][A residual 16 KB][Y head][Y residual].
 __global__ void __launch_bounds__(kF32Threads, 1)
     xty_f32_kernel(const __grid_constant__ CUtensorMap tmXr, const __grid_constant__ CUtensorMap tmY, int Dt, int Sg,
-                   int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status) {
+                   int kst, int flush, int m_pad, int stages, float* __restrict__ Zacc, int* status,
+                   const int64_t* __restrict__ row0) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* tiles = align1024(smem_raw);
     const uint32_t a_bytes = 128u * 128u;
@@ -1475,6 +1481,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
+            const int xr0 = row0 ? (int)*row0 : 0;     // device-side first row of X (graph-replayed steps)
             for (int task = blockIdx.x; task < ntask && ok; task += gridDim.x) {
                 const int s = task % Dt, g = task / Dt;
                 const int k0 = (int)((int64_t)g * kst / Sg), k1 = (int)((int64_t)(g + 1) * kst / Sg);
@@ -1489,7 +1496,7 @@ __global__ void __launch_bounds__(kF32Threads, 1)
                     uint8_t* st = tiles + (size_t)si * stage_bytes;
 #pragma unroll
                     for (int bx = 0; bx < 4; ++bx)
-                        tc::tma_load_2d(st + bx * 4096, &tmXr, &hd->full[si], s * 128 + bx * 32, k * kBK32);
+                        tc::tma_load_2d(st + bx * 4096, &tmXr, &hd->full[si], s * 128 + bx * 32, xr0 + k * kBK32);
                     tc::tma_load_2d(st + 3 * a_bytes, &tmY, &hd->full[si], k * kBK32, 0);
                     tc::tma_load_2d(st + 3 * a_bytes + b_piece, &tmY, &hd->full[si], k * kBK32, m_pad);
                 }
@@ -2046,10 +2053,12 @@ struct PassShape {
     int m_pad, Dt, ntiles, nk;
 };
 
+// row0_dev (device, may be NULL): the batch's first row, read by the kernels;
+// the X descriptors then cover all n rows and r0 only fixes the batch size.
 template <int S, bool FP8X = false>
 cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, const TcPassScratch& sc,
                          PassShape& ps, CUtensorMap& tmXa, CUtensorMap& tmXb, CUtensorMap& tmV, CUtensorMap& tmY,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int64_t* row0_dev = nullptr) {
     ps.d = x.d;
     ps.rows = r1 - r0;
     ps.m_pad = m_pad_of(m);
@@ -2068,13 +2077,14 @@ cudaError_t prepare_pass(const XView& x, const float* V, int m, int64_t r0, int6
         split_v_kernel<S><<<blocks, 256, 0, st>>>(V, ps.d, m, ps.m_pad, ps.ldv, Vp);
     }
     const int esz = FP8X ? 1 : 2;
-    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * esz;
-    const bool xmaps = FP8X ? encode_2d(&tmXa, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, ps.rows, x.ld, 64, 128,
+    const void* xbase = static_cast<const char*>(x.ptr) + (row0_dev ? 0 : r0) * x.ld * esz;
+    const uint64_t xrows = row0_dev ? (uint64_t)x.n : (uint64_t)ps.rows;
+    const bool xmaps = FP8X ? encode_2d(&tmXa, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, xrows, x.ld, 64, 128,
                                         CU_TENSOR_MAP_SWIZZLE_NONE) &&
-                                  encode_2d(&tmXb, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, ps.rows, x.ld, 128, 64,
+                                  encode_2d(&tmXb, CU_TENSOR_MAP_DATA_TYPE_UINT8, xbase, ps.d, xrows, x.ld, 128, 64,
                                             CU_TENSOR_MAP_SWIZZLE_NONE)
-                            : encode_bf16_2d(&tmXa, xbase, ps.d, ps.rows, x.ld * 2, 64, 128) &&
-                                  encode_bf16_2d(&tmXb, xbase, ps.d, ps.rows, x.ld * 2, 64, 64);
+                            : encode_bf16_2d(&tmXa, xbase, ps.d, xrows, x.ld * 2, 64, 128) &&
+                                  encode_bf16_2d(&tmXb, xbase, ps.d, xrows, x.ld * 2, 64, 64);
     if (!xmaps ||
         !encode_bf16_2d(&tmV, Vp, ps.d, (uint64_t)S * ps.m_pad, ps.ldv * 2, 64, ps.m_pad) ||
         !encode_bf16_2d(&tmY, Yt, ps.ldy, (uint64_t)S * ps.m_pad, ps.ldy * 2, 64, ps.m_pad))
@@ -2117,10 +2127,11 @@ cudaError_t launch_zreduce(const float* Zacc, int Sg, int Dt, int64_t d, int m, 
 // Two GEMM kernels: Y = X V, then Z = X^T Y (X is read twice).
 template <int S, bool FP8X = false>
 cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
-                     const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+                     const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st,
+                     const int64_t* row0_dev = nullptr) {
     PassShape ps;
     CUtensorMap tmXa, tmXb, tmV, tmY;
-    cudaError_t e = prepare_pass<S, FP8X>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st);
+    cudaError_t e = prepare_pass<S, FP8X>(x, V, m, r0, r1, sc, ps, tmXa, tmXb, tmV, tmY, st, row0_dev);
     constexpr int threads = FP8X ? kThreadsFp8 : kThreads;
     constexpr uint32_t raw_xv = FP8X ? 128u * 64u : 0u, raw_xty = FP8X ? 64u * 128u : 0u;
     if (e != cudaSuccess) return e;
@@ -2147,7 +2158,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         note_launch();
         const float* scales = FP8X ? x.scales + r0 : nullptr;
         xv_tc_kernel<S, FP8X><<<grid, threads, smem, st>>>(tmXa, tmV, ps.ntiles, ps.nk, ps.m_pad, stages, Yt,
-                                                            ps.ldy, ksplit, Ypart, scales, ps.rows, status);
+                                                            ps.ldy, ksplit, Ypart, scales, ps.rows, status, row0_dev);
         if (ksplit > 1) {
             const int64_t total = ps.ldy * ps.m_pad;
             int blocks = (int)((total + 255) / 256);
@@ -2169,7 +2180,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
         xty_tc_kernel<S, FP8X><<<grid, threads, smem, st>>>(tmXb, tmY, ps.Dt, Sg, kst, flush, ps.m_pad, stages,
-                                                              Zacc, status);
+                                                              Zacc, status, row0_dev);
     }
     return launch_zreduce(Zacc, Sg, ps.Dt, ps.d, m, ps.m_pad, Z, st);
 }
@@ -2301,7 +2312,8 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
 
 // FP32 data: 3xTF32 passes (two kernels; X read twice).
 cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, int flush,
-                         const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st) {
+                         const TcPassScratch& sc, int* status, int num_sms, cudaStream_t st,
+                         const int64_t* row0_dev = nullptr) {
     const int64_t d = x.d, rows = r1 - r0;
     const int m_pad = m_pad_of(m);
     const int64_t ldv4 = round_up(d, 4);
@@ -2318,11 +2330,13 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         note_launch();
         split_v_f32_kernel<<<blocks, 256, 0, st>>>(V, d, m, m_pad, ldv4, Vp);
     }
-    const void* xbase = static_cast<const char*>(x.ptr) + r0 * x.ld * 4;
+    // row0_dev (device, may be NULL): the batch's first row, read by the kernels
+    const void* xbase = static_cast<const char*>(x.ptr) + (row0_dev ? 0 : r0) * x.ld * 4;
+    const uint64_t xrows = row0_dev ? (uint64_t)x.n : (uint64_t)rows;
     CUtensorMap tmX, tmXr, tmV, tmY;
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    if (!encode_2d(&tmX, f32, xbase, d, rows, x.ld * 4, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !encode_2d(&tmXr, f32, xbase, d, rows, x.ld * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE) ||
+    if (!encode_2d(&tmX, f32, xbase, d, xrows, x.ld * 4, 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !encode_2d(&tmXr, f32, xbase, d, xrows, x.ld * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_NONE) ||
         !encode_2d(&tmV, f32, Vp, d, 2 * (uint64_t)m_pad, ldv4 * 4, 32, m_pad, CU_TENSOR_MAP_SWIZZLE_128B) ||
         !encode_2d(&tmY, f32, Yt, ldy, 2 * (uint64_t)m_pad, ldy * 4, 32, m_pad, CU_TENSOR_MAP_SWIZZLE_128B))
         return cudaErrorInvalidValue;
@@ -2348,7 +2362,7 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         float* Ypart = static_cast<float*>(sc.zacc);
         note_launch();
         xv_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages, Yt, ldy, ksplit, Ypart,
-                                                       status);
+                                                       status, row0_dev);
         if (ksplit > 1) {
             const int64_t total = ldy * m_pad;
             int blocks = (int)((total + 255) / 256);
@@ -2370,7 +2384,8 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         const int ntask = Dt * Sg;
         const int grid = ntask < num_sms ? ntask : num_sms;
         note_launch();
-        xty_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmXr, tmY, Dt, Sg, kst, flush, m_pad, stages, Zacc, status);
+        xty_f32_kernel<<<grid, kF32Threads, smem, st>>>(tmXr, tmY, Dt, Sg, kst, flush, m_pad, stages, Zacc, status,
+                                                        row0_dev);
     }
     return launch_zreduce(Zacc, Sg, Dt, d, m, m_pad, Z, st);
 }
@@ -2404,8 +2419,16 @@ bool tc_pass_supported(const XView& x, int m) {
 }
 
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
-                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st) {
+                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st,
+                     const int64_t* row0_dev) {
     if (r1 <= r0) return cudaErrorInvalidValue;
+    if (row0_dev) {
+        // device-side first row: whole 128-row tiles of FP32 or BF16 data, two-kernel forms
+        if ((r1 - r0) % 128 != 0 || x.dtype == PPCA_FP8_E4M3) return cudaErrorInvalidValue;
+        if (x.dtype == PPCA_F32) return run_pass_f32(x, V, m, r0, r1, Z, 64, s, status, num_sms, st, row0_dev);
+        if (prec == PPCA_PREC_ACCURATE) return run_pass<3>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st, row0_dev);
+        return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st, row0_dev);
+    }
     if (x.dtype == PPCA_F32) return run_pass_f32(x, V, m, r0, r1, Z, 64, s, status, num_sms, st);   // FAST only
     if (x.dtype == PPCA_FP8_E4M3) {
         if (prec == PPCA_PREC_ACCURATE) return run_pass<3, true>(x, V, m, r0, r1, Z, 32, s, status, num_sms, st);
@@ -2422,6 +2445,14 @@ cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t 
     const bool fuse = sched.fused != 0 && can_fuse;
     if (fuse) return run_fused(x, V, m, r0, r1, Z, s, sched, status, num_sms, st);
     return run_pass<1>(x, V, m, r0, r1, Z, 256, s, status, num_sms, st);
+}
+
+bool xpass_tc_row0_same(const XView& x, int64_t rows, ppca_precision prec, const TcSchedule& sched, int num_sms) {
+    if (rows % 128 != 0 || x.dtype == PPCA_FP8_E4M3) return false;
+    if (x.dtype == PPCA_F32 || prec == PPCA_PREC_ACCURATE) return true;
+    const int Dt = (int)((x.d + 127) / 128);
+    const bool can_fuse = (Dt + 1) / 2 <= num_sms && rows >= 128 * 4;
+    return !(sched.fused != 0 && can_fuse);
 }
 
 bool grouped_encode_maps(const GInst& g, GMaps& out) {

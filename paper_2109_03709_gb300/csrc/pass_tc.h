@@ -50,7 +50,14 @@ cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, cons
 // device (ns = 0: the default 2 s), one setter per translation unit.
 cudaError_t pass_tc_set_wait_limit(uint64_t ns);
 cudaError_t pass_gram_set_wait_limit(uint64_t ns);
+// row0_dev (device, may be NULL): the kernels read the first row of the rows
+// [r0, r1) there instead of taking r0 (r1 - r0 a multiple of 128; FP32 or
+// BF16 data; the two-kernel forms), so a captured pass can serve any batch.
 cudaError_t xpass_tc(const XView& x, const float* V, int m, int64_t r0, int64_t r1, float* Z, ppca_precision prec,
-                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st);
+                     const TcPassScratch& s, const TcSchedule& sched, int* status, int num_sms, cudaStream_t st,
+                     const int64_t* row0_dev = nullptr);
+// True when the device-first-row form of a pass over `rows` rows runs the same
+// kernels (and so gives the same bits) as the ordinary form.
+bool xpass_tc_row0_same(const XView& x, int64_t rows, ppca_precision prec, const TcSchedule& sched, int num_sms);
 
 }  // namespace ppca

@@ -1042,7 +1042,8 @@ __global__ void sign_kernel(float* __restrict__ E, int64_t d, const double* __re
 // (row, column), kOjaRows rows of W and S (as FP32) staged in shared memory per CTA.
 constexpr int kOjaRows = 8;
 __global__ void oja_update_kernel(float* __restrict__ W, const float* __restrict__ Z, const double* __restrict__ S,
-                                  int64_t d, int m, float c) {
+                                  int64_t d, int m, float c_host, const float* __restrict__ c_dev) {
+    const float c = c_dev ? *c_dev : c_host;
     extern __shared__ float sm[];
     float* Ss = sm;                        // m x m (row-major)
     float* w = sm + m * m;                 // kOjaRows x m, the old rows of W
@@ -1063,6 +1064,18 @@ __global__ void oja_update_kernel(float* __restrict__ W, const float* __restrict
         W[(int64_t)j * d + r] = wr[j] + c * (Z[(int64_t)j * d + r] - acc);
     }
 }
+
+// Step state of graph-replayed minibatch steps: step t's batch starts at row
+// (t mod per_epoch) b, and Oja's coefficient is lr / (t + lr_offset) / b, both
+// computed here in the same double arithmetic as the host's; then t advances.
+__global__ void primer_step_kernel(PrimerStep* ps, int64_t per_epoch, int64_t b, double lr, double lr_offset) {
+    const int64_t t = ps->t;
+    ps->row0 = (t % per_epoch) * b;
+    ps->c = (float)(lr / ((double)t + lr_offset) / (double)b);
+    ps->t = t + 1;
+}
+
+__global__ void primer_set_kernel(PrimerStep* ps, int64_t t) { ps->t = t; }
 
 // ------------------------------------------------------------------ EigenGame
 
@@ -1724,12 +1737,26 @@ cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, c
     return cudaGetLastError();
 }
 
-cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c, cudaStream_t st) {
+cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c, cudaStream_t st,
+                       const float* c_dev) {
     const size_t smem = ((size_t)m * m + (size_t)kOjaRows * m) * sizeof(float);
     cudaError_t e = allow_smem(oja_update_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    oja_update_kernel<<<ceil_div_i(d, kOjaRows), 256, smem, st>>>(W, Z, S, d, m, (float)c);
+    oja_update_kernel<<<ceil_div_i(d, kOjaRows), 256, smem, st>>>(W, Z, S, d, m, (float)c, c_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t primer_step_begin(PrimerStep* ps, int64_t per_epoch, int64_t b, double lr, double lr_offset,
+                              cudaStream_t st) {
+    note_launch();
+    primer_step_kernel<<<1, 1, 0, st>>>(ps, per_epoch, b, lr, lr_offset);
+    return cudaGetLastError();
+}
+
+cudaError_t primer_step_set(PrimerStep* ps, int64_t t, cudaStream_t st) {
+    note_launch();
+    primer_set_kernel<<<1, 1, 0, st>>>(ps, t);
     return cudaGetLastError();
 }
 
