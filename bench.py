@@ -257,7 +257,7 @@ def measure_rows(peaks):
     ms = _events_ms(lambda: P.ppca_prime(h, P.PPCA_POWER, m, 1, None, V0=V0), 5, stream)
     rows["power_iteration_fp32_100000x1024_m64"] = {"ms": round(ms, 4), "note": "orth(V0) + one pass + CholeskyQR2"}
     oja = P.ppca_prime_params_default(P.PPCA_OJA)
-    steps = 50
+    steps = 200                  # one ppca_prime each: orth(V0), then the steps (graph-replayed blocks of 16)
     ms = _events_ms(lambda: P.ppca_prime(h, P.PPCA_OJA, m, steps, oja, V0=V0), 2, stream)
     rows["oja_step_fp32_b256"] = {"us_per_step": round(ms * 1e3 / steps, 2), "batch": 256}
     eg = P.ppca_prime_params_default(P.PPCA_EIGENGAME)
