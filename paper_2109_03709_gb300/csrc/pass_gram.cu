@@ -7,24 +7,28 @@
 //
 //   ygen   Y = X Q    persistent over 128-row tiles of X.  Q (FP32) is split
 //                     into NV BF16 pieces; FP32 X is split in shared memory
-//                     into NX BF16 pieces by four transform warps (BF16 X is
+//                     into NX BF16 pieces by eight transform warps (BF16 X is
 //                     one exact piece).  Of the piece products x_a q_b those
 //                     with a + b < max(NX, NV) are kept; the dropped ones are
 //                     below 2^-24 of the result.
 //   gram   G = Y^T Y  from Y's three BF16 pieces, products y_a^T y_b with
-//                     a + b <= 2, one double-float partial per CTA.
+//                     a + b <= 2, one partial per CTA (FP32 pairs, second 0).
 //   reduce G = sum of the partials in FP64, symmetrised.
 //
 // Accumulation.  An FP32 tensor-core accumulator that takes many MMAs in a row
 // drifts: on sm_103a a relative error of roughly 2e-8 per accumulating MMA was
-// measured, systematic rather than random, so it grows linearly with K.  Both
-// kernels therefore empty the accumulator every `flush` K-stages (64 wide) into
-// a double-float running sum kept in TMEM beside it (columns [2 m_pad, 4 m_pad)),
-// which caps the drift at the MMAs of one flush group.
+// measured, systematic rather than random, so it grows linearly with K, relative
+// to the accumulator's own size.  In split precision both kernels therefore
+// keep the product of the two leading pieces in an accumulator of its own,
+// emptied every `flush` K-stages (64 wide) into an FP32 running sum in TMEM
+// (which caps its drift at the MMAs of one flush group), and the products of
+// the smaller pieces, at most 2^-8 of the result, in a second accumulator that
+// is read once: its drift is relative to that smaller sum.  The FAST forms
+// (one or three products) fold, if at all, into a double-float running sum.
 //
 // Warp roles: warp 0 issues TMA, warp 1 owns TMEM and issues the MMAs (one
 // thread), warps 2-5 are the epilogue (TMEM lane quarter = warp % 4), warps
-// 6-9 (FP32 X only) make the X pieces.  Every wait is bounded (2 s); on a
+// 6-13 (FP32 X only) make the X pieces.  Every wait is bounded (2 s); on a
 // timeout the kernel records kDevWaitTimeout, drains its copies, frees TMEM
 // and returns.
 #include <cudaTypedefs.h>
@@ -424,11 +428,12 @@ __global__ void __launch_bounds__(F32X ? kGThreadsF32 : kGThreadsBf16, 1)
                         float x0 = v[i][e], x1 = v[i][e + 1];
 #pragma unroll
                         for (int p = 0; p < NX; ++p) {
-                            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-                            wd[p][e / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
-                                           ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                            x0 = __fsub_rn(x0, __bfloat162float(h0));
-                            x1 = __fsub_rn(x1, __bfloat162float(h1));
+                            // both values rounded to nearest by one paired conversion (x0 low)
+                            const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+                            wd[p][e / 2] = *reinterpret_cast<const uint32_t*>(&h);
+                            const float2 hf = __bfloat1622float2(h);
+                            x0 = __fsub_rn(x0, hf.x);
+                            x1 = __fsub_rn(x1, hf.y);
                         }
                     }
                     const uint32_t off = (uint32_t)r * 128u + (uint32_t)((c ^ (r & 7)) << 4);
@@ -482,7 +487,11 @@ struct GramGroup {
 
 // Stage: three 16 KB slots (pieces y1, y2, y3 of 64 rows of Y, as m_pad rows of
 // Y^T x 128 B); slot rows m_pad .. 127 stay zero so the M = 128 MMA reads
-// zeros there.  Every CTA has at least one K-stage.
+// zeros there.  Every CTA has at least one K-stage.  Accumulation as in
+// ygen's split precision: y1^T y1 in accumulator b (TMEM column b m_pad),
+// emptied every `flush` K-stages into an FP32 running sum (column 2 m_pad);
+// the five smaller products in one accumulator (column 3 m_pad) for the CTA's
+// whole K range.
 template <class Work>
 __global__ void __launch_bounds__(kGThreadsBf16, 1)
     gram_y_kernel(const __grid_constant__ Work work, int flush, int stages, int* status) {
@@ -529,7 +538,8 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16(128, m_pad, false, false);
-            uint32_t it = 0;
+            const uint32_t s_tmem = tmem + 3u * (uint32_t)m_pad;
+            uint32_t it = 0, acc_s = 0;
             bool ok = true;
             for (int g = 0; g < ngroups && ok; ++g) {
                 const uint32_t b = (uint32_t)g & 1u, tph = ((uint32_t)g >> 1) & 1u;
@@ -559,8 +569,13 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
                                 if (pa + pb > 2) continue;
                                 const uint64_t ad = tc::smem_desc_sw128(a0 + pa * kPiece + kk * 32, 16, 1024);
                                 const uint64_t bd = tc::smem_desc_sw128(a0 + pb * kPiece + kk * 32, 16, 1024);
-                                tc::mma_f16(d_tmem, ad, bd, idesc, acc);
-                                acc = 1;
+                                if ((pa | pb) != 0) {
+                                    tc::mma_f16(s_tmem, ad, bd, idesc, acc_s);
+                                    acc_s = 1;
+                                } else {
+                                    tc::mma_f16(d_tmem, ad, bd, idesc, acc);
+                                    acc = 1;
+                                }
                             }
                         }
                     }
@@ -584,13 +599,25 @@ __global__ void __launch_bounds__(kGThreadsBf16, 1)
             const bool last = g == ngroups - 1;
             if (live) {
                 for (int c0 = 0; c0 < m_pad; c0 += 32) {
-                    uint32_t a[32], rh[32], rl[32];
-                    fold_chunk(lane_base, b * (uint32_t)m_pad + (uint32_t)c0, 2u * (uint32_t)m_pad + (uint32_t)c0,
-                               (uint32_t)m_pad, g, !last, a, rh, rl);
-                    if (last) {
+                    const uint32_t a_col = b * (uint32_t)m_pad + (uint32_t)c0, r_col = 2u * (uint32_t)m_pad + (uint32_t)c0;
+                    uint32_t a[32], r[32];
+                    tc::tmem_ld32(lane_base + a_col, a);
+                    if (g > 0) tc::tmem_ld32(lane_base + r_col, r);
+                    tc::tmem_ld_wait();
+                    if (g > 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) a[j] = __float_as_uint(__uint_as_float(r[j]) + __uint_as_float(a[j]));
+                    }
+                    if (!last) {
+                        tc::tmem_st32(lane_base + r_col, a);
+                        tc::tmem_st_wait();
+                    } else {
+                        tc::tmem_ld32(lane_base + 3u * (uint32_t)m_pad + (uint32_t)c0, r);
+                        tc::tmem_ld_wait();
                         float2* dst = gw.part + (int64_t)i * m_pad + c0;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) dst[j] = make_float2(__uint_as_float(rh[j]), __uint_as_float(rl[j]));
+                        for (int j = 0; j < 32; ++j)
+                            dst[j] = make_float2(__uint_as_float(a[j]) + __uint_as_float(r[j]), 0.f);
                     }
                 }
             }
@@ -668,7 +695,7 @@ cudaError_t launch_gram_y(const Work& work, int grid, int* status, cudaStream_t 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    kern<<<grid, kGThreadsBf16, smem, st>>>(work, 1, gstages, status);
+    kern<<<grid, kGThreadsBf16, smem, st>>>(work, 12, gstages, status);
     return cudaGetLastError();
 }
 
@@ -747,9 +774,9 @@ cudaError_t projected_gram_tc_blocks(const XView& x, const float* Q, int m, cons
 
 // G = Z^T Z for a d x m column-major FP32 Z (CholeskyQR's Gram matrix) on the
 // tensor cores: Z is split into three BF16 pieces (the layout of the projected
-// Gram's Y pieces, K = d), G = sum over the six piece products with a + b <= 2,
-// flushed into double-float partials every K-stage, summed and symmetrised in
-// FP64; Gf receives the FP32 rounding of G.
+// Gram's Y pieces, K = d), G = sum over the six piece products with a + b <= 2
+// (accumulated as in gram_y_kernel), one partial per CTA, summed and
+// symmetrised in FP64; Gf receives the FP32 rounding of G.
 cudaError_t gram_tc(const float* Z, int64_t d, int m, double* G, float* Gf, const TcPassScratch& sc, int* status,
                     int num_sms, cudaStream_t st) {
     if (m < 1 || m > 128 || d < 1) return cudaErrorInvalidValue;

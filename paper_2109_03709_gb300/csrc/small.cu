@@ -20,6 +20,7 @@
 #include <cuda_fp8.h>
 #include <math.h>
 
+#include <algorithm>
 #include <mutex>
 
 namespace ppca {
@@ -1945,9 +1946,15 @@ cudaError_t grouped_copy_vout(const GInst* gi, GTable dm_blocks, cudaStream_t st
     return cudaGetLastError();
 }
 
+// A grouped launch already spreads hundreds of instances over the GPU: row
+// slices of 256 rows (not the single problem's 32, which fill the GPU with one
+// narrow basis) keep the block count, and its scheduling cost, down.
+constexpr int kGroupedGramRows = 256;
+
 GShape grouped_shape(int64_t d, int m) {
     GShape s;
-    s.gram_P = gram_nslices(d, m);
+    s.gram_P = (int)std::min<int64_t>(gram_nslices(d, m), std::max<int64_t>(1, (d + kGroupedGramRows - 1) /
+                                                                                  kGroupedGramRows));
     s.gram_T = (m + kGramTile - 1) / kGramTile;
     s.gram_L = gram_reduce_lanes(s.gram_P);
     s.gram_blocks = s.gram_T * s.gram_T * s.gram_P;
