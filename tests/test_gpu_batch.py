@@ -199,3 +199,45 @@ def test_lockstep_priming_against_slots_and_oracle(cuda_device):
             assert oracle.principal_angles(Va, Vo).max() <= 3e-2, i
         # the slot path from the same start (the seeded instance: the same Philox draw)
         assert oracle.principal_angles(Va, Vc).max() <= 3e-2, i
+
+
+def test_lockstep_full_size_subset_matches_oracle(cuda_device):
+    """16 instances of the 512-instance workload at full size (the first 16 that
+    its generator draws: n up to 185952, d from 64 to 2048), FP32 data primed in
+    lockstep on the BF16 rounding with the workload's T = 10: each instance's E
+    and lambda against the oracle's pPCA step (Algorithm 1, steps 2-5, FP64) on
+    the instance's own primed basis V_out (eigenvalues 1e-5 relative, angles
+    1e-4 rad); for four of them also the primed subspace against the oracle's
+    FP64 block power on the BF16-rounded data (3e-2 rad, as above); and the run
+    takes the same 40 + 13T launches whatever the instance count."""
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    cfg = synth.CONFIGS["batch512_fp32"]
+    T = cfg.primers["power"]["T"]
+    shapes = synth.batch_instances(512, cfg.seed)[:16]
+    inst = []
+    for s in shapes:
+        n, d, k, m = s["n"], s["d"], s["k"], s["m"]
+        X = synth.instance_data_torch(n, d, s["rho"] ** np.arange(1, d + 1), s["seed"], "cuda", torch.float32)
+        V0 = torch.from_numpy(np.ascontiguousarray(synth.initial_basis(d, m, s["seed"]).T, dtype=np.float32)).cuda()
+        inst.append({"X": X, "k": k, "m": m, "T": T, "V0": V0,
+                     "E": torch.empty((k, d), dtype=torch.float32, device="cuda"),
+                     "lam": torch.empty(k, dtype=torch.float64, device="cuda"),
+                     "V_out": torch.empty((m, d), dtype=torch.float32, device="cuda")})
+    b = P.ppca_batch_create(inst, slots=4)
+    P.ppca_batch_set_priming(b, P.PPCA_BF16)
+    P.ppca_batch_run(b)
+    P.ppca_batch_sync(b)
+    assert P.ppca_batch_lockstep(b)
+    assert P.ppca_batch_kernel_count(b) <= 40 + 13 * T
+    for i, ins in enumerate(inst):
+        Xs = ins["X"].double().cpu().numpy()
+        Vg = host_basis(ins["V_out"])
+        Eo, lo = oracle.ppca_finalize(Xs, Vg, ins["k"])
+        np.testing.assert_allclose(ins["lam"].cpu().numpy(), lo, rtol=1e-5, err_msg=f"instance {i}")
+        assert oracle.angles(host_basis(ins["E"]), Eo).max() <= 1e-4, i
+        if i < 4:
+            Vo = oracle.power_prime(oracle.bf16_round_rne(Xs), host_basis(ins["V0"]), T)
+            assert oracle.principal_angles(Vg, Vo).max() <= 3e-2, i
+        del Xs
