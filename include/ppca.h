@@ -249,7 +249,9 @@ PPCA_API ppca_status ppca_variance_captured(ppca_handle *h, const float *E, int3
                                             ppca_precision precision);
 
 /* Device copy of the current primed basis V (d x m column-major FP32): the
- * output of Algorithm 1, step 1. */
+ * output of Algorithm 1, step 1.  Only span(V) passes to the pPCA step; after
+ * block power steps V's columns are orthonormal to about 1e-4 (the second
+ * CholeskyQR pass of a step runs only when the first leaves more). */
 PPCA_API ppca_status ppca_get_basis(const ppca_handle *h, float *V_out);
 
 /* Wait for the handle's stream; return the first device-side error, if any,

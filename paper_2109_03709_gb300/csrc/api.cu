@@ -80,7 +80,7 @@ struct ppca_handle {
     size_t ws_bytes = 0;
     int ws_m = 0;
     int* status = nullptr;    // device status word (own 256-byte allocation; status[1] is the
-                              // CholeskyQR fallback flag)
+                              // CholeskyQR fallback flag, status[2] the need for a second pass)
 
     float* V = nullptr;       // primed basis d x m
     float* Z = nullptr;       // pass output d x m
@@ -316,7 +316,13 @@ ppca_status global_rows(ppca_handle* h, int64_t local, int64_t* out) {
 
 int64_t rows_total(const ppca_handle* h) { return h->ar_fn ? h->n_total : h->x.n; }
 
-ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
+// span_only: the caller needs span(Q) and a well-conditioned Q, not Q^T Q = I to
+// working precision (a block power step: the next product and CholeskyQR see
+// only the span).  Then, when the first pass's FP32 factor was accepted with a
+// conditioning bound of at most 2^10 (Q^T Q within ~1e-4 of I), the second
+// pass's Gram and factor are skipped on the device (R^-1 = I, Q = the first
+// pass's result).
+ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m, bool span_only = false) {
     const int64_t d = h->x.d;
     const float* src = V;
     // Tall bases (d >= 16384): Gram matrices on the tensor cores (three BF16
@@ -325,14 +331,18 @@ ppca_status run_orth(ppca_handle* h, const float* V, float* Q, int m) {
     // the rejection flag).  Shorter bases: the CUDA-core double-float Gram (the
     // two break even near d = 4096; at 262144 x 64 the tensor cores halve CholeskyQR2).
     const bool tc_gram = d >= 16384 && encode_fn() != nullptr && h->sched.engine != 2;
+    const bool gate = span_only && !tc_gram;
+    int* need_second = h->status + 2;            // device flag of the gated second pass
     for (int rep = 0; rep < 2; ++rep) {
         float* dst = rep == 0 ? h->T : Q;
+        const int* run_if = gate && rep == 1 ? need_second : nullptr;
         if (tc_gram)
             CUDA_TRY(gram_tc(src, d, m, h->G, h->Gf, h->tc, h->status, h->num_sms, h->stream));
         else
-            CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream, h->Gf));
+            CUDA_TRY(gram_df(src, src, d, m, h->G, h->gram_part, h->stream, h->Gf, run_if));
         CUDA_TRY(cholesky_adaptive(h->G, h->Gf, m, h->Rf, rep == 0, h->status + 1, h->status, h->stream,
-                                   tc_gram ? src : nullptr, d, h->gram_part));
+                                   tc_gram ? src : nullptr, d, h->gram_part,
+                                   gate && rep == 0 ? need_second : nullptr, run_if));
         CUDA_TRY(apply_rinv(src, h->Rf, d, m, dst, h->stream));
         src = dst;
     }
@@ -534,7 +544,7 @@ ppca_status run_steps(ppca_handle* h, int64_t T) {
         case PPCA_POWER:
             PPCA_TRY(run_xpass(h, h->x, h->V, m, 0, n, h->Z, prime_prec(h)));
             PPCA_TRY(allreduce(h, h->Z, d * m, 4));                               // Z over all ranks' rows
-            PPCA_TRY(run_orth(h, h->Z, h->V, m));
+            PPCA_TRY(run_orth(h, h->Z, h->V, m, /*span_only=*/true));
             ++h->iters;
             break;
         default:

@@ -41,9 +41,13 @@ cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G,
 // Zdf: when G did not come from gram_df (tensor-core Gram), the d x m matrix
 // whose double-float Gram the fallback recomputes into G first (gated by *flag,
 // part as for gram_df); NULL otherwise.
+// next (may be NULL, first pass): set to 0 when the accepted FP32 factor's
+// conditioning bound is at most 2^10 (Q^T Q within ~1e-4 of I), else 1.
+// run_if (may be NULL, second pass): while *run_if == 0 the factor is skipped
+// and Rinv = I.
 cudaError_t cholesky_adaptive(double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
                               int* status, cudaStream_t st, const float* Zdf = nullptr, int64_t d = 0,
-                              float* part = nullptr);
+                              float* part = nullptr, int* next = nullptr, const int* run_if = nullptr);
 // Q = V R^-1 as a product with the triangular inverse; Q must not alias V.
 cudaError_t apply_rinv(const float* V, const float* Rinv, int64_t d, int m, float* Q, cudaStream_t st);
 

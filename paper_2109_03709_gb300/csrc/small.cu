@@ -296,6 +296,10 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
 constexpr int kCBThreads = 512;
 constexpr int kCB = 32;
 constexpr float kCholKappaMax = 65536.f;     // 2^16
+// An accepted first-pass factor whose bound is at most 2^10 leaves Q^T Q within
+// about 1e-4 of I: when only span(Q) matters (a block power step) the second
+// CholeskyQR pass is skipped (*next = 0).
+constexpr float kCholSkipMax = 1024.f;
 
 // C (m x m, upper part, row stride lda) = op(X) Y for upper-triangular X and Y
 // on 4 x 4 register tiles: TRANS_X: C = X^T Y (both read by rows); else C = X Y.
@@ -423,7 +427,8 @@ __device__ bool chol_series(float* A, float* W, const float* dsc, int m, int lda
 }
 
 __device__ __forceinline__ void chol_blocked_body(const float* __restrict__ Gf, int m, float* __restrict__ Rinv,
-                                                  int* fallback, int* status, int near_identity) {
+                                                  int* fallback, int* status, int near_identity,
+                                                  int* next = nullptr) {
     extern __shared__ __align__(16) float cbs[];
     const int lda = (m + 3) & ~3;           // shared-memory row stride: rows start 16-byte aligned
     float* A = cbs;                         // m x lda; upper triangle, rows of R' overwrite it panel by panel
@@ -668,6 +673,7 @@ __device__ __forceinline__ void chol_blocked_body(const float* __restrict__ Gf, 
             const bool reject = bad || !(rowsum_max * t <= kCholKappaMax);
             if (fallback) *fallback = reject ? 1 : 0;
             else if (bad) set_status(status, kDevCholeskyBreakdown);
+            if (next) *next = (reject || !(rowsum_max * t <= kCholSkipMax)) ? 1 : 0;
         }
     }
     for (int i = warp; i < m; i += nw) {
@@ -676,10 +682,17 @@ __device__ __forceinline__ void chol_blocked_body(const float* __restrict__ Gf, 
     }
 }
 
+// run_if (may be NULL): when *run_if == 0 the pass is skipped and Rinv = I, so
+// that the following Q = V Rinv is an exact copy.  next: see kCholSkipMax.
 __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_kernel(const float* __restrict__ Gf, int m,
                                                                    float* __restrict__ Rinv, int* fallback,
-                                                                   int* status, int near_identity) {
-    chol_blocked_body(Gf, m, Rinv, fallback, status, near_identity);
+                                                                   int* status, int near_identity,
+                                                                   const int* run_if, int* next) {
+    if (run_if && *run_if == 0) {
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) Rinv[e] = (e / m == e % m) ? 1.f : 0.f;
+        return;
+    }
+    chol_blocked_body(Gf, m, Rinv, fallback, status, near_identity, next);
 }
 
 // Q = V X with X = R^-1 upper triangular (row-major).  A block stages X and
@@ -1496,14 +1509,15 @@ cudaError_t gram_df(const float* A, const float* B, int64_t d, int m, double* G,
 }
 
 cudaError_t cholesky_adaptive(double* G, const float* Gf, int m, float* Rinv, bool may_fall_back, int* flag,
-                              int* status, cudaStream_t st, const float* Zdf, int64_t d, float* part) {
+                              int* status, cudaStream_t st, const float* Zdf, int64_t d, float* part, int* next,
+                              const int* run_if) {
     const size_t lda = (size_t)((m + 3) & ~3);
     const size_t smem = ((size_t)2 * m * lda + (size_t)((m + kCB - 1) / kCB) * kCB * kCB + m) * sizeof(float);
     cudaError_t e = allow_smem(chol_blocked_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
     chol_blocked_kernel<<<1, kCBThreads, smem, st>>>(Gf, m, Rinv, may_fall_back ? flag : nullptr, status,
-                                                      may_fall_back ? 0 : 1);
+                                                      may_fall_back ? 0 : 1, run_if, next);
     e = cudaGetLastError();
     if (e != cudaSuccess || !may_fall_back) return e;
     if (Zdf) {       // G came from the tensor cores: the fallback needs the double-float Gram
