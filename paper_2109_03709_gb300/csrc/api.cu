@@ -1398,7 +1398,7 @@ bool prepare_lockstep(ppca_batch* b) {
         o[i].Gf = take((size_t)m * m * 4);
         o[i].Rinv = take((size_t)m * m * 4);
         o[i].part = take(gram_part_floats(d, m) * 4);
-        o[i].flag = take(4);
+        o[i].flag = take(8);
         c_quant[i] = f32 ? (int)cdiv(n * (d / 8), 256) : 0;
         c_splitv[i] = (int)cdiv((int64_t)g.m_pad * g.ldv, 256);
         c_xv[i] = g.ntiles;
@@ -1456,6 +1456,7 @@ bool prepare_lockstep(ppca_batch* b) {
         g.Rinv = reinterpret_cast<float*>(base + o[i].Rinv);
         g.gram_part = reinterpret_cast<float*>(base + o[i].part);
         g.flag = reinterpret_cast<int*>(base + o[i].flag);
+        g.next = g.flag + 1;
         g.status = st;
         g.Q3 = reinterpret_cast<__nv_bfloat16*>(base + o[i].q3);
         g.Y3 = reinterpret_cast<__nv_bfloat16*>(base + o[i].y3);
@@ -1534,16 +1535,18 @@ bool prepare_lockstep(ppca_batch* b) {
     return true;
 }
 
-// CholeskyQR2 of every instance's src (V or Z) into dst (V or Z), through T (as run_orth).
-cudaError_t lockstep_orth(ppca_batch* b, int src, int dst) {
+// CholeskyQR2 of every instance's src (V or Z) into dst (V or Z), through T (as
+// run_orth; span_only: block power steps, each instance's second pass gated on
+// its first pass's conditioning bound).
+cudaError_t lockstep_orth(ppca_batch* b, int src, int dst, bool span_only = false) {
     const int count = (int)b->descs.size();
     cudaStream_t st = b->stream;
     cudaError_t e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, src, b->g_max_m, false, st);
-    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, false, st);
+    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, false, st, span_only);
     if (e == cudaSuccess) e = grouped_chol_fallback(b->g_inst, count, b->g_max_m, st);
     if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, src, kGT, b->g_max_m, st);
-    if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, false, st);
-    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st);
+    if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, span_only, st);
+    if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st, false, span_only);
     if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, dst, b->g_max_m, st);
     return e;
 }
@@ -1563,7 +1566,7 @@ ppca_status enqueue_lockstep(ppca_batch* b) {
     for (int t = 0; t < b->descs[0].T; ++t) {
         CUDA_TRY(grouped_split_v(b->g_inst, b->t_splitv, st));
         CUDA_TRY(grouped_xpass(b->g_inst, b->g_maps, b->t_xv, b->t_xty, b->t_dm, b->g_status, b->num_sms, st));
-        CUDA_TRY(lockstep_orth(b, kGZ, kGV));
+        CUDA_TRY(lockstep_orth(b, kGZ, kGV, /*span_only=*/true));
     }
     // steps 2-5 for every instance: Q = orth(V) (into Z), G = (X Q)^T (X Q) at
     // split precision on the data as given, the eigensolve, E = Q U[:, :k]

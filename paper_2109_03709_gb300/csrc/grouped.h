@@ -36,6 +36,7 @@ struct GInst {
     float* gram_part;         // gram_P x m x m x 2
     int gram_P, gram_T, gram_L;
     int* flag;                // CholeskyQR: the FP32 factor was rejected
+    int* next;                // CholeskyQR: a second pass is needed (gated block power steps)
     int* status;              // device status word of the batch
 
     // the pPCA step (Algorithm 1, steps 2-5), Q = orth(V) held in Z
@@ -99,9 +100,13 @@ __host__ __device__ inline float* garray(const GInst& g, int which) {
 }
 
 // ---- launchers (small.cu): CholeskyQR2 of every instance, src -> dst (V, Z or T)
+// gated: an instance's blocks do nothing while *next == 0 (its second pass is
+// skipped).  grouped_chol: first pass (near_identity false) sets *next when
+// span_only; second pass with gated writes R^-1 = I where *next == 0.
 cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_blocks, int src, int max_m,
                          bool gated, cudaStream_t st);
-cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st);
+cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st,
+                         bool span_only = false, bool gated = false);
 cudaError_t grouped_chol_fallback(const GInst* gi, int count, int max_m, cudaStream_t st);
 cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st);
 cudaError_t grouped_quantize_bf16(const float* const* X32, const int64_t* ld32, const GInst* gi, GTable blocks,

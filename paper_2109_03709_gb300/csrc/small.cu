@@ -1376,7 +1376,7 @@ cudaError_t allow_smem(K kernel, size_t bytes) {
 __global__ void gram_df_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int src, int gated) {
     const int i = group_find(tab, blockIdx.x);
     const GInst& g = gi[i];
-    if (gated && *g.flag == 0) return;                 // the FP32 factor was accepted
+    if (gated && *g.next == 0) return;                 // this instance's second pass is skipped
     const int local = blockIdx.x - tab.base[i], T = g.gram_T;
     const int ti = local % T, tj = (local / T) % T, p = local / (T * T);
     const float* A = garray(g, src);
@@ -1386,14 +1386,20 @@ __global__ void gram_df_grouped_kernel(const GInst* __restrict__ gi, GTable tab,
 __global__ void gram_reduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int gated) {
     const int i = group_find(tab, blockIdx.x);
     const GInst& g = gi[i];
-    if (gated && *g.flag == 0) return;
+    if (gated && *g.next == 0) return;
     gram_reduce_body(g.gram_part, g.gram_P, g.m, g.gram_L, true, g.G, g.Gf, blockIdx.x - tab.base[i]);
 }
 
 __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_grouped_kernel(const GInst* __restrict__ gi,
-                                                                           int near_identity) {
+                                                                           int near_identity, int span_only,
+                                                                           int gated) {
     const GInst& g = gi[blockIdx.x];
-    chol_blocked_body(g.Gf, g.m, g.Rinv, near_identity ? nullptr : g.flag, g.status, near_identity);
+    if (gated && *g.next == 0) {
+        for (int e = threadIdx.x; e < g.m * g.m; e += blockDim.x) g.Rinv[e] = (e / g.m == e % g.m) ? 1.f : 0.f;
+        return;
+    }
+    chol_blocked_body(g.Gf, g.m, g.Rinv, near_identity ? nullptr : g.flag, g.status, near_identity,
+                      span_only ? g.next : nullptr);
 }
 
 __global__ void __launch_bounds__(kCholThreads) cholesky_grouped_kernel(const GInst* __restrict__ gi) {
@@ -1895,14 +1901,16 @@ cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_bloc
     return cudaGetLastError();
 }
 
-cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st) {
+cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st, bool span_only,
+                         bool gated) {
     const size_t lda = (size_t)((max_m + 3) & ~3);
     const size_t smem = ((size_t)2 * max_m * lda + (size_t)((max_m + kCB - 1) / kCB) * kCB * kCB + max_m) *
                         sizeof(float);
     cudaError_t e = allow_smem(chol_blocked_grouped_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    chol_blocked_grouped_kernel<<<count, kCBThreads, smem, st>>>(gi, near_identity ? 1 : 0);
+    chol_blocked_grouped_kernel<<<count, kCBThreads, smem, st>>>(gi, near_identity ? 1 : 0, span_only ? 1 : 0,
+                                                                  gated ? 1 : 0);
     return cudaGetLastError();
 }
 
