@@ -1543,7 +1543,6 @@ cudaError_t lockstep_orth(ppca_batch* b, int src, int dst, bool span_only = fals
     cudaStream_t st = b->stream;
     cudaError_t e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, src, b->g_max_m, false, st);
     if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, false, st, span_only);
-    if (e == cudaSuccess) e = grouped_chol_fallback(b->g_inst, count, b->g_max_m, st);
     if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, src, kGT, b->g_max_m, st);
     if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, span_only, st);
     if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st, false, span_only);

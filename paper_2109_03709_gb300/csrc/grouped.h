@@ -101,13 +101,13 @@ __host__ __device__ inline float* garray(const GInst& g, int which) {
 
 // ---- launchers (small.cu): CholeskyQR2 of every instance, src -> dst (V, Z or T)
 // gated: an instance's blocks do nothing while *next == 0 (its second pass is
-// skipped).  grouped_chol: first pass (near_identity false) sets *next when
-// span_only; second pass with gated writes R^-1 = I where *next == 0.
+// skipped).  grouped_chol: the first pass (near_identity false) redoes a
+// rejected FP32 factor in double-float in the same block and sets *next when
+// span_only; the second pass with gated writes R^-1 = I where *next == 0.
 cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_blocks, int src, int max_m,
                          bool gated, cudaStream_t st);
 cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st,
                          bool span_only = false, bool gated = false);
-cudaError_t grouped_chol_fallback(const GInst* gi, int count, int max_m, cudaStream_t st);
 cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st);
 cudaError_t grouped_quantize_bf16(const float* const* X32, const int64_t* ld32, const GInst* gi, GTable blocks,
                                   cudaStream_t st);

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(kCholThreads) cholesky_kernel(const double* __
 // Without `fallback` (second pass, G' within rounding of I) a non-positive
 // pivot is recorded as kDevCholeskyBreakdown.
 constexpr int kCBThreads = 512;
+static_assert(kCBThreads == kCholThreads, "the grouped factor kernel runs the fallback in the same block");
 constexpr int kCB = 32;
 constexpr float kCholKappaMax = 65536.f;     // 2^16
 // An accepted first-pass factor whose bound is at most 2^10 leaves Q^T Q within
@@ -1400,12 +1401,12 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_grouped_kernel(con
     }
     chol_blocked_body(g.Gf, g.m, g.Rinv, near_identity ? nullptr : g.flag, g.status, near_identity,
                       span_only ? g.next : nullptr);
-}
-
-__global__ void __launch_bounds__(kCholThreads) cholesky_grouped_kernel(const GInst* __restrict__ gi) {
-    const GInst& g = gi[blockIdx.x];
-    if (*g.flag == 0) return;                           // the FP32 factor was accepted
-    cholesky_body<true>(g.G, g.m, g.Rinv, g.status);
+    if (!near_identity) {
+        // a rejected FP32 factor is redone in double-float by the same block
+        // (one launch instead of a second, mostly empty one)
+        __syncthreads();
+        if (*(volatile int*)g.flag) cholesky_body<true>(g.G, g.m, g.Rinv, g.status);
+    }
 }
 
 __global__ void __launch_bounds__(256) apply_rinv_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int src,
@@ -1904,22 +1905,14 @@ cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_bloc
 cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st, bool span_only,
                          bool gated) {
     const size_t lda = (size_t)((max_m + 3) & ~3);
-    const size_t smem = ((size_t)2 * max_m * lda + (size_t)((max_m + kCB - 1) / kCB) * kCB * kCB + max_m) *
-                        sizeof(float);
+    size_t smem = ((size_t)2 * max_m * lda + (size_t)((max_m + kCB - 1) / kCB) * kCB * kCB + max_m) *
+                  sizeof(float);
+    if (!near_identity) smem = std::max(smem, (size_t)3 * max_m * max_m * sizeof(float));   // the fallback
     cudaError_t e = allow_smem(chol_blocked_grouped_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
     chol_blocked_grouped_kernel<<<count, kCBThreads, smem, st>>>(gi, near_identity ? 1 : 0, span_only ? 1 : 0,
                                                                   gated ? 1 : 0);
-    return cudaGetLastError();
-}
-
-cudaError_t grouped_chol_fallback(const GInst* gi, int count, int max_m, cudaStream_t st) {
-    const size_t smem = (size_t)3 * max_m * max_m * sizeof(float);
-    cudaError_t e = allow_smem(cholesky_grouped_kernel, smem);
-    if (e != cudaSuccess) return e;
-    note_launch();
-    cholesky_grouped_kernel<<<count, kCholThreads, smem, st>>>(gi);
     return cudaGetLastError();
 }
 

@@ -241,3 +241,38 @@ def test_lockstep_full_size_subset_matches_oracle(cuda_device):
             Vo = oracle.power_prime(oracle.bf16_round_rne(Xs), host_basis(ins["V0"]), T)
             assert oracle.principal_angles(Vg, Vo).max() <= 3e-2, i
         del Xs
+
+
+def test_lockstep_ill_conditioned_start(cuda_device):
+    """A starting basis with condition number 1e3 (kappa of its Gram matrix 1e6,
+    past the FP32 factor's acceptance bound 2^16) makes CholeskyQR's FP32 factor
+    fail its conditioning test, so the grouped factor kernel redoes it in
+    double-float in the same block.  With T = 0 the lockstep output is orth(V0):
+    orthonormal to 1e-5 and spanning the oracle's orthonormalisation of V0 to
+    5e-4 rad (Q = V R^-1 applied in FP32 perturbs the span by about
+    kappa(V) u = 6e-5 per column); the pPCA step on it matches the oracle's."""
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    for T, bound in ((0, 5e-4),):
+        inst = make_batch(3, seed=733, T=T, nmax=8000, dtypes=[torch.bfloat16])
+        V0 = host_basis(inst[1]["V0"])
+        U, _, Wt = np.linalg.svd(V0, full_matrices=False)
+        sv = np.logspace(0, -3, V0.shape[1])                 # kappa(V0) = 1e3
+        inst[1]["V0"] = torch.from_numpy(np.ascontiguousarray(((U * sv) @ Wt).T, dtype=np.float32)).cuda()
+        b = P.ppca_batch_create(inst, slots=2)
+        P.ppca_batch_run(b)
+        P.ppca_batch_sync(b)
+        assert P.ppca_batch_lockstep(b)
+        for i, a in enumerate(inst):
+            Xs = a["X"].double().cpu().numpy()
+            Va = host_basis(a["V_out"])
+            Vo = oracle.power_prime(Xs, host_basis(a["V0"]), T) if T else oracle.orth(host_basis(a["V0"]))
+            assert oracle.principal_angles(Va, Vo).max() <= bound, (T, i)
+            if T == 0:
+                assert np.abs(Va.T @ Va - np.eye(Va.shape[1])).max() <= 1e-5, i
+            # the pPCA step's eigenvalues: relative 1e-5, or for the small ones of an
+            # unprimed (T = 0) basis the projected Gram's bound, 4e-6 of its largest
+            Eo, lo = oracle.ppca_finalize(Xs, Va, a["k"])
+            np.testing.assert_allclose(a["lam"].cpu().numpy(), lo, rtol=1e-5, atol=4e-6 * lo.max(),
+                                       err_msg=f"instance {i}")
