@@ -370,7 +370,8 @@ typedef struct ppca_timing {
  * captured once (per handle, shape and parameters) on a private stream joined
  * to the handle's stream by events; steps that hold an epoch's partial batch,
  * FP8 data, minibatches that are not whole 128-row tiles, row sharding, pass
- * timing and the CUDA-core engine run step by step.  The results are the same
+ * timing, the CUDA-core engine and calls made while the handle's stream is
+ * being captured run step by step.  The results are the same
  * bits either way (the same kernels and arithmetic).  enable == 0: always step
  * by step.  Infrastructure: no counterpart in the paper.
  */

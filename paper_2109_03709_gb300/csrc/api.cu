@@ -428,6 +428,13 @@ struct StepGraphKey {
 
 bool step_graph_eligible(const ppca_handle* h) {
     if (!h->step_graphs || h->ar_fn || h->timing) return false;
+    // the caller is capturing the handle's stream: plain steps, which it can capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(h->stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return false;
     if (h->method != PPCA_OJA && h->method != PPCA_EIGENGAME) return false;
     const ppca_precision prec = prime_prec(h);
     const bool supported = tc_pass_supported(h->x, h->m);

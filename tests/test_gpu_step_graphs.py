@@ -83,3 +83,42 @@ def test_step_graphs_skip_ragged_batches(cuda_device):
     Vs, ls = prime(P, Xd, P.PPCA_OJA, m, 40, kw, V0, False, counter)
     assert torch.equal(Vg, Vs)
     assert lg == ls
+
+
+def test_steps_inside_a_caller_capture(cuda_device):
+    """A caller capturing the handle's stream gets plain steps it can capture:
+    40 Oja steps captured with torch.cuda.graph and replayed once give the same
+    bits as the same steps run directly (graph-replayed inside the library)."""
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    P.load_library()
+    n, d, m = 20000, 512, 32
+    X, _ = synth.gaussian_data(n, d, 0.95 ** np.arange(1, d + 1), seed=8)
+    Xd = dev_matrix(X, "f32")
+    V0 = dev_basis(synth.initial_basis(d, m, seed=9))
+    kw = {"batch": 256, "lr": 1.0, "lr_offset": 100.0}
+    out = []
+    for captured in (False, True):
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            h = P.ppca_create(Xd, stream=st)
+            prm = P.ppca_prime_params_default(P.PPCA_OJA)
+            for k, v in kw.items():
+                setattr(prm, k, v)
+            prm.precision = P.PPCA_PREC_FAST
+            P.ppca_prime(h, P.PPCA_OJA, m, 0, prm, V0=V0)
+            P.ppca_sync(h)
+            if captured:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=st):
+                    P.ppca_prime_continue(h, 40)
+                g.replay()
+            else:
+                P.ppca_prime_continue(h, 40)
+            V = torch.empty((m, d), dtype=torch.float32, device="cuda")
+            P.ppca_get_basis(h, V)
+            P.ppca_sync(h)
+        torch.cuda.synchronize()
+        out.append(V)
+    assert torch.equal(out[0], out[1])
