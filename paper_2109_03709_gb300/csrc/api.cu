@@ -1353,7 +1353,9 @@ bool prepare_lockstep(ppca_batch* b) {
         g.nk = (int)cdiv(d, 64);
         g.ntiles = (int)(g.ldy / 128);
         g.kst = (int)(g.ldy / 64);
-        g.Sg = (int)cdiv(g.kst, 128);        // Z = X^T Y row groups of at most 8192 rows
+        // Z = X^T Y row groups of at most 8192 rows (128 K-stages): within the grouped
+        // pass's fold interval (256), so each group's partial is one FP32 sum
+        g.Sg = (int)cdiv(g.kst, 128);
         g.V0 = ds.V0;
         const bool f32 = ds.dtype == PPCA_F32;
         b->any_f32 |= f32;
@@ -1400,7 +1402,7 @@ bool prepare_lockstep(ppca_batch* b) {
         o[i].t = take((size_t)d * m * 4);
         o[i].vp = take((size_t)g.m_pad * g.ldv * 2);
         o[i].yt = take((size_t)g.m_pad * g.ldy * 2);
-        o[i].zacc = take((size_t)g.Sg * g.m_pad * g.Dt * 128 * 8);
+        o[i].zacc = take((size_t)g.Sg * g.m_pad * g.Dt * 128 * 4);
         o[i].G = take((size_t)m * m * 8);
         o[i].Gf = take((size_t)m * m * 4);
         o[i].Rinv = take((size_t)m * m * 4);
@@ -1518,10 +1520,15 @@ bool prepare_lockstep(ppca_batch* b) {
              cudaMemcpy(base + o_x32, x32.data(), sizeof(float*) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaMemcpy(base + o_ld32, ld32.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice) == cudaSuccess &&
              cudaEventCreateWithFlags(&b->g_done, cudaEventDisableTiming) == cudaSuccess;
+    // the BF16 bases' padding (rows m..m_pad, columns d..ldv) stays zero for good
+    for (int i = 0; i < count && ok; ++i)
+        ok = cudaMemset(gi[i].Vp, 0, (size_t)gi[i].m_pad * gi[i].ldv * 2) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         cudaFree(mem);
         cudaFree(st);
+        if (b->g_done) cudaEventDestroy(b->g_done);
+        b->g_done = nullptr;
         return false;
     }
     b->g_mem = mem;
@@ -1553,7 +1560,8 @@ cudaError_t lockstep_orth(ppca_batch* b, int src, int dst, bool span_only = fals
     if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, src, kGT, b->g_max_m, st);
     if (e == cudaSuccess) e = grouped_gram(b->g_inst, b->t_gram, b->t_reduce, kGT, b->g_max_m, span_only, st);
     if (e == cudaSuccess) e = grouped_chol(b->g_inst, count, b->g_max_m, true, st, false, span_only);
-    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, dst, b->g_max_m, st);
+    // the basis the next pass reads: its BF16 rounding written by the same kernel
+    if (e == cudaSuccess) e = grouped_apply_rinv(b->g_inst, b->t_apply, kGT, dst, b->g_max_m, st, dst == kGV);
     return e;
 }
 
@@ -1570,7 +1578,6 @@ ppca_status enqueue_lockstep(ppca_batch* b) {
             CUDA_TRY(init_gaussian(b->g_host[i].V, b->descs[i].d, b->descs[i].m, b->descs[i].seed, st));
     CUDA_TRY(lockstep_orth(b, kGV, kGV));
     for (int t = 0; t < b->descs[0].T; ++t) {
-        CUDA_TRY(grouped_split_v(b->g_inst, b->t_splitv, st));
         CUDA_TRY(grouped_xpass(b->g_inst, b->g_maps, b->t_xv, b->t_xty, b->t_dm, b->g_status, b->num_sms, st));
         CUDA_TRY(lockstep_orth(b, kGZ, kGV, /*span_only=*/true));
     }

@@ -28,7 +28,7 @@ struct GInst {
     int64_t ldv;
     __nv_bfloat16* Yt;        // [m_pad][ldy]: Y^T rounded to BF16
     int64_t ldy;
-    float* Zacc;              // [Sg][m_pad][Dt * 128] double-float partials of Z
+    float* Zacc;              // [Sg][m_pad][Dt * 128] FP32 partials of Z, one per row group
     int Dt, Sg, kst, ntiles, nk;
     double* G;                // m x m
     float* Gf;                // m x m
@@ -108,7 +108,9 @@ cudaError_t grouped_gram(const GInst* gi, GTable gram_blocks, GTable reduce_bloc
                          bool gated, cudaStream_t st);
 cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identity, cudaStream_t st,
                          bool span_only = false, bool gated = false);
-cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st);
+// split: also the BF16 rounding of the result into each instance's Vp.
+cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st,
+                               bool split = false);
 cudaError_t grouped_quantize_bf16(const float* const* X32, const int64_t* ld32, const GInst* gi, GTable blocks,
                                   cudaStream_t st);
 cudaError_t grouped_copy_v0(const GInst* gi, GTable dm_blocks, cudaStream_t st);
@@ -134,7 +136,6 @@ cudaError_t grouped_projected_gram(const GInst* gi, const GMaps* maps, GTable yg
 bool grouped_encode_gram_maps(const GInst& g, GMaps& out);
 
 // ---- launchers (pass_tc.cu): the fast BF16 X-pass of every instance
-cudaError_t grouped_split_v(const GInst* gi, GTable blocks, cudaStream_t st);
 // Q (held in Z) as three BF16 pieces Q3 (the pPCA step's split precision).
 cudaError_t grouped_split_q(const GInst* gi, GTable blocks, cudaStream_t st);
 cudaError_t grouped_xpass(const GInst* gi, const GMaps* maps, GTable xv_items, GTable xty_items,

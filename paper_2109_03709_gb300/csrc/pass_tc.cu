@@ -1696,22 +1696,14 @@ __global__ void zreduce_kernel(const float* __restrict__ Zacc, int Sg, int Dt, i
 
 // ---------------------------------------------------------------- grouped fast BF16 pass
 //
-// The two-kernel fast pass of many instances in one launch each (grouped.h):
+// The two-kernel fast pass of many instances in one launch each (grouped.h).
+// A Z item's K range (a row group) is at most 128 K-stages, inside the fold
+// interval, so each item leaves one FP32 partial, summed in double-float by
+// zreduce_grouped_kernel.
 // work item w of Y = X V is tile w - base[i] of instance i, of Z = X^T Y task
 // w - base[i] (128-column slice s, row group g) of instance i.  Each item uses
 // its instance's TMA descriptors (device memory), basis width (the MMA's N)
 // and buffers; the shared-memory stages and TMEM are sized for the widest basis.
-
-__global__ void split_v_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
-    const int i = group_find(tab, blockIdx.x);
-    const GInst& g = gi[i];
-    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)g.m_pad * g.ldv) return;
-    const int c = (int)(e / g.ldv);
-    const int64_t k = e % g.ldv;
-    const float v = (c < g.m && k < g.d) ? g.V[(int64_t)c * g.d + k] : 0.f;
-    g.Vp[e] = __float2bfloat16_rn(v);
-}
 
 __global__ void split_q_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
     const int i = group_find(tab, blockIdx.x);
@@ -1733,11 +1725,7 @@ __global__ void zreduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab)
     const int c = (int)(e / g.d);
     const int64_t j = e % g.d;
     float hi = 0.f, lo = 0.f;
-    for (int q = 0; q < g.Sg; ++q) {
-        const float2 v = reinterpret_cast<const float2*>(g.Zacc)[((int64_t)q * g.m_pad + c) * (g.Dt * 128) + j];
-        df_add(hi, lo, v.x);
-        df_add(hi, lo, v.y);
-    }
+    for (int q = 0; q < g.Sg; ++q) df_add(hi, lo, g.Zacc[((int64_t)q * g.m_pad + c) * (g.Dt * 128) + j]);
     g.Z[e] = hi + lo;
 }
 
@@ -1929,8 +1917,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int s = task % g.Dt, grp = task / g.Dt;
             const int k0 = (int)((int64_t)grp * g.kst / g.Sg), k1 = (int)((int64_t)(grp + 1) * g.kst / g.Sg);
             const int64_t j = (int64_t)s * 128 + q * 32 + lane;
-            const int64_t zs = (int64_t)g.Dt * 128;     // Z partials [g][column][row]
-            float2* z = reinterpret_cast<float2*>(g.Zacc) + (int64_t)grp * g.m_pad * zs + j;
+            const int64_t zs = (int64_t)g.Dt * 128;     // Z partials [g][column][row], FP32
+            float* z = g.Zacc + (int64_t)grp * g.m_pad * zs + j;
             for (int kb = k0; kb < k1; kb += flush, ++fb) {
                 const uint32_t b = fb & 1u, tph = (fb >> 1) & 1u;
                 if (!tc::mbar_wait(&hd->tfull[b], tph, status) || *(volatile int*)&hd->abort) {
@@ -1943,18 +1931,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t r[32];
                     tc::tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + b * 128u + (uint32_t)c0, r);
                     tc::tmem_ld_wait();
-                    float2* zz = z + (int64_t)c0 * zs;
-                    if (kb == k0) {
+                    // one fold per item (its K range is at most `flush` stages): store
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) zz[jj * zs] = make_float2(__uint_as_float(r[jj]), 0.f);
-                    } else {
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            float2 v = zz[jj * zs];
-                            df_add(v.x, v.y, __uint_as_float(r[jj]));
-                            zz[jj * zs] = v;
-                        }
-                    }
+                    for (int jj = 0; jj < 32; ++jj) z[(int64_t)(c0 + jj) * zs] = __uint_as_float(r[jj]);
                 }
                 tc::fence_before_sync();
                 tc::mbar_arrive(&hd->tempty[b]);
@@ -2461,12 +2440,6 @@ bool grouped_encode_maps(const GInst& g, GMaps& out) {
            encode_bf16_2d(&out.v, g.Vp, g.d, (uint64_t)g.m_pad, g.ldv * 2, 64, g.m_pad) &&
            encode_bf16_2d(&out.xb, X, g.d, g.n, g.ld * 2, 64, 64) &&
            encode_bf16_2d(&out.y, g.Yt, g.ldy, (uint64_t)g.m_pad, g.ldy * 2, 64, g.m_pad);
-}
-
-cudaError_t grouped_split_v(const GInst* gi, GTable blocks, cudaStream_t st) {
-    note_launch();
-    split_v_grouped_kernel<<<blocks.total, 256, 0, st>>>(gi, blocks);
-    return cudaGetLastError();
 }
 
 cudaError_t grouped_split_q(const GInst* gi, GTable blocks, cudaStream_t st) {

@@ -706,8 +706,10 @@ constexpr int kApplyHalf = kApplyRows / 2;
 
 __host__ __device__ inline int apply_xs_floats(int m) { return (m * m + 3) & ~3; }
 
+// Qb (may be NULL): Q's BF16 rounding as well, column c at Qb + c * ldb.
 __device__ __forceinline__ void apply_rinv_body(const float* __restrict__ V, const float* __restrict__ Rinv,
-                                                int64_t d, int m, float* __restrict__ Q, int block) {
+                                                int64_t d, int m, float* __restrict__ Q, int block,
+                                                __nv_bfloat16* __restrict__ Qb = nullptr, int64_t ldb = 0) {
     extern __shared__ __align__(16) float ars[];
     float* xs = ars;                          // m x m, X row-major
     float* vs = ars + apply_xs_floats(m);     // m x kApplyRows, vs[l][r] = V[r0 + r, l]
@@ -748,6 +750,12 @@ __device__ __forceinline__ void apply_rinv_body(const float* __restrict__ V, con
 #pragma unroll
     for (int r = 0; r < kApplyHalf; ++r)
         if (rb + r < d) out[r] = acc[r];
+    if (Qb) {
+        __nv_bfloat16* ob = Qb + (int64_t)c * ldb + rb;
+#pragma unroll
+        for (int r = 0; r < kApplyHalf; ++r)
+            if (rb + r < d) ob[r] = __float2bfloat16_rn(acc[r]);
+    }
 }
 
 __global__ void __launch_bounds__(256) apply_rinv_kernel(const float* __restrict__ V, const float* __restrict__ Rinv,
@@ -1409,11 +1417,14 @@ __global__ void __launch_bounds__(kCBThreads, 1) chol_blocked_grouped_kernel(con
     }
 }
 
+// split: also write Q's BF16 rounding into Vp (the next pass's operand; its
+// padding rows and columns stay zero from the set-up).
 __global__ void __launch_bounds__(256) apply_rinv_grouped_kernel(const GInst* __restrict__ gi, GTable tab, int src,
-                                                                 int dst) {
+                                                                 int dst, int split) {
     const int i = group_find(tab, blockIdx.x);
     const GInst& g = gi[i];
-    apply_rinv_body(garray(g, src), g.Rinv, g.d, g.m, garray(g, dst), blockIdx.x - tab.base[i]);
+    apply_rinv_body(garray(g, src), g.Rinv, g.d, g.m, garray(g, dst), blockIdx.x - tab.base[i],
+                    split ? g.Vp : nullptr, g.ldv);
 }
 
 // BF16 rounding of every instance's FP32 X (d % 8 == 0, 16-byte aligned rows), eight values a thread.
@@ -1916,14 +1927,15 @@ cudaError_t grouped_chol(const GInst* gi, int count, int max_m, bool near_identi
     return cudaGetLastError();
 }
 
-cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st) {
+cudaError_t grouped_apply_rinv(const GInst* gi, GTable blocks, int src, int dst, int max_m, cudaStream_t st,
+                               bool split) {
     if (max_m > 128) return cudaErrorInvalidValue;
     const int threads = 2 * ((max_m + 31) / 32 * 32);
     const size_t smem = ((size_t)apply_xs_floats(max_m) + (size_t)max_m * kApplyRows) * sizeof(float);
     cudaError_t e = allow_smem(apply_rinv_grouped_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
-    apply_rinv_grouped_kernel<<<blocks.total, threads, smem, st>>>(gi, blocks, src, dst);
+    apply_rinv_grouped_kernel<<<blocks.total, threads, smem, st>>>(gi, blocks, src, dst, split ? 1 : 0);
     return cudaGetLastError();
 }
 
