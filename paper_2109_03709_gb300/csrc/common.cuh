@@ -128,6 +128,12 @@ __device__ __forceinline__ void set_status(int* status, int code) {
 void note_launch();
 int64_t launches_so_far();
 
+// Raises kernel `func`'s dynamic shared-memory limit on the current device to
+// at least `bytes`, and never lowers it: a captured graph's kernel nodes keep
+// the sizes they were captured with, so a later launch of the same kernel with
+// less shared memory must not shrink the limit under them.
+cudaError_t smem_at_least(const void* func, size_t bytes);
+
 // Row sample of the pPCA step (the paper projects 10 % of the data in its
 // large runs): 128-row block t is kept when the t-th output of the SplitMix64
 // stream seeded with `seed` (Steele, Lea and Flood, 2014), as a 53-bit

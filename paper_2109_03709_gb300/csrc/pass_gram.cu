@@ -678,7 +678,7 @@ cudaError_t launch_ygen(const Work& work, int items, int flush, int m_pad_max, i
     const uint32_t acc_stride = (uint32_t)m_pad_max;
     const uint32_t tmem_cols = pow2_cols(4u * acc_stride);
     auto kern = ygen_kernel<NX, NV, F32X, Work>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
     const int grid = items < num_sms ? items : num_sms;
     note_launch();
@@ -692,7 +692,7 @@ cudaError_t launch_gram_y(const Work& work, int grid, int* status, cudaStream_t 
     const int gstages = 4;
     const size_t smem = 1024 + (size_t)gstages * 3 * kPiece + sizeof(GHeader);
     auto kern = gram_y_kernel<Work>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least(reinterpret_cast<const void*>(kern), smem);
     if (e != cudaSuccess) return e;
     note_launch();
     kern<<<grid, kGThreadsBf16, smem, st>>>(work, 12, gstages, status);

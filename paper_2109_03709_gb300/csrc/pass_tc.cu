@@ -2120,7 +2120,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const uint32_t stage_bytes = raw_xv + 128u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        e = cudaFuncSetAttribute(xv_tc_kernel<S, FP8X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_at_least(reinterpret_cast<const void*>(xv_tc_kernel<S, FP8X>), smem);
         if (e != cudaSuccess) return e;
         // few row tiles (a minibatch) and a long K: split K so that every SM has work
         int ksplit = 1;
@@ -2151,7 +2151,7 @@ cudaError_t run_pass(const XView& x, const float* V, int m, int64_t r0, int64_t 
         const uint32_t stage_bytes = raw_xty + 2u * 64u * 128u + S * (uint32_t)ps.m_pad * 128u;
         const int stages = stages_for(stage_bytes);
         const size_t smem = smem_bytes(stages, stage_bytes);
-        e = cudaFuncSetAttribute(xty_tc_kernel<S, FP8X>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_at_least(reinterpret_cast<const void*>(xty_tc_kernel<S, FP8X>), smem);
         if (e != cudaSuccess) return e;
         const int kst = (int)(ps.ldy / kBK);
         Sg = choose_row_groups(ps.Dt, kst, num_sms, sc.z_bytes, ps.m_pad);
@@ -2198,9 +2198,9 @@ cudaError_t run_pass_f8(const XView& x, const float* V, int m, int64_t r0, int64
     const uint32_t stage_bytes = 2u * 128u * 128u + 2u * (uint32_t)m_pad * 128u;
     const int stages = stages_for(stage_bytes);
     const size_t smem = smem_bytes(stages, stage_bytes);
-    e = cudaFuncSetAttribute(xv_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_at_least(reinterpret_cast<const void*>(xv_f8_kernel), smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(xty_f8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_at_least(reinterpret_cast<const void*>(xty_f8_kernel), smem);
     if (e != cudaSuccess) return e;
     note_launch();
     xv_f8_kernel<<<ntiles < num_sms ? ntiles : num_sms, kThreads, smem, st>>>(tmX, tmV, ntiles, nk, m_pad, stages,
@@ -2254,7 +2254,7 @@ cudaError_t run_fused(const XView& x, const float* V, int m, int64_t r0, int64_t
     if (p_stages < 2) return cudaErrorInvalidValue;
     const size_t smem =
         1024 + (size_t)p_stages * p_stage + (size_t)c_stages * c_stage + sizeof(FusedHeader);
-    e = cudaFuncSetAttribute(xpass_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = smem_at_least(reinterpret_cast<const void*>(xpass_fused_kernel), smem);
     if (e != cudaSuccess) return e;
     int* ready = sc.flags;
     int* consumed = sc.flags + ps.ntiles + 1;
@@ -2325,7 +2325,7 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         int stages = (int)((kSmemBudget - 2048) / stage_bytes);
         if (stages > kMaxStages) stages = kMaxStages;
         const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(F32Header);
-        e = cudaFuncSetAttribute(xv_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_at_least(reinterpret_cast<const void*>(xv_f32_kernel), smem);
         if (e != cudaSuccess) return e;
         // few row tiles (a minibatch) and a long K: split K so that every SM has work
         int ksplit = 1;
@@ -2356,7 +2356,7 @@ cudaError_t run_pass_f32(const XView& x, const float* V, int m, int64_t r0, int6
         int stages = (int)((kSmemBudget - 2048) / stage_bytes);
         if (stages > kMaxStages) stages = kMaxStages;
         const size_t smem = 1024 + (size_t)stages * stage_bytes + sizeof(F32Header);
-        e = cudaFuncSetAttribute(xty_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = smem_at_least(reinterpret_cast<const void*>(xty_f32_kernel), smem);
         if (e != cudaSuccess) return e;
         const int kst = (int)(ldy / kBK32);
         Sg = choose_row_groups(Dt, kst, num_sms, sc.z_bytes, m_pad);
@@ -2453,7 +2453,7 @@ cudaError_t grouped_xpass(const GInst* gi, const GMaps* maps, GTable xv_items, G
     const uint32_t xv_stage = 128u * 128u + 128u * 128u;
     const int xv_stages = stages_for(xv_stage);
     const size_t xv_smem = smem_bytes(xv_stages, xv_stage);
-    cudaError_t e = cudaFuncSetAttribute(xv_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xv_smem);
+    cudaError_t e = smem_at_least(reinterpret_cast<const void*>(xv_grouped_kernel), xv_smem);
     if (e != cudaSuccess) return e;
     note_launch();
     xv_grouped_kernel<<<std::min(xv_items.total, num_sms), kThreads, xv_smem, st>>>(gi, maps, xv_items, xv_stages,
@@ -2461,7 +2461,7 @@ cudaError_t grouped_xpass(const GInst* gi, const GMaps* maps, GTable xv_items, G
     const uint32_t xty_stage = 2u * 64u * 128u + 128u * 128u;
     const int xty_stages = stages_for(xty_stage);
     const size_t xty_smem = smem_bytes(xty_stages, xty_stage);
-    e = cudaFuncSetAttribute(xty_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xty_smem);
+    e = smem_at_least(reinterpret_cast<const void*>(xty_grouped_kernel), xty_smem);
     if (e != cudaSuccess) return e;
     note_launch();
     xty_grouped_kernel<<<std::min(xty_items.total, num_sms), kThreads, xty_smem, st>>>(gi, maps, xty_items, 256,

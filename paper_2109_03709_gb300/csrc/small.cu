@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 
 namespace ppca {
@@ -1373,8 +1374,7 @@ __global__ void copy_kernel(const float* __restrict__ s, float* __restrict__ d, 
 
 template <typename K>
 cudaError_t allow_smem(K kernel, size_t bytes) {
-    if (bytes <= 32 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return smem_at_least(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 // ------------------------------------------------------------------ grouped launches
@@ -1502,6 +1502,21 @@ __global__ void copy_v0_grouped_kernel(const GInst* __restrict__ gi, GTable tab)
 }  // namespace
 
 // ============================================================================ launchers
+
+cudaError_t smem_at_least(const void* func, size_t bytes) {
+    if (bytes <= 32 * 1024) return cudaSuccess;          // within every kernel's default limit
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> set;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t& now = set[std::make_pair(dev, func)];
+    if (bytes <= now) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) now = bytes;
+    return e;
+}
 
 // The workspace sized for m also serves every narrower basis.
 size_t gram_part_floats(int64_t d, int m) {
