@@ -1720,12 +1720,15 @@ __global__ void split_q_grouped_kernel(const GInst* __restrict__ gi, GTable tab)
 __global__ void zreduce_grouped_kernel(const GInst* __restrict__ gi, GTable tab) {
     const int i = group_find(tab, blockIdx.x);
     const GInst& g = gi[i];
-    const int64_t e = (int64_t)(blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
-    if (e >= g.d * g.m) return;
-    const int c = (int)(e / g.d);
-    const int64_t j = e % g.d;
+    // an instance's d m (< 2^31) fits 32-bit index arithmetic
+    const int e = (blockIdx.x - tab.base[i]) * blockDim.x + threadIdx.x;
+    const int d = (int)g.d;
+    if (e >= d * g.m) return;
+    const int c = e / d, j = e - c * d;
+    const int64_t stride = (int64_t)g.m_pad * (g.Dt * 128);
+    const float* p = g.Zacc + (int64_t)c * (g.Dt * 128) + j;
     float hi = 0.f, lo = 0.f;
-    for (int q = 0; q < g.Sg; ++q) df_add(hi, lo, g.Zacc[((int64_t)q * g.m_pad + c) * (g.Dt * 128) + j]);
+    for (int q = 0; q < g.Sg; ++q) df_add(hi, lo, p[q * stride]);
     g.Z[e] = hi + lo;
 }
 
