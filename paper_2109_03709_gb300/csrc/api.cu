@@ -1221,7 +1221,7 @@ struct ppca_batch {
     GMaps* g_maps = nullptr;              // device: one per instance
     int* g_status = nullptr;              // device status word of the lockstep kernels
     std::vector<GInst> g_host;
-    GTable t_quant{}, t_splitv{}, t_xv{}, t_xty{}, t_dm{}, t_gram{}, t_reduce{}, t_apply{};
+    GTable t_quant{}, t_splitq{}, t_xv{}, t_xty{}, t_dm{}, t_gram{}, t_reduce{}, t_apply{};
     GTable t_ygen32{}, t_ygen16{}, t_ychunks{}, t_gred{}, t_rayleigh{}, t_rotate{}, t_sign{};
     bool any_vout = false;
     const float* const* g_x32 = nullptr;  // device: FP32 X of each instance (quantize)
@@ -1329,8 +1329,8 @@ bool prepare_lockstep(ppca_batch* b) {
         size_t q3, y3, gpart, gp, evals, uf, u64, lam, sweeps, w, U;
     };
     std::vector<Off> o(count);
-    int64_t n_quant = 0, n_splitv = 0, n_xv = 0, n_xty = 0, n_dm = 0, n_gram = 0, n_reduce = 0, n_apply = 0;
-    std::vector<int> c_quant(count), c_splitv(count), c_xv(count), c_xty(count), c_dm(count), c_gram(count),
+    int64_t n_quant = 0, n_splitq = 0, n_xv = 0, n_xty = 0, n_dm = 0, n_gram = 0, n_reduce = 0, n_apply = 0;
+    std::vector<int> c_quant(count), c_splitq(count), c_xv(count), c_xty(count), c_dm(count), c_gram(count),
         c_reduce(count), c_apply(count);
     std::vector<int> c_ygen32(count), c_ygen16(count), c_ychunks(count), c_gred(count), c_rayleigh(count),
         c_rotate(count), c_sign(count);
@@ -1409,7 +1409,7 @@ bool prepare_lockstep(ppca_batch* b) {
         o[i].part = take(gram_part_floats(d, m) * 4);
         o[i].flag = take(8);
         c_quant[i] = f32 ? (int)cdiv(n * (d / 8), 256) : 0;
-        c_splitv[i] = (int)cdiv((int64_t)g.m_pad * g.ldv, 256);
+        c_splitq[i] = (int)cdiv((int64_t)g.m_pad * g.ldv, 256);
         c_xv[i] = g.ntiles;
         c_xty[i] = g.Dt * g.Sg;
         c_dm[i] = (int)cdiv(d * m, 256);
@@ -1417,7 +1417,7 @@ bool prepare_lockstep(ppca_batch* b) {
         c_reduce[i] = shp[i].reduce_blocks;
         c_apply[i] = shp[i].apply_blocks;
         n_quant += c_quant[i];
-        n_splitv += c_splitv[i];
+        n_splitq += c_splitq[i];
         n_xv += c_xv[i];
         n_xty += c_xty[i];
         n_dm += c_dm[i];
@@ -1425,7 +1425,7 @@ bool prepare_lockstep(ppca_batch* b) {
         n_reduce += c_reduce[i];
         n_apply += c_apply[i];
     }
-    const int64_t most = std::max({n_quant, n_splitv, n_xv, n_xty, n_dm, n_gram, n_reduce, n_apply});
+    const int64_t most = std::max({n_quant, n_splitq, n_xv, n_xty, n_dm, n_gram, n_reduce, n_apply});
     if (most >= (int64_t)1 << 31 || n_pp * count >= (int64_t)1 << 31) return false;
     const size_t tab_ints = (size_t)15 * (count + 1);
     const size_t o_tabs = take(tab_ints * 4);
@@ -1499,7 +1499,7 @@ bool prepare_lockstep(ppca_batch* b) {
         return t;
     };
     b->t_quant = table(c_quant);
-    b->t_splitv = table(c_splitv);
+    b->t_splitq = table(c_splitq);
     b->t_xv = table(c_xv);
     b->t_xty = table(c_xty);
     b->t_dm = table(c_dm);
@@ -1585,7 +1585,7 @@ ppca_status enqueue_lockstep(ppca_batch* b) {
     // split precision on the data as given, the eigensolve, E = Q U[:, :k]
     if (b->any_vout) CUDA_TRY(grouped_copy_vout(b->g_inst, b->t_dm, st));
     CUDA_TRY(lockstep_orth(b, kGV, kGZ));
-    CUDA_TRY(grouped_split_q(b->g_inst, b->t_splitv, st));
+    CUDA_TRY(grouped_split_q(b->g_inst, b->t_splitq, st));
     CUDA_TRY(grouped_projected_gram(b->g_inst, b->g_maps, b->t_ygen32, b->t_ygen16, b->t_ychunks, b->t_gred,
                                     b->g_max_m, b->g_status, b->num_sms, st));
     CUDA_TRY(grouped_eigh(b->g_inst, count, b->t_rayleigh, b->g_max_m, st));
