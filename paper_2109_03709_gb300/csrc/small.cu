@@ -1069,20 +1069,21 @@ __global__ void oja_update_kernel(float* __restrict__ W, const float* __restrict
                                   int64_t d, int m, float c_host, const float* __restrict__ c_dev) {
     const float c = c_dev ? *c_dev : c_host;
     extern __shared__ float sm[];
+    const int ws = m + 1;                  // row stride: consecutive rows in different banks
     float* Ss = sm;                        // m x m (row-major)
-    float* w = sm + m * m;                 // kOjaRows x m, the old rows of W
+    float* w = sm + m * m;                 // kOjaRows x ws, the old rows of W
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) Ss[e] = (float)S[e];
     const int64_t r0 = (int64_t)blockIdx.x * kOjaRows;
     for (int e = threadIdx.x; e < kOjaRows * m; e += blockDim.x) {
-        const int i = e / m, j = e % m;
-        w[e] = r0 + i < d ? W[(int64_t)j * d + r0 + i] : 0.f;
+        const int i = e % kOjaRows, j = e / kOjaRows;      // consecutive threads: consecutive rows
+        w[i * ws + j] = r0 + i < d ? W[(int64_t)j * d + r0 + i] : 0.f;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < kOjaRows * m; e += blockDim.x) {
         const int i = e % kOjaRows, j = e / kOjaRows;      // consecutive threads: consecutive rows (coalesced)
         const int64_t r = r0 + i;
         if (r >= d) continue;
-        const float* wr = w + i * m;
+        const float* wr = w + i * ws;
         float acc = 0.f;
         for (int l = 0; l <= j; ++l) acc = __fmaf_rn(wr[l], Ss[l * m + j], acc);
         W[(int64_t)j * d + r] = wr[j] + c * (Z[(int64_t)j * d + r] - acc);
@@ -1142,16 +1143,19 @@ __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, c
                                const float* __restrict__ coef_g, const float* __restrict__ alpha_g, int64_t d, int m,
                                int rows, float inv_b, float lr, float mu, float2* __restrict__ colpart) {
     extern __shared__ float sm[];
+    // row stride m + 1: a warp's threads take consecutive rows, which a stride
+    // of m (a multiple of 32) would put in one shared-memory bank
+    const int ms = m + 1;
     float* coef = sm;                      // m x m
     float* alpha = coef + m * m;           // m
-    float* mv = alpha + m;                 // rows x m: Z rows / b
-    float* vn = mv + rows * m;             // rows x m: the new rows of V
+    float* mv = alpha + m;                 // rows x ms: Z rows / b
+    float* vn = mv + rows * ms;            // rows x ms: the new rows of V
     const int64_t r0 = (int64_t)blockIdx.x * rows;
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) coef[e] = coef_g[e];
     for (int e = threadIdx.x; e < m; e += blockDim.x) alpha[e] = alpha_g[e];
     for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
         const int i = e % rows, j = e / rows;      // consecutive threads: consecutive rows
-        mv[i * m + j] = r0 + i < d ? Z[(int64_t)j * d + r0 + i] * inv_b : 0.f;
+        mv[i * ms + j] = r0 + i < d ? Z[(int64_t)j * d + r0 + i] * inv_b : 0.f;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
@@ -1159,7 +1163,7 @@ __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, c
         const int64_t r = r0 + i;
         float out = 0.f;
         if (r < d) {
-            const float* mr = mv + i * m;
+            const float* mr = mv + i * ms;
             float g = 2.f * mr[j];
             for (int l = 0; l < j; ++l) g = __fmaf_rn(-2.f * coef[l * m + j], mr[l], g);
             const float v = V[(int64_t)j * d + r];
@@ -1169,14 +1173,14 @@ __global__ void eg_step_kernel(float* __restrict__ V, float* __restrict__ buf, c
             out = __fmaf_rn(lr, __fmaf_rn(mu, b, g), v);          // Nesterov step
             V[(int64_t)j * d + r] = out;
         }
-        vn[i * m + j] = out;
+        vn[i * ms + j] = out;
     }
     __syncthreads();
     // this block's part of each column's squared norm (squares exact as hi + lo)
     for (int j = threadIdx.x; j < m; j += blockDim.x) {
         dfloat q = {0.f, 0.f};
         for (int i = 0; i < rows; ++i) {
-            const float x = vn[i * m + j];
+            const float x = vn[i * ms + j];
             const float p = __fmul_rn(x, x);
             q = df_addx(q, df_norm(p, __fmaf_rn(x, x, -p)));
         }
@@ -1787,7 +1791,7 @@ cudaError_t rotate_and_sign(const float* Q, int64_t d, int m, const double* U, c
 
 cudaError_t oja_update(float* W, const float* Z, const double* S, int64_t d, int m, double c, cudaStream_t st,
                        const float* c_dev) {
-    const size_t smem = ((size_t)m * m + (size_t)kOjaRows * m) * sizeof(float);
+    const size_t smem = ((size_t)m * m + (size_t)kOjaRows * (m + 1)) * sizeof(float);
     cudaError_t e = allow_smem(oja_update_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
@@ -1824,7 +1828,7 @@ cudaError_t eigengame_update(float* V, float* buf, const float* Z, const double*
     float2* part = reinterpret_cast<float2*>(p);
     note_launch();
     eg_coef_kernel<<<m, kCoefThreads, 0, st>>>(C, m, inv_b, coef, alpha);
-    const size_t smem = ((size_t)m * m + (size_t)m + 2 * (size_t)rows * m) * 4;
+    const size_t smem = ((size_t)m * m + (size_t)m + 2 * (size_t)rows * (m + 1)) * 4;
     cudaError_t e = allow_smem(eg_step_kernel, smem);
     if (e != cudaSuccess) return e;
     note_launch();
