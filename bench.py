@@ -77,6 +77,9 @@ def parse_args(argv=None):
     ap.add_argument("--power-cap", type=int, default=5000, help="paper_synthetic: power steps per direction")
     ap.add_argument("--rows", type=int, default=0,
                     help="override n with a smaller row count (for profiler captures of a small case)")
+    ap.add_argument("--probe", choices=["projected_gram"], default=None,
+                    help="time one kernel family alone on the default workload's shape (for profiler captures "
+                         "of a small case with --rows): projected_gram = G = (XQ)^T(XQ), split precision")
     ap.add_argument("--cpu-leg", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-rows", type=int, default=32768, help=argparse.SUPPRESS)
     ap.add_argument("--cpu-passes", type=int, default=8, help=argparse.SUPPRESS)
@@ -1220,12 +1223,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_probe(args):
+    """One kernel family alone on the default workload's shape (n from --rows), timed with CUDA
+    events after warm-up; prints one JSON line.  projected_gram: the pPCA step's split-precision
+    G = (XQ)^T(XQ) (BF16 X, m = 128, Q orthonormal from a host QR)."""
+    import numpy as np
+    import torch
+
+    import paper_2109_03709_gb300 as P
+    import synth
+    cfg = synth.CONFIGS[DEFAULT_WORKLOAD]
+    n, d, m = args.rows or cfg.n, cfg.d, cfg.m
+    X, _ = synth.gaussian_data_torch(n, d, cfg.lam(), cfg.seed, "cuda", torch.bfloat16)
+    Qn, _ = np.linalg.qr(np.random.default_rng(cfg.seed).standard_normal((d, m)))
+    Q = torch.from_numpy(np.ascontiguousarray(Qn.T)).float().cuda()
+    G = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = P.ppca_create(X, stream=stream)
+    ms = _events_ms(lambda: P.ppca_projected_gram(h, Q, m, 0, n, G, P.PPCA_PREC_ACCURATE), max(args.steps, 1),
+                    stream)
+    P.ppca_sync(h)
+    print(json.dumps({"probe": args.probe, "n": n, "d": d, "m": m, "ms": round(ms, 4),
+                      "gbs": round(n * d * 2 / ms / 1e6, 1)}))
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.cpu_leg:
         cpu_leg(args.workload, args.cpu_rows, args.cpu_passes, args.warmup)
         return
-    if args.tune_eg_lr:
+    if args.probe:
+        run_probe(args)
+    elif args.tune_eg_lr:
         tune_eg_lr(args)
     elif args.impl == "reference":
         run_reference(args)
