@@ -1211,9 +1211,9 @@ struct ppca_batch {
     bool prime_bf16 = false;              // FP32 instances primed on a BF16 rounding of X
     std::vector<void*> prime_buf;         // per slot: that rounding, for its largest FP32 instance
 
-    // Lockstep priming: every instance's power iterations in grouped launches
-    // (grouped.h), one launch per kernel kind and iteration for the whole batch;
-    // the pPCA steps then run on the slots.
+    // Lockstep: every instance's power iterations and pPCA step in grouped
+    // launches (grouped.h), one launch per kernel kind and iteration for the
+    // whole batch; the slots are not used.
     bool lockstep = true;                 // allowed (ppca_batch_set_lockstep)
     bool grouped = false;                 // the captured graph primes in lockstep
     void* g_mem = nullptr;                // per-instance buffers, tables, descriptors
@@ -1291,14 +1291,13 @@ ppca_status bind_instance(ppca_batch* b, ppca_handle* h, int slot, const ppca_in
     return PPCA_OK;
 }
 
-// ---- lockstep priming
+// ---- lockstep batch
 
 inline int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// Lockstep priming covers a batch whose instances all prime on BF16 data (BF16
-// X, or FP32 X with BF16 priming and d % 8 == 0), with one T for all, on the
-// tensor-core pass.
+// A lockstep batch: all instances prime on BF16 data (BF16 X, or FP32 X with
+// BF16 priming and d % 8 == 0), with one T for all, on the tensor-core pass.
 bool lockstep_eligible(const ppca_batch* b) {
     if (!b->lockstep) return false;
     const int T = b->descs[0].T;
@@ -1314,7 +1313,7 @@ bool lockstep_eligible(const ppca_batch* b) {
     return true;
 }
 
-// Buffers, work tables and TMA descriptors of the lockstep priming (once, before
+// Buffers, work tables and TMA descriptors of the lockstep batch (once, before
 // the capture).  Returns false, with nothing allocated, when the device memory
 // is not there (the batch then primes on its slots).
 bool prepare_lockstep(ppca_batch* b) {
