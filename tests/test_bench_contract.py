@@ -53,3 +53,14 @@ def test_reference_arm_runs_on_rank_zero_only():
                        capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_probe_and_batch_options_parse():
+    """The profiler probe and the batch switches parse, and the default run uses neither."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = bench.parse_args(["--probe", "projected_gram", "--rows", "131072", "--steps", "5"])
+    assert a.probe == "projected_gram" and a.rows == 131072 and a.steps == 5
+    d = bench.parse_args([])
+    assert d.probe is None and not d.batch_no_lockstep and d.batch_priming == "bf16"
+    assert bench.parse_args(["--batch-no-lockstep"]).batch_no_lockstep
